@@ -1,0 +1,211 @@
+"""Plain FP64 CPU oracle for sum-factorised hexahedral assembly.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The library never
+does, and this package never imports the library.
+
+The C core (``oracle.c``) evaluates every integral by naive quadrature over the
+tensor Gauss rule with every basis function evaluated directly (no sum
+factorisation); see the header of ``oracle.c`` for the paper sections each
+routine follows.  This module only marshals numpy arrays.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FAMILIES = {"Q": 0, "DQ": 1, "NCF": 2, "NCE": 3, "VQ": 4}
+FORMS = {"mass": 0, "laplace": 1, "helmholtz": 2, "ncf_mass_divdiv": 3,
+         "nce_curlcurl": 4, "neohooke": 5, "svk": 6}
+
+# default form parameters {alpha, beta, mu, lambda} by form
+#   helmholtz: alpha * laplace + beta * mass with beta = -k^2, k = 1
+#   ncf: alpha * mass + beta * div-div;  nce: alpha * mass + beta * curl-curl
+DEFAULT_PARAMS = {
+    "mass": (0.0, 1.0, 0.0, 0.0),
+    "laplace": (1.0, 0.0, 0.0, 0.0),
+    "helmholtz": (1.0, -1.0, 0.0, 0.0),
+    "ncf_mass_divdiv": (1.0, 1.0, 0.0, 0.0),
+    "nce_curlcurl": (0.0, 1.0, 0.0, 0.0),
+    "neohooke": (0.0, 0.0, 1.0, 10.0),
+    "svk": (0.0, 0.0, 1.0, 10.0),
+}
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        d, i, i64 = C.c_double, C.c_int, C.c_int64
+        P = C.c_void_p
+        L.orc_gauss_legendre.argtypes = [i, P, P]
+        L.orc_gauss_lobatto.argtypes = [i, P, P]
+        L.orc_lagrange.argtypes = [P, i, i, d]
+        L.orc_lagrange.restype = d
+        L.orc_lagrange_deriv.argtypes = [P, i, i, d]
+        L.orc_lagrange_deriv.restype = d
+        L.orc_space_size.argtypes = [i, i, i, i, i, P, P]
+        L.orc_cell_dofs.argtypes = [i, i, i, i, i, i64, P]
+        L.orc_cell_map.argtypes = [i, i, i, i, i, P]
+        L.orc_cell_vectors.argtypes = [i, i, i, i, P, i, i, i, P, P, i, P, i64, P, i]
+        L.orc_action.argtypes = [i, i, i, i, P, i, i, i, P, P, P, i, i]
+        L.orc_cell_matrices.argtypes = [i, i, i, i, P, i, i, i, P, i64, i64, P, i]
+        L.orc_energy.argtypes = [i, i, i, P, i, i, i, P, P, P]
+        L.orc_q_node_coords.argtypes = [i, i, i, i, P, P]
+        L.orc_interp_grad_q_to_nce.argtypes = [i, i, i, i, P, P]
+        L.orc_interp_curl_nce_to_ncf.argtypes = [i, i, i, i, P, P]
+        L.orc_interp_linear_field.argtypes = [i, i, i, i, i, P, P, P, P]
+        L.orc_set_plant.argtypes = [i]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError("oracle %s failed (rc=%d)" % (what, rc))
+
+
+def gauss_legendre(n):
+    x, w = np.zeros(n), np.zeros(n)
+    _check(lib().orc_gauss_legendre(n, _p(x), _p(w)), "gauss_legendre")
+    return x, w
+
+
+def gauss_lobatto(n):
+    x, w = np.zeros(n), np.zeros(n)
+    _check(lib().orc_gauss_lobatto(n, _p(x), _p(w)), "gauss_lobatto")
+    return x, w
+
+
+def lagrange(nodes, i, x, deriv=False):
+    nodes = _f64(nodes)
+    f = lib().orc_lagrange_deriv if deriv else lib().orc_lagrange
+    return f(_p(nodes), len(nodes), i, float(x))
+
+
+def space_size(family, p, dims):
+    nd, nl = C.c_int64(), C.c_int()
+    _check(lib().orc_space_size(FAMILIES[family], p, *dims, C.byref(nd), C.byref(nl)), "space_size")
+    return nd.value, nl.value
+
+
+def cell_map(family, p, dims):
+    ndof, nloc = space_size(family, p, dims)
+    m = np.zeros((dims[0] * dims[1] * dims[2], nloc), dtype=np.int32)
+    _check(lib().orc_cell_map(FAMILIES[family], p, *dims, _p(m)), "cell_map")
+    return m
+
+
+def _params(form, params):
+    return _f64(DEFAULT_PARAMS[form] if params is None else params)
+
+
+def action(family, form, p, dims, coords, x, nq=None, params=None, nthreads=0):
+    """y = sum_K P_K^T b^K.  x: (ndof,) or (ndof, nrhs)."""
+    ndof, nloc = space_size(family, p, dims)
+    x = _f64(x)
+    nrhs = 1 if x.ndim == 1 else x.shape[1]
+    assert x.shape[0] == ndof
+    y = np.zeros_like(x)
+    pr = _params(form, params)
+    coords = _f64(coords)
+    _check(lib().orc_action(FAMILIES[family], FORMS[form], p, nq or p + 1, _p(pr), *dims,
+                            _p(coords), _p(x), _p(y), nrhs, nthreads), "action")
+    return y
+
+
+def cell_vectors(family, form, p, dims, coords, x, cells, nq=None, params=None, nthreads=0):
+    """Per-cell local vectors b^K for the listed cells: (ncells, nloc[, nrhs])."""
+    ndof, nloc = space_size(family, p, dims)
+    x = _f64(x)
+    nrhs = 1 if x.ndim == 1 else x.shape[1]
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    b = np.zeros((len(cells), nloc, nrhs))
+    pr = _params(form, params)
+    coords = _f64(coords)
+    _check(lib().orc_cell_vectors(FAMILIES[family], FORMS[form], p, nq or p + 1, _p(pr), *dims,
+                                  _p(coords), _p(x), nrhs, _p(cells), len(cells), _p(b), nthreads),
+           "cell_vectors")
+    return b[:, :, 0] if x.ndim == 1 else b
+
+
+def cell_matrices(family, form, p, dims, coords, cell_begin=0, cell_end=None, nq=None,
+                  params=None, nthreads=0):
+    """A[c, j, i], row = test j, column = trial i."""
+    ndof, nloc = space_size(family, p, dims)
+    ncell = dims[0] * dims[1] * dims[2]
+    cell_end = ncell if cell_end is None else cell_end
+    A = np.zeros((cell_end - cell_begin, nloc, nloc))
+    pr = _params(form, params)
+    coords = _f64(coords)
+    _check(lib().orc_cell_matrices(FAMILIES[family], FORMS[form], p, nq or p + 1, _p(pr), *dims,
+                                   _p(coords), cell_begin, cell_end, _p(A), nthreads), "cell_matrices")
+    return A
+
+
+def energy(form, p, dims, coords, x, nq=None, params=None):
+    e = C.c_double()
+    pr = _params(form, params)
+    coords, x = _f64(coords), _f64(x)
+    _check(lib().orc_energy(FORMS[form], p, nq or p + 1, _p(pr), *dims, _p(coords), _p(x),
+                            C.byref(e)), "energy")
+    return e.value
+
+
+def q_node_coords(p, dims, coords):
+    ndof, _ = space_size("Q", p, dims)
+    out = np.zeros((ndof, 3))
+    _check(lib().orc_q_node_coords(p, *dims, _p(_f64(coords)), _p(out)), "q_node_coords")
+    return out
+
+
+def interp_grad_q_to_nce(p, dims, xq):
+    ndof, _ = space_size("NCE", p, dims)
+    out = np.zeros(ndof)
+    _check(lib().orc_interp_grad_q_to_nce(p, *dims, _p(_f64(xq)), _p(out)), "interp_grad")
+    return out
+
+
+def interp_curl_nce_to_ncf(p, dims, xnce):
+    ndof, _ = space_size("NCF", p, dims)
+    out = np.zeros(ndof)
+    _check(lib().orc_interp_curl_nce_to_ncf(p, *dims, _p(_f64(xnce)), _p(out)), "interp_curl")
+    return out
+
+
+def interp_linear_field(family, p, dims, coords, A, b):
+    """Covariant (NCE) / contravariant (NCF) interpolant of u(x) = A x + b."""
+    ndof, _ = space_size(family, p, dims)
+    out = np.zeros(ndof)
+    _check(lib().orc_interp_linear_field(FAMILIES[family], p, *dims, _p(_f64(coords)),
+                                         _p(_f64(A)), _p(_f64(b)), _p(out)), "interp_linear_field")
+    return out
+
+
+class planted:
+    """Context manager that switches on one deliberate mistake in the oracle
+    (tests only: it shows the pins catch it)."""
+
+    def __init__(self, which):
+        self.which = which
+
+    def __enter__(self):
+        lib().orc_set_plant(self.which)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_plant(0)
+        return False

@@ -1,0 +1,95 @@
+"""The pins catch plausible mistakes: each test switches on one deliberate
+error inside the oracle (on the CPU) and checks that a pin from the other
+oracle test files now fails, then that it passes again once switched off."""
+import numpy as np
+import pytest
+
+from paper_1711_02473_gb300 import inputs
+
+D = (3, 2, 3)
+
+
+def patch_ok(orc):
+    p, X = 2, inputs.box_coords(*D, perturb=0.1, seed=0)
+    a = np.array([0.3, -0.7, 1.1])
+    u = orc.q_node_coords(p, D, X) @ a
+    Au = orc.action("Q", "laplace", p, D, X, u)
+    M = [p * d + 1 for d in D]
+    I, J, K = np.unravel_index(np.arange(len(u)), M)
+    inner = (I > 0) & (I < M[0] - 1) & (J > 0) & (J < M[1] - 1) & (K > 0) & (K < M[2] - 1)
+    return np.abs(Au[inner]).max() < 1e-13 and abs(u @ Au - a @ a) < 1e-13
+
+
+def moments_ok(orc):
+    p, X = 2, inputs.box_coords(*D, perturb=0.1, seed=0)
+    ndof, _ = orc.space_size("Q", p, D)
+    xq = orc.q_node_coords(p, D, X)
+    return (abs(orc.action("Q", "mass", p, D, X, np.ones(ndof)).sum() - 1) < 1e-13
+            and abs(orc.action("Q", "mass", p, D, X, xq[:, 0]).sum() - 0.5) < 1e-13)
+
+
+def sequence_ok(orc):
+    p, d = 2, (2, 2, 2)
+    X = inputs.box_coords(*d, perturb=0.1, seed=3)
+    nq, _ = orc.space_size("Q", p, d)
+    g = orc.interp_grad_q_to_nce(p, d, inputs.random_vector(nq, 1, seed=11))
+    y = orc.action("NCE", "nce_curlcurl", p, d, X, g, params=(0, 1, 0, 0))
+    return np.abs(y).max() < 1e-10
+
+
+def curl_energy_ok(orc):
+    """NCE_2 covariant interpolant of u = A x: u^T K u = |curl u|^2."""
+    p, d = 2, (2, 2, 2)
+    X = inputs.box_coords(*d, perturb=0.1, seed=6)
+    A = np.array([[0.3, -0.5, 0.2], [0.4, 0.1, -0.6], [-0.2, 0.7, 0.5]])
+    u = orc.interp_linear_field("NCE", p, d, X, A, np.zeros(3))
+    W = A - A.T
+    c = np.array([W[2, 1], W[0, 2], W[1, 0]])
+    return abs(u @ orc.action("NCE", "nce_curlcurl", p, d, X, u, params=(0, 1, 0, 0)) - c @ c) < 1e-12
+
+
+def rotation_ok(orc):
+    p, d = 2, (2, 1, 2)
+    X = inputs.box_coords(*d, perturb=0.1, seed=4)
+    th = 0.6
+    R = np.array([[np.cos(th), 0, np.sin(th)], [0, 1, 0], [-np.sin(th), 0, np.cos(th)]])
+    v = orc.q_node_coords(p, d, X) @ (R - np.eye(3)).T
+    u = np.concatenate([v[:, 0], v[:, 1], v[:, 2]])
+    return np.abs(orc.action("VQ", "neohooke", p, d, X, u)).max() < 1e-12
+
+
+def lagrange_ok(orc):
+    nodes, _ = orc.gauss_lobatto(4)
+    t = 0.37
+    return all(abs(sum(nodes[i] ** k * orc.lagrange(nodes, i, t, deriv=True) for i in range(4))
+                   - k * t ** (k - 1)) < 1e-12 for k in range(1, 4))
+
+
+def piola_scale_ok(orc):
+    p, h = 1, 0.5
+    X = inputs.box_coords(2, 2, 2, perturb=0.0)
+    A = orc.cell_matrices("NCF", "ncf_mass_divdiv", p, (2, 2, 2), X, params=(1, 0, 0, 0))[0]
+    A1 = orc.cell_matrices("NCF", "ncf_mass_divdiv", p, (1, 1, 1), inputs.box_coords(1, 1, 1, perturb=0.0),
+                           params=(1, 0, 0, 0))[0]
+    return np.abs(A - A1 / h).max() < 1e-13
+
+
+PLANTS = {
+    1: ("G used where G^T belongs", patch_ok),
+    2: ("|J| dropped from the scalar forms", moments_ok),
+    3: ("sign error in one curl component", curl_energy_ok),
+    4: ("wrong quadrature-weight index", moments_ok),
+    5: ("F^{-1} used for F^{-T}", rotation_ok),
+    6: ("a term dropped from the Lagrange derivative", lagrange_ok),
+    7: ("1/|J| dropped from the contravariant Piola map", piola_scale_ok),
+}
+
+
+@pytest.mark.parametrize("which", sorted(PLANTS))
+def test_planted_mistake_is_caught(orc, which):
+    name, check = PLANTS[which]
+    assert check(orc), "pin fails on the correct oracle: " + name
+    with orc.planted(which):
+        caught = not check(orc)
+    assert caught, "planted mistake not caught: " + name
+    assert check(orc)
