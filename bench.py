@@ -1,0 +1,345 @@
+"""Benchmark: sum-factorised operator action on a 64^3 perturbed hexahedral mesh.
+
+Workload (one "step"): the mass, Laplace and Helmholtz (k = 1) actions on
+Q_p and DQ_p for every requested degree (default p = 1..8), (p+1)^3 Gauss
+points, input vectors uniform[-1, 1) (seed 1), mesh interior vertices
+perturbed by uniform(+-0.1 h) (seed 0).  Metric: DoFs/s = sum of global DoFs
+of all actions in a step / step time (the paper's N/t, Sec. 4).
+
+Prints ONE JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
+reference arm) on a bounded sample of cells of the same workload instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (64, 64, 64)
+FORMS = ("mass", "laplace", "helmholtz")
+HELM = (1.0, -1.0, 0.0, 0.0)  # alpha * laplace + beta * mass, beta = -k^2, k = 1
+FP64_PEAK_GFLOPS = 1250.0     # nominal GB300 FP64 (FMA pipe), see the design doc
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sfx", choices=["sfx", "reference"])
+    ap.add_argument("--degrees", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--families", default="Q,DQ")
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--dims", default="64,64,64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def cases(args):
+    ps = [int(p) for p in args.degrees.split(",")]
+    fams = args.families.split(",")
+    return [(f, p, form) for p in ps for f in fams for form in FORMS]
+
+
+def flops_per_cell(fam, p, form):
+    """Algorithmic FP64 flops of the implemented sum-factorised action per cell
+    (q = n = p+1): 1D contractions 2*n^4 flops each -- B (3 forward, 3 back;
+    absent for DQ) and the collocation derivative Dq (3 forward, 3 back; Laplace
+    part only) -- plus the pointwise work per point: Laplace geometry 73 flops
+    (3 cross products, det, w/S, 6 dot products of the adjugate rows, scaling)
+    and 15 for the flux; mass 17 (det, w S, scaling)."""
+    n = p + 1
+    lap = form != "mass"
+    mas = form != "laplace"
+    ncontr = (0 if fam == "DQ" else 6) + (6 if lap else 0)
+    pw = (73 + 15 if lap else 0) + (17 if mas and not lap else (4 if mas else 0))
+    return ncontr * 2 * n ** 4 + pw * n ** 3
+
+
+def launches_per_action(fam):
+    return 1 if fam == "DQ" else 8
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 8:
+                continue
+            for name, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_sample(orc, inputs, wl_cases, dims, X, seconds, rng_seed=5):
+    """Time the oracle's per-cell assembly on a growing seeded sample of cells
+    per case; extrapolate to the whole mesh.  Returns (DoFs/s, desc, threads)."""
+    ncell = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(rng_seed)
+    per_case = seconds / max(1, len(wl_cases))
+    tot_dofs, tot_time, sampled = 0, 0.0, 0
+    xs = {}
+    for fam, p, form in wl_cases:
+        ndof, nloc = orc.space_size(fam, p, dims)
+        key = (fam, p)
+        if key not in xs:
+            xs[key] = inputs.random_vector(ndof, 1, seed=1)
+        m = 4
+        while True:
+            cells = rng.choice(ncell, m, replace=False)
+            t0 = time.perf_counter()
+            orc.cell_vectors(fam, form, p, dims, X, xs[key], cells, params=HELM if form == "helmholtz" else None)
+            dt = time.perf_counter() - t0
+            if dt >= per_case or m >= ncell:
+                break
+            m = min(ncell, max(m * 2, int(m * per_case / max(dt, 1e-4) * 1.1)))
+        tot_dofs += ndof
+        tot_time += dt / m * ncell
+        sampled += m
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = ("oracle per-cell assembly timed on %d seeded cells in total across %d cases (doubling until "
+            "~%.1f s per case), extrapolated linearly to all %d cells per case; scatter not timed"
+            % (sampled, len(wl_cases), per_case, ncell))
+    return tot_dofs / tot_time, desc, threads
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle as orc
+    from paper_1711_02473_gb300 import inputs
+    dims = tuple(int(v) for v in args.dims.split(","))
+    X = inputs.box_coords(*dims, perturb=0.1, seed=0)
+    wl = cases(args)
+    orc.lib()
+    secs = max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_sample(orc, inputs, wl[:1], dims, X, 0.2)
+    vals, t0 = [], time.perf_counter()
+    for s in range(args.steps):
+        v, desc, thr = cpu_sample(orc, inputs, wl, dims, X, secs, rng_seed=100 + s)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    val = float(np.median(vals))
+    out = {"impl": "reference", "metric": "DoFs/s (sum-factorised action; FP64 oracle, naive quadrature, CPU)",
+           "value": val, "unit": "DoF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": wall / max(1, args.steps) * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "config-2 action sweep: mass/laplace/helmholtz on Q_p and DQ_p, "
+                                  "p=%s, %dx%dx%d perturbed hex mesh" % (args.degrees, *dims),
+                      "families": args.families, "degrees": args.degrees},
+           "cpu_baseline": {"value": val, "unit": "DoF/s", "cores": thr, "kind": "oracle", "sample": desc},
+           "e2e": {"value": val, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_setup(args)
+    import torch
+    import paper_1711_02473_gb300 as sfx
+    from paper_1711_02473_gb300 import inputs
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sfx.build()
+    ctx = sfx.Context(local)
+    dims = tuple(int(v) for v in args.dims.split(","))
+    mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    wl = cases(args)
+    spaces, xs, ys = {}, {}, {}
+    for fam, p, form in wl:
+        if (fam, p) not in spaces:
+            sp = sfx.Space(mesh, fam, p)
+            spaces[(fam, p)] = sp
+            xs[(fam, p)] = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
+            ys[(fam, p)] = torch.empty_like(xs[(fam, p)])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    prec = args.precision
+
+    def run_case(fam, p, form):
+        sfx.sfx_assemble_action(ctx, form, spaces[(fam, p)], xs[(fam, p)], ys[(fam, p)], precision=prec,
+                                params=HELM if form == "helmholtz" else None, stream=stream)
+
+    ev = {c: [] for c in wl}
+
+    def step(record):
+        for c in wl:
+            flush.fill_(1.0)  # evict L2 between cases
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                run_case(*c)
+                e1.record(stream)
+                ev[c].append((e0, e1))
+            else:
+                run_case(*c)
+
+    for _ in range(max(3, args.warmup)):
+        step(False)
+    torch.cuda.synchronize()
+    if ctx.sync_status() != 0:
+        raise RuntimeError("device status flagged during warm-up")
+    clk = ClockSampler(local)
+    clk.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    ms_total = t0.elapsed_time(t1)
+    if ws > 1:
+        tt = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_total = tt.item()
+    ms_step = ms_total / args.steps
+    dofs_step = sum(spaces[(f, p)].ndof for f, p, _ in wl)
+    value = dofs_step * ws / (ms_step * 1e-3)
+
+    per_case, dom, dom_t = [], None, -1.0
+    ncell = mesh_cells = dims[0] * dims[1] * dims[2]
+    for c in wl:
+        ts = [a.elapsed_time(b) for a, b in ev[c]]
+        t = float(np.median(ts))
+        fam, p, form = c
+        nd = spaces[(fam, p)].ndof
+        fl = flops_per_cell(fam, p, form) * ncell
+        per_case.append({"family": fam, "p": p, "form": form, "ms": round(t, 4),
+                         "dofs_per_s": nd / (t * 1e-3), "gflops": fl / (t * 1e-3) / 1e9})
+        if t > dom_t:
+            dom_t, dom = t, c
+    fam, p, form = dom
+    nl = launches_per_action(fam)
+    fl = flops_per_cell(fam, p, form) * mesh_cells
+    achieved = fl / (dom_t * 1e-3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_action_scalar_fp64 %s p=%d %s" % dom,
+                "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                "note": "FP64 flops per action (all %d colour launches) / event time; peak = nominal FP64 "
+                        "(152 SMs x 4 FP64 flop/clk x 2.07 GHz, of nominal)" % nl}
+
+    out = {"metric": "DoFs/s (sum-factorised action, %s)" % prec, "value": value, "unit": "DoF/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "config-2 action sweep: mass/laplace/helmholtz on Q_p and DQ_p, p=%s, "
+                                  "%dx%dx%d perturbed hex mesh, (p+1)^3 Gauss points" % (args.degrees, *dims),
+                      "precision": prec, "families": args.families, "degrees": args.degrees,
+                      "l2": "flushed between cases (256 MiB write)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+           "gpu_launches": sum(launches_per_action(f) for f, _, _ in wl) * args.steps,
+           "clocks": clocks, "roofline": roofline, "per_case": per_case}
+
+    if not args.no_e2e:
+        out["e2e"] = e2e(args, sfx, torch, ctx, spaces, wl, prec, stream)
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as orc
+        X = mesh.coords()
+        v, desc, thr = cpu_sample(orc, inputs, wl, dims, X, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": "DoF/s", "cores": thr, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e(args, sfx, torch, ctx, spaces, wl, prec, stream):
+    """Same sweep through the public call with host buffers: every case copies
+    its input from pinned host memory, runs the action and copies the result
+    back, all inside the timed region."""
+    hx, hy, dx, dy = {}, {}, {}, {}
+    for key, sp in spaces.items():
+        hx[key] = torch.empty(sp.ndof, dtype=torch.float64, pin_memory=True)
+        hx[key].copy_(torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, sp.ndof)))
+        hy[key] = torch.empty(sp.ndof, dtype=torch.float64, pin_memory=True)
+        dx[key] = torch.empty(sp.ndof, dtype=torch.float64, device="cuda")
+        dy[key] = torch.empty_like(dx[key])
+
+    def step():
+        for fam, p, form in wl:
+            k = (fam, p)
+            dx[k].copy_(hx[k], non_blocking=True)
+            sfx.sfx_assemble_action(ctx, form, spaces[k], dx[k], dy[k], precision=prec,
+                                    params=HELM if form == "helmholtz" else None, stream=stream)
+            hy[k].copy_(dy[k], non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    nb = sum(spaces[(f, p)].ndof * 8 for f, p, _ in wl)
+    dofs = sum(spaces[(f, p)].ndof for f, p, _ in wl)
+    return {"value": dofs / dt, "unit": "DoF/s", "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * sfx.h -- C ABI of the sum-factorised hexahedral assembly library (GB300, sm_103a).
+ *
+ * Implements cell-local finite element assembly by sum factorisation
+ * (Homolya, Kirby & Ham, "Exposing and exploiting structure: optimal code
+ * generation for high-order finite element methods"): matrix-free operator
+ * actions (Sec. 1.1, the action as a parametrised linear form; Sec. 3.3, Eqs.
+ * coeff_eval and form_eval) and local element matrices (Sec. 3.2, Eqs.
+ * poisson_gem, opt1_product, opt2_product) on hexahedral meshes, for Q_p,
+ * DQ_p, NCF_p (H(div)), NCE_p (H(curl)) and vector Q_p elements.
+ *
+ * Conventions used by every entry point:
+ *   - Return value: SFX_OK (0) or a negative sfx_status.  No entry point throws,
+ *     exits or prints.  Argument errors are detected on the host before any
+ *     work is queued and leave outputs untouched.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the context's device (e.g. torch tensors' data_ptr()).
+ *     The caller owns every array it passes; the library never frees them.
+ *   - Objects (ctx, mesh, space) own their own host and device copies.
+ *     Create/destroy calls are synchronous.  Assembly calls are asynchronous
+ *     on the caller's stream (a cudaStream_t passed as void*, NULL = legacy
+ *     default stream).
+ *   - Reference cell [0,1]^3.  Local dofs are row-major over (i1,i2,i3) with
+ *     i3 fastest (Sec. 3.5, Eqs. rtcf_split_x/y); H(div)/H(curl) blocks are
+ *     concatenated x, y, z (Sec. 2.6, Eq. enriched_basis).
+ *   - Floating point arrays are IEEE double.  Multi-RHS vectors are
+ *     ndof x nrhs with the RHS index fastest.
+ *   - Device-detected conditions (an inverted cell, det F <= 0) never trap:
+ *     they set bits in the context's device status word, read by
+ *     sfx_sync_status().
+ */
+#ifndef SFX_H
+#define SFX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sfx_status;
+#define SFX_OK 0
+#define SFX_ERR_ARG (-1)         /* null pointer, bad size, bad enum, mismatch */
+#define SFX_ERR_UNSUPPORTED (-2) /* valid but not implemented (degree, form/family) */
+#define SFX_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define SFX_ERR_ALLOC (-4)       /* host or device allocation failed */
+#define SFX_ERR_RANGE (-5)       /* sizes exceed 32-bit dof indexing */
+
+/* device status bits (sfx_sync_status) */
+#define SFX_DEV_INVERTED 1u /* det J <= 0 at a quadrature point; the cell's output is zero */
+#define SFX_DEV_DETF 2u     /* det F <= 0 in a hyperelastic residual; that point contributes zero */
+#define SFX_DEV_BADCELL 4u  /* a caller-supplied cell id is out of range; that slot is skipped */
+
+typedef enum { SFX_Q = 0, SFX_DQ = 1, SFX_NCF = 2, SFX_NCE = 3, SFX_VQ = 4 } sfx_family;
+
+/* Forms (bilinear unless noted), with the integrand on cell K (J = dF_K/dX,
+ * S = det J, G = J^{-1}; w the quadrature weight):
+ *   SFX_MASS            S u v
+ *   SFX_LAPLACE         S (G^T grad u).(G^T grad v)                 Sec. 1.1, Eq. laplace_prefiat
+ *   SFX_HELMHOLTZ       alpha * LAPLACE + beta * MASS (beta = -k^2)
+ *   SFX_NCF_MASS_DIVDIV (1/S) [alpha (J u^).(J v^) + beta div^u div^v]  contravariant Piola
+ *   SFX_NCE_CURLCURL    beta (1/S)(J curl^u).(J curl^v) + alpha S (G^T u^).(G^T v^)
+ *                                                         covariant Piola, Eq. curl_curl_form
+ *   SFX_NEOHOOKE        residual (linear form in v): S P(F) : (grad^v G), F = I + grad^u G,
+ *                       P = mu (F - F^{-T}) + lambda ln(det F) F^{-T}
+ *   SFX_SVK             residual with P = F (lambda tr(E) I + 2 mu E), E = (F^T F - I)/2
+ *                       (Sec. 4.1, Saint Venant-Kirchhoff)                                   */
+typedef enum {
+  SFX_MASS = 0,
+  SFX_LAPLACE = 1,
+  SFX_HELMHOLTZ = 2,
+  SFX_NCF_MASS_DIVDIV = 3,
+  SFX_NCE_CURLCURL = 4,
+  SFX_NEOHOOKE = 5,
+  SFX_SVK = 6
+} sfx_form;
+
+typedef struct {
+  double alpha, beta, mu, lambda;
+} sfx_form_params;
+
+typedef enum { SFX_NODES_GLL = 0, SFX_NODES_GL = 1 } sfx_nodes;
+
+/* Arithmetic of the contractions.  FP64: all in double.  TF32X3 / BF16X3:
+ * the 1D contractions run on the tensor cores as three split products
+ * (hi*hi + hi*lo + lo*hi, FP32 accumulation); the geometry (J, det J, J^{-1}),
+ * the quadrature-weight scaling, the pointwise physics and the scatter stay in
+ * double. */
+typedef enum { SFX_PREC_FP64 = 0, SFX_PREC_TF32X3 = 1, SFX_PREC_BF16X3 = 2 } sfx_precision;
+
+/* SUMFACT: sum-factorised kernels.  NAIVE: dense 3D tabulation, O(n^6) per
+ * cell for the action (the un-factorised form of Sec. 3.2, for comparison). */
+typedef enum { SFX_ALGO_SUMFACT = 0, SFX_ALGO_NAIVE = 1 } sfx_algo;
+
+typedef struct sfx_ctx sfx_ctx;
+typedef struct sfx_mesh sfx_mesh;
+typedef struct sfx_space sfx_space;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (makes it current).  device = -1
+ * gives a host-only context: meshes and spaces get no device copies (for
+ * inspecting maps and coordinates without a GPU) and assembly calls on them
+ * return SFX_ERR_ARG.  Allocates the
+ * 4-byte device status word.  Errors: SFX_ERR_ARG (out NULL), SFX_ERR_CUDA. */
+sfx_status sfx_ctx_create(int device, sfx_ctx** out);
+void sfx_ctx_destroy(sfx_ctx* ctx);
+
+/* Wait for `stream`, then copy the device status word (SFX_DEV_* bits) to
+ * *bits and clear it.  Errors: SFX_ERR_ARG, SFX_ERR_CUDA. */
+sfx_status sfx_sync_status(sfx_ctx* ctx, void* stream, uint32_t* bits);
+
+const char* sfx_status_string(sfx_status s);
+
+/* -------------------------------------------------------------------- mesh */
+
+/* Structured nx*ny*nz hexahedral box on [0,1]^3.  Vertex (I,J,K) (K fastest,
+ * v = (I*(ny+1)+J)*(nz+1)+K); cell (i,j,k) likewise; cell vertex 4a+2b+c is the
+ * reference corner (a,b,c).  Each interior vertex is moved by
+ * perturb*h_d*(2u-1) along each axis d, u from the SplitMix64 stream `seed`
+ * (draw k = mix(seed + (k+1)*0x9E3779B97F4A7C15), u = (z>>11)*2^-53; three draws
+ * per interior vertex in vertex order).  The trilinear coordinate field is the
+ * vector-Q1 field of Sec. 3.1.  Errors: SFX_ERR_ARG (n < 1, |perturb| >= 0.5),
+ * SFX_ERR_RANGE, SFX_ERR_ALLOC, SFX_ERR_CUDA. */
+sfx_status sfx_mesh_create_box(sfx_ctx* ctx, int nx, int ny, int nz, double perturb, uint64_t seed,
+                               sfx_mesh** out);
+/* Same topology with caller-supplied vertex coordinates (host, nvert x 3,
+ * copied).  Errors as above. */
+sfx_status sfx_mesh_create_structured(sfx_ctx* ctx, int nx, int ny, int nz, const double* xyz_host,
+                                      sfx_mesh** out);
+/* Host view of the vertex coordinates (owned by the mesh). */
+sfx_status sfx_mesh_info(const sfx_mesh* mesh, int64_t* nvert, int64_t* ncell, const double** xyz_host);
+void sfx_mesh_destroy(sfx_mesh* mesh);
+
+/* ------------------------------------------------------------------- space */
+
+/* Function space of `family` and degree p (1 <= p <= 8) on `mesh`; builds the
+ * int32 cell-node map (ncell x nloc, host and device) and, for the continuous
+ * families, the 8-colour cell lists used by the conflict-free scatter.
+ * Numbering: Q_p/vector-Q_p global node (I,J,K) on the (pN+1)^3 GLL grid,
+ * vector-Q_p component-major; DQ_p cell-major (cell*n^3 + l); NCF_p/NCE_p one
+ * lexicographic grid per block, block-major.  The mesh must outlive the space.
+ * Errors: SFX_ERR_ARG, SFX_ERR_UNSUPPORTED (p out of range), SFX_ERR_RANGE,
+ * SFX_ERR_ALLOC, SFX_ERR_CUDA. */
+sfx_status sfx_space_create(const sfx_mesh* mesh, sfx_family family, int degree, sfx_space** out);
+/* Sizes and a host view of the cell-node map (owned by the space). */
+sfx_status sfx_space_info(const sfx_space* space, int64_t* ndof, int* nloc, int64_t* ncell,
+                          const int32_t** host_map);
+void sfx_space_destroy(sfx_space* space);
+
+/* ------------------------------------------------------------ tabulation */
+
+/* 1D rule and Lagrange table on [0,1] (Sec. 1.2, Eq. tpps; Sec. 2.5, Eq.
+ * colocated): `points`/`weights` (host, nq each) receive the quadrature rule
+ * `qrule` (GL: Gauss-Legendre, GLL: Gauss-Lobatto) with nq points; `table`
+ * (host, nq x ndof1d row-major) receives phi_i(x_q) (deriv = 0) or phi_i'(x_q)
+ * (deriv = 1) for the Lagrange basis on the ndof1d `nodes`.  Any output may be
+ * NULL.  Errors: SFX_ERR_ARG (ndof1d < 1, GLL with < 2 points, nq < 1 or > 32). */
+sfx_status sfx_tabulate_1d(sfx_nodes nodes, int ndof1d, sfx_nodes qrule, int nq, int deriv,
+                           double* points, double* weights, double* table);
+
+/* --------------------------------------------------------------- assembly */
+
+/* Operator action / residual y = sum_K P_K^T b^K with
+ * b^K_j = sum_q w_q I(u_K, psi_j)(xi_q) on the (p+1)^3 Gauss rule (Sec. 1.1;
+ * Sec. 3.3, Eqs. coeff_def, coeff_eval, form_eval), u_K = sum_i x_{map(K,i)} psi_i.
+ *   x, y   device, ndof x nrhs doubles (x read-only; must not alias y)
+ *   nrhs   1 <= nrhs <= 64
+ *   accumulate = 0: y is overwritten (zeroed on `stream` first); 1: y += action.
+ *   params may be NULL (defaults: Helmholtz alpha=1, beta=-1; NCF alpha=beta=1;
+ *   NCE alpha=0, beta=1; hyperelastic mu=1, lambda=10).
+ * The scatter is deterministic (8 colour passes for shared-dof families).
+ * Errors: SFX_ERR_ARG (null, nrhs, form/family mismatch), SFX_ERR_UNSUPPORTED
+ * (precision or algorithm not available for this form), SFX_ERR_CUDA. */
+sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                               const sfx_space* space, const double* x, double* y, int nrhs,
+                               int accumulate, sfx_precision prec, sfx_algo algo, void* stream);
+
+/* Per-cell local vectors b^K (no scatter) for the cells listed in `cells`
+ * (device int64, ncells entries, each in [0, ncell)), written to b (device,
+ * ncells x nloc x nrhs).  Same arithmetic as sfx_assemble_action.  Used to
+ * compare sampled cells of large meshes.  Errors as sfx_assemble_action. */
+sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                     const sfx_space* space, const double* x, int nrhs,
+                                     const int64_t* cells, int64_t ncells, double* b,
+                                     sfx_precision prec, void* stream);
+
+/* Local element matrices A[c][j][i] (row = test j, column = trial i) of the
+ * bilinear forms for cells [cell_begin, cell_end) (Sec. 3.2: argument
+ * factorisation into P^(k,l) factors and sum factorisation, O(n^7) per cell;
+ * Sec. 3.5 for the H(div)/H(curl) blocks).  A: device,
+ * (cell_end - cell_begin) x nloc x nloc doubles.  algo NAIVE uses the dense
+ * tabulation (O(n^9)).  Errors: SFX_ERR_ARG (range, null, residual forms),
+ * SFX_ERR_UNSUPPORTED, SFX_ERR_CUDA. */
+sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                      const sfx_space* space, int64_t cell_begin, int64_t cell_end,
+                                      double* A, sfx_precision prec, sfx_algo algo, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFX_H */

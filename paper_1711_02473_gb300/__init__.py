@@ -1,0 +1,242 @@
+"""Python binding of the sfx C ABI (include/sfx.h): argument marshalling only.
+
+Every computation runs in the CUDA library ``_build/libsfx.so``; this module
+passes pointers and sizes.  Device arrays are torch CUDA tensors (float64,
+int64), used for memory and streams only.  If the library has not been built
+the first call raises ``RuntimeError``; there is no CPU fallback.
+
+Function names mirror the C entry points: ``sfx_assemble_action`` etc.; the
+small classes ``Context``, ``Mesh`` and ``Space`` own the C objects.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsfx.so")
+
+FAMILY = {"Q": 0, "DQ": 1, "NCF": 2, "NCE": 3, "VQ": 4}
+FORM = {"mass": 0, "laplace": 1, "helmholtz": 2, "ncf_mass_divdiv": 3, "nce_curlcurl": 4,
+        "neohooke": 5, "svk": 6}
+NODES = {"GLL": 0, "GL": 1}
+PRECISION = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+ALGO = {"sumfact": 0, "naive": 1}
+DEV_INVERTED, DEV_DETF, DEV_BADCELL = 1, 2, 4
+STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported combination", -3: "CUDA runtime error",
+          -4: "allocation failed", -5: "size exceeds 32-bit indexing"}
+
+# every symbol include/sfx.h declares
+EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_string",
+           "sfx_mesh_create_box", "sfx_mesh_create_structured", "sfx_mesh_info", "sfx_mesh_destroy",
+           "sfx_space_create", "sfx_space_info", "sfx_space_destroy", "sfx_tabulate_1d",
+           "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices"]
+
+
+class SfxError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, STATUS.get(code, "unknown"), code))
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("mu", C.c_double), ("lam", C.c_double)]
+
+
+_lib = None
+
+
+def build(force=False):
+    """Compile the CUDA library for sm_103a (nvcc) into _build/."""
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsfx.so is not built (%s); run paper_1711_02473_gb300.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        P, i, i64, u64, d = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
+        L.sfx_ctx_create.argtypes = [i, C.POINTER(P)]
+        L.sfx_ctx_destroy.argtypes = [P]
+        L.sfx_ctx_destroy.restype = None
+        L.sfx_sync_status.argtypes = [P, P, C.POINTER(C.c_uint32)]
+        L.sfx_status_string.argtypes = [i]
+        L.sfx_status_string.restype = C.c_char_p
+        L.sfx_mesh_create_box.argtypes = [P, i, i, i, d, u64, C.POINTER(P)]
+        L.sfx_mesh_create_structured.argtypes = [P, i, i, i, P, C.POINTER(P)]
+        L.sfx_mesh_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(P)]
+        L.sfx_mesh_destroy.argtypes = [P]
+        L.sfx_mesh_destroy.restype = None
+        L.sfx_space_create.argtypes = [P, i, i, C.POINTER(P)]
+        L.sfx_space_info.argtypes = [P, C.POINTER(i64), C.POINTER(i), C.POINTER(i64), C.POINTER(P)]
+        L.sfx_space_destroy.argtypes = [P]
+        L.sfx_space_destroy.restype = None
+        L.sfx_tabulate_1d.argtypes = [i, i, i, i, i, P, P, P]
+        L.sfx_assemble_action.argtypes = [P, i, C.POINTER(_Params), P, P, P, i, i, i, i, P]
+        L.sfx_assemble_cell_vectors.argtypes = [P, i, C.POINTER(_Params), P, P, i, P, i64, P, i, P]
+        L.sfx_assemble_cell_matrices.argtypes = [P, i, C.POINTER(_Params), P, i64, i64, P, i, i, P]
+        for name in EXPORTS:
+            f = getattr(L, name)
+            if f.restype is C.c_int:
+                f.restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise SfxError(rc, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype_name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise TypeError("expected %s, got %s" % (dtype_name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _params(params):
+    if params is None:
+        return None
+    a = tuple(params) + (0.0,) * (4 - len(params))
+    return C.byref(_Params(*a))
+
+
+class Context:
+    def __init__(self, device=0):
+        self.h = C.c_void_p()
+        _check(lib().sfx_ctx_create(device, C.byref(self.h)), "sfx_ctx_create")
+
+    def sync_status(self, stream=None):
+        bits = C.c_uint32()
+        _check(lib().sfx_sync_status(self.h, _stream(stream), C.byref(bits)), "sfx_sync_status")
+        return bits.value
+
+    def close(self):
+        if self.h:
+            lib().sfx_ctx_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    def __init__(self, ctx, h, dims):
+        self.ctx, self.h, self.dims = ctx, h, tuple(dims)
+
+    @classmethod
+    def box(cls, ctx, nx, ny, nz, perturb=0.1, seed=0):
+        h = C.c_void_p()
+        _check(lib().sfx_mesh_create_box(ctx.h, nx, ny, nz, perturb, seed, C.byref(h)), "sfx_mesh_create_box")
+        return cls(ctx, h, (nx, ny, nz))
+
+    @classmethod
+    def structured(cls, ctx, nx, ny, nz, xyz):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        if xyz.shape != ((nx + 1) * (ny + 1) * (nz + 1), 3):
+            raise ValueError("xyz must be (nvert, 3)")
+        h = C.c_void_p()
+        _check(lib().sfx_mesh_create_structured(ctx.h, nx, ny, nz, xyz.ctypes.data_as(C.c_void_p), C.byref(h)),
+               "sfx_mesh_create_structured")
+        return cls(ctx, h, (nx, ny, nz))
+
+    def coords(self):
+        nv, nc, p = C.c_int64(), C.c_int64(), C.c_void_p()
+        _check(lib().sfx_mesh_info(self.h, C.byref(nv), C.byref(nc), C.byref(p)), "sfx_mesh_info")
+        return np.ctypeslib.as_array(C.cast(p, C.POINTER(C.c_double)), shape=(nv.value, 3)).copy()
+
+    def close(self):
+        if self.h:
+            lib().sfx_mesh_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Space:
+    def __init__(self, mesh, family, degree):
+        self.mesh, self.family, self.p = mesh, family, degree
+        self.h = C.c_void_p()
+        _check(lib().sfx_space_create(mesh.h, FAMILY[family], degree, C.byref(self.h)), "sfx_space_create")
+        nd, nl, nc, mp = C.c_int64(), C.c_int(), C.c_int64(), C.c_void_p()
+        _check(lib().sfx_space_info(self.h, C.byref(nd), C.byref(nl), C.byref(nc), C.byref(mp)), "sfx_space_info")
+        self.ndof, self.nloc, self.ncell = nd.value, nl.value, nc.value
+        self._map = mp
+
+    def cell_map(self):
+        return np.ctypeslib.as_array(C.cast(self._map, C.POINTER(C.c_int32)), shape=(self.ncell, self.nloc)).copy()
+
+    def close(self):
+        if self.h:
+            lib().sfx_space_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sfx_tabulate_1d(nodes, ndof1d, qrule, nq, deriv=0):
+    pts, wts, tab = np.zeros(nq), np.zeros(nq), np.zeros((nq, ndof1d))
+    P = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(lib().sfx_tabulate_1d(NODES[nodes], ndof1d, NODES[qrule], nq, deriv, P(pts), P(wts), P(tab)),
+           "sfx_tabulate_1d")
+    return pts, wts, tab
+
+
+def sfx_assemble_action(ctx, form, space, x, y, nrhs=None, accumulate=False, precision="fp64",
+                        algo="sumfact", params=None, stream=None):
+    nrhs = nrhs if nrhs is not None else (1 if x.dim() == 1 else x.shape[1])
+    if x.numel() != space.ndof * nrhs or y.numel() != space.ndof * nrhs:
+        raise ValueError("x and y must hold ndof * nrhs doubles")
+    _check(lib().sfx_assemble_action(ctx.h, FORM[form], _params(params), space.h, _dptr(x, "float64"),
+                                     _dptr(y, "float64"), nrhs, int(bool(accumulate)), PRECISION[precision],
+                                     ALGO[algo], _stream(stream)), "sfx_assemble_action")
+    return y
+
+
+def sfx_assemble_cell_vectors(ctx, form, space, x, cells, b, nrhs=None, precision="fp64", params=None,
+                              stream=None):
+    nrhs = nrhs if nrhs is not None else (1 if x.dim() == 1 else x.shape[1])
+    if b.numel() != cells.numel() * space.nloc * nrhs:
+        raise ValueError("b must hold ncells * nloc * nrhs doubles")
+    _check(lib().sfx_assemble_cell_vectors(ctx.h, FORM[form], _params(params), space.h, _dptr(x, "float64"), nrhs,
+                                           _dptr(cells, "int64"), cells.numel(), _dptr(b, "float64"),
+                                           PRECISION[precision], _stream(stream)), "sfx_assemble_cell_vectors")
+    return b
+
+
+def sfx_assemble_cell_matrices(ctx, form, space, cell_begin, cell_end, A, precision="fp64", algo="sumfact",
+                               params=None, stream=None):
+    if A.numel() != (cell_end - cell_begin) * space.nloc * space.nloc:
+        raise ValueError("A must hold ncells * nloc * nloc doubles")
+    _check(lib().sfx_assemble_cell_matrices(ctx.h, FORM[form], _params(params), space.h, cell_begin, cell_end,
+                                            _dptr(A, "float64"), PRECISION[precision], ALGO[algo],
+                                            _stream(stream)), "sfx_assemble_cell_matrices")
+    return A

@@ -1,0 +1,108 @@
+// kern_common.cuh -- device helpers shared by the kernel files: the per-degree
+// 1D tables in constant memory, status flags, trilinear geometry and the
+// per-team 1D contractions used by sum factorisation.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sfx_internal.h"
+
+namespace sfx {
+
+// Per-translation-unit copy of the 1D tables, one per degree (index p).  The
+// contents depend only on p, so every space uploads the same bytes.
+static __constant__ Tab1D c_tab[kMaxDeg + 1];
+
+#define SFX_DEFINE_TAB_UPLOAD(fn)                                                          \
+  int fn(const Tab1D* t) {                                                                 \
+    return (int)cudaMemcpyToSymbol(c_tab, t, sizeof(Tab1D), sizeof(Tab1D) * (size_t)t->p); \
+  }
+
+__device__ __forceinline__ void set_flag(uint32_t* st, uint32_t bit) { atomicOr(st, bit); }
+
+// Resolve the cell handled by `slot`; false if the slot is idle or the
+// caller's id is out of range (flagged).
+__device__ __forceinline__ bool slot_cell(const ActArgs& a, int64_t slot, int64_t ncell_total, int* cell) {
+  if (slot >= a.ncells) return false;
+  if (a.cells) { *cell = a.cells[slot]; return true; }
+  if (a.cells64) {
+    int64_t c = a.cells64[slot];
+    if (c < 0 || c >= ncell_total) { set_flag(a.status, SFX_DEV_BADCELL); return false; }
+    *cell = (int)c;
+    return true;
+  }
+  *cell = (int)slot;
+  return true;
+}
+
+// Columns of the trilinear Jacobian on the tensor grid of quadrature points.
+// Column d of J = dx/dxi_d does not depend on xi_d (Sec. 3.1: the coordinate
+// field is vector-Q1 and its derivative tabulation factorises), so it is
+// tabulated on the 2D grid of the other two coordinates:
+//   Jc[0][(a,b)] = dx/dxi1 at (xi2, xi3) = (x_a, x_b)
+//   Jc[1][(a,b)] = dx/dxi2 at (xi1, xi3) = (x_a, x_b)
+//   Jc[2][(a,b)] = dx/dxi3 at (xi1, xi2) = (x_a, x_b)
+// X holds the 8 corners, corner (a,b,c) at 4a+2b+c.  Thread t = (a,b) fills entry t.
+template <int N>
+__device__ __forceinline__ void jacobian_columns(const double (*X)[3], const double* xq, double (*Jc)[N * N][3],
+                                                 int t) {
+  const int a = t / N, b = t - (t / N) * N;
+  const double ya = xq[a], yb = xq[b];
+  const double w00 = (1.0 - ya) * (1.0 - yb), w01 = (1.0 - ya) * yb, w10 = ya * (1.0 - yb), w11 = ya * yb;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Jc[0][t][k] = w00 * (X[4][k] - X[0][k]) + w01 * (X[5][k] - X[1][k]) + w10 * (X[6][k] - X[2][k]) +
+                  w11 * (X[7][k] - X[3][k]);
+    Jc[1][t][k] = w00 * (X[2][k] - X[0][k]) + w01 * (X[3][k] - X[1][k]) + w10 * (X[6][k] - X[4][k]) +
+                  w11 * (X[7][k] - X[5][k]);
+    Jc[2][t][k] = w00 * (X[1][k] - X[0][k]) + w01 * (X[3][k] - X[2][k]) + w10 * (X[5][k] - X[4][k]) +
+                  w11 * (X[7][k] - X[6][k]);
+  }
+}
+
+__device__ __forceinline__ void cross3(const double* u, const double* v, double* w) {
+  w[0] = u[1] * v[2] - u[2] * v[1];
+  w[1] = u[2] * v[0] - u[0] * v[2];
+  w[2] = u[0] * v[1] - u[1] * v[0];
+}
+__device__ __forceinline__ double dot3(const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; }
+
+// One 1D contraction of an N0 x N1 x N2 array held in shared memory, along
+// axis AX, for the fiber owned by thread `t` (fibers are indexed by the two
+// other axes; t < product of their extents):
+//   out[.., r, ..] = (ACC ? out[.., r, ..] : 0) + sum_k M[r][k] in[.., k, ..]
+// TRANS uses M[k][r].  NIN / NOUT: extents of the contracted axis before and
+// after; D0..D2 the full extents of the *input* array (the output has NOUT at
+// AX).  In-place use (in == out, NIN == NOUT) is safe: a fiber is read whole
+// into registers before it is written, and no other thread touches it.
+template <int D0, int D1, int D2, int AX, int NOUT, bool TRANS, bool ACC, int LDM>
+__device__ __forceinline__ void contract(const double* in, double* out, const double (*M)[LDM], int t) {
+  constexpr int NIN = AX == 0 ? D0 : (AX == 1 ? D1 : D2);
+  // output extents
+  constexpr int E1 = AX == 1 ? NOUT : D1, E2 = AX == 2 ? NOUT : D2;
+  int ib, ob, is, os;
+  if (AX == 0) {
+    const int f0 = t / D2, f1 = t - (t / D2) * D2;  // (i1, i2)
+    ib = f0 * D2 + f1; is = D1 * D2;
+    ob = f0 * E2 + f1; os = E1 * E2;
+  } else if (AX == 1) {
+    const int f0 = t / D2, f1 = t - (t / D2) * D2;  // (i0, i2)
+    ib = f0 * D1 * D2 + f1; is = D2;
+    ob = f0 * E1 * E2 + f1; os = E2;
+  } else {
+    const int f0 = t / D1, f1 = t - (t / D1) * D1;  // (i0, i1)
+    ib = (f0 * D1 + f1) * D2; is = 1;
+    ob = (f0 * E1 + f1) * E2; os = 1;
+  }
+  double v[NIN];
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) v[k] = in[ib + k * is];
+#pragma unroll
+  for (int r = 0; r < NOUT; ++r) {
+    double acc = ACC ? out[ob + r * os] : 0.0;
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) acc = fma(TRANS ? M[k][r] : M[r][k], v[k], acc);
+    out[ob + r * os] = acc;
+  }
+}
+
+}  // namespace sfx

@@ -1,0 +1,592 @@
+// sfx_host.cpp -- host side of the C ABI: contexts, meshes, spaces (dof maps,
+// colouring), 1D tabulation, argument validation and kernel dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "sfx_internal.h"
+
+using namespace sfx;
+
+namespace {
+
+sfx_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SFX_OK : SFX_ERR_CUDA; }
+
+template <class T>
+sfx_status to_device(const T* h, size_t n, T** d) {
+  *d = nullptr;
+  if (n == 0) return SFX_OK;
+  if (cudaMalloc((void**)d, n * sizeof(T)) != cudaSuccess) { *d = nullptr; return SFX_ERR_ALLOC; }
+  if (cudaMemcpy(*d, h, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(*d); *d = nullptr; return SFX_ERR_CUDA;
+  }
+  return SFX_OK;
+}
+
+// SplitMix64 draw k of stream `seed` (Steele, Lea & Flood 2014, counter form).
+inline uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Legendre P_n and P_n' at t by the three-term recurrence.
+void legendre(int n, double t, double* P, double* dP) {
+  double p0 = 1.0, p1 = t;
+  if (n == 0) { *P = 1.0; *dP = 0.0; return; }
+  for (int k = 1; k < n; ++k) {
+    double p2 = ((2.0 * k + 1.0) * t * p1 - k * p0) / (k + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;
+  *dP = n * (t * p1 - p0) / (t * t - 1.0);  // valid for |t| < 1
+}
+
+bool family_ok(sfx_family f) { return f >= SFX_Q && f <= SFX_VQ; }
+bool form_ok(sfx_family fam, sfx_form form) {
+  switch (form) {
+    case SFX_MASS: case SFX_LAPLACE: case SFX_HELMHOLTZ: return fam == SFX_Q || fam == SFX_DQ;
+    case SFX_NCF_MASS_DIVDIV: return fam == SFX_NCF;
+    case SFX_NCE_CURLCURL: return fam == SFX_NCE;
+    case SFX_NEOHOOKE: case SFX_SVK: return fam == SFX_VQ;
+  }
+  return false;
+}
+
+sfx_form_params default_params(sfx_form form) {
+  switch (form) {
+    case SFX_HELMHOLTZ: return {1.0, -1.0, 0.0, 0.0};
+    case SFX_NCF_MASS_DIVDIV: return {1.0, 1.0, 0.0, 0.0};
+    case SFX_NCE_CURLCURL: return {0.0, 1.0, 0.0, 0.0};
+    case SFX_NEOHOOKE: case SFX_SVK: return {0.0, 0.0, 1.0, 10.0};
+    default: return {0.0, 0.0, 0.0, 0.0};
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ 1D rules
+namespace sfx {
+
+void gauss_legendre(int n, double* x, double* w) {
+  // roots of P_n by Newton from the asymptotic guesses cos(pi (i + 3/4)/(n + 1/2))
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double P, dP;
+    for (int it = 0; it < 100; ++it) {
+      legendre(n, t, &P, &dP);
+      double dt = P / dP;
+      t -= dt;
+      if (std::fabs(dt) < 1e-17) break;
+    }
+    legendre(n, t, &P, &dP);
+    // ascending order on [0,1]
+    x[n - 1 - i] = 0.5 * (t + 1.0);
+    w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dP * dP);  // 2/((1-t^2)P'^2) halved
+  }
+}
+
+void gauss_lobatto(int n, double* x, double* w) {
+  // interior nodes: roots of g(t) = P_{m-1}(t) - t P_m(t) (proportional to
+  // (1-t^2) P_m'(t)), m = n-1, by Newton from Chebyshev-Lobatto guesses.
+  int m = n - 1;
+  x[0] = 0.0;
+  x[n - 1] = 1.0;
+  for (int i = 1; i < n - 1; ++i) {
+    double t = -std::cos(M_PI * i / m);
+    for (int it = 0; it < 100; ++it) {
+      double Pm, dPm, Pm1, dPm1;
+      legendre(m, t, &Pm, &dPm);
+      legendre(m - 1, t, &Pm1, &dPm1);
+      double g = Pm1 - t * Pm;
+      double dg = dPm1 - Pm - t * dPm;
+      double dt = g / dg;
+      t -= dt;
+      if (std::fabs(dt) < 1e-17) break;
+    }
+    x[i] = 0.5 * (t + 1.0);
+  }
+  for (int i = 0; i < n; ++i) {
+    double t = 2.0 * x[i] - 1.0, P, dP;
+    if (i == 0 || i == n - 1) {
+      P = (i == 0 && (m % 2)) ? -1.0 : 1.0;
+    } else {
+      legendre(m, t, &P, &dP);
+    }
+    w[i] = 1.0 / (n * (n - 1.0) * P * P);  // 2/(n(n-1)P_m^2) halved
+  }
+}
+
+// Barycentric Lagrange evaluation (Berrut & Trefethen 2004): values or first
+// derivatives of the n basis functions on `nodes` at q points.
+void lagrange_table(const double* nodes, int n, const double* pts, int q, int deriv, double* out) {
+  double lam[64];
+  for (int j = 0; j < n; ++j) {
+    double prod = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) prod *= nodes[j] - nodes[k];
+    lam[j] = 1.0 / prod;
+  }
+  for (int a = 0; a < q; ++a) {
+    double t = pts[a];
+    int hit = -1;
+    for (int j = 0; j < n; ++j)
+      if (t == nodes[j]) hit = j;
+    double* row = out + (size_t)a * n;
+    if (hit >= 0) {
+      for (int j = 0; j < n; ++j) {
+        if (!deriv) { row[j] = (j == hit) ? 1.0 : 0.0; continue; }
+        if (j != hit) {
+          row[j] = (lam[j] / lam[hit]) / (nodes[hit] - nodes[j]);
+        } else {
+          double s = 0.0;
+          for (int k = 0; k < n; ++k)
+            if (k != hit) s += 1.0 / (nodes[hit] - nodes[k]);
+          row[j] = s;
+        }
+      }
+      continue;
+    }
+    double den = 0.0, s = 0.0;
+    for (int k = 0; k < n; ++k) {
+      den += lam[k] / (t - nodes[k]);
+      s += 1.0 / (t - nodes[k]);
+    }
+    for (int j = 0; j < n; ++j) {
+      double l = (lam[j] / (t - nodes[j])) / den;
+      row[j] = deriv ? l * (s - 1.0 / (t - nodes[j])) : l;
+    }
+  }
+}
+
+void make_tab1d(int p, Tab1D* t) {
+  std::memset(t, 0, sizeof(*t));
+  int n = p + 1, q = p + 1;
+  t->p = p;
+  t->q = q;
+  gauss_legendre(q, t->x, t->w);
+  double xc[kMaxN], wc[kMaxN], xd[kMaxN], wd[kMaxN], tmp[kMaxQ * kMaxN];
+  gauss_lobatto(n, xc, wc);
+  lagrange_table(xc, n, t->x, q, 0, tmp);
+  for (int a = 0; a < q; ++a) for (int j = 0; j < n; ++j) t->Bc[a][j] = tmp[a * n + j];
+  lagrange_table(xc, n, t->x, q, 1, tmp);
+  for (int a = 0; a < q; ++a) for (int j = 0; j < n; ++j) t->Dc[a][j] = tmp[a * n + j];
+  gauss_legendre(p, xd, wd);
+  lagrange_table(xd, p, t->x, q, 0, tmp);
+  for (int a = 0; a < q; ++a) for (int j = 0; j < p; ++j) t->Bd[a][j] = tmp[a * p + j];
+  lagrange_table(xd, p, t->x, q, 1, tmp);
+  for (int a = 0; a < q; ++a) for (int j = 0; j < p; ++j) t->Dd[a][j] = tmp[a * p + j];
+  lagrange_table(t->x, q, t->x, q, 1, tmp);
+  for (int a = 0; a < q; ++a) for (int j = 0; j < q; ++j) t->Dq[a][j] = tmp[a * q + j];
+}
+
+}  // namespace sfx
+
+// Copy the 1D tables of one degree into every kernel file's constant memory.
+static int upload_tables(const Tab1D* t) {
+  int e = upload_tab_scalar(t);
+  return e;
+}
+
+// ------------------------------------------------------------------ context
+extern "C" sfx_status sfx_ctx_create(int device, sfx_ctx** out) {
+  if (!out || device < -1) return SFX_ERR_ARG;
+  *out = nullptr;
+  sfx_ctx* c = new (std::nothrow) sfx_ctx;
+  if (!c) return SFX_ERR_ALLOC;
+  c->device = device;
+  if (device < 0) {  // host-only: meshes and spaces without device copies
+    *out = c;
+    return SFX_OK;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) { delete c; return SFX_ERR_CUDA; }
+  if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess) { delete c; return SFX_ERR_ALLOC; }
+  if (cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+    cudaFree(c->d_status); delete c; return SFX_ERR_CUDA;
+  }
+  *out = c;
+  return SFX_OK;
+}
+
+extern "C" void sfx_ctx_destroy(sfx_ctx* c) {
+  if (!c) return;
+  if (c->d_status) cudaFree(c->d_status);
+  delete c;
+}
+
+extern "C" sfx_status sfx_sync_status(sfx_ctx* c, void* stream, uint32_t* bits) {
+  if (!c || !bits || c->device < 0) return SFX_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t h = 0;
+  if (cudaMemcpyAsync(&h, c->d_status, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SFX_ERR_CUDA;
+  if (cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), s) != cudaSuccess) return SFX_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SFX_ERR_CUDA;
+  *bits = h;
+  return SFX_OK;
+}
+
+extern "C" const char* sfx_status_string(sfx_status s) {
+  switch (s) {
+    case SFX_OK: return "ok";
+    case SFX_ERR_ARG: return "invalid argument";
+    case SFX_ERR_UNSUPPORTED: return "unsupported combination";
+    case SFX_ERR_CUDA: return "CUDA runtime error";
+    case SFX_ERR_ALLOC: return "allocation failed";
+    case SFX_ERR_RANGE: return "size exceeds 32-bit indexing";
+  }
+  return "unknown status";
+}
+
+// --------------------------------------------------------------------- mesh
+static sfx_status mesh_finish(sfx_mesh* m) {
+  const int nx = m->nx, ny = m->ny, nz = m->nz;
+  std::vector<int32_t> vmap((size_t)m->ncell * 8);
+  for (int64_t c = 0; c < m->ncell; ++c) {
+    int64_t k = c % nz, j = (c / nz) % ny, i = c / ((int64_t)ny * nz);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int cc = 0; cc < 2; ++cc)
+          vmap[c * 8 + 4 * a + 2 * b + cc] = (int32_t)(((i + a) * (ny + 1) + (j + b)) * (int64_t)(nz + 1) + (k + cc));
+  }
+  if (m->ctx->device < 0) return SFX_OK;
+  sfx_status st = to_device(m->xyz.data(), m->xyz.size(), &m->d_xyz);
+  if (st) return st;
+  return to_device(vmap.data(), vmap.size(), &m->d_vmap);
+}
+
+static sfx_status mesh_alloc(sfx_ctx* ctx, int nx, int ny, int nz, sfx_mesh** out) {
+  if (!ctx || !out || nx < 1 || ny < 1 || nz < 1) return SFX_ERR_ARG;
+  *out = nullptr;
+  int64_t nvert = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  if (nvert > 2000000000LL) return SFX_ERR_RANGE;
+  sfx_mesh* m = new (std::nothrow) sfx_mesh;
+  if (!m) return SFX_ERR_ALLOC;
+  m->ctx = ctx;
+  m->nx = nx; m->ny = ny; m->nz = nz;
+  m->nvert = nvert;
+  m->ncell = (int64_t)nx * ny * nz;
+  try { m->xyz.resize((size_t)nvert * 3); } catch (...) { delete m; return SFX_ERR_ALLOC; }
+  *out = m;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_mesh_create_box(sfx_ctx* ctx, int nx, int ny, int nz, double perturb, uint64_t seed,
+                                          sfx_mesh** out) {
+  if (!(std::fabs(perturb) < 0.5)) return SFX_ERR_ARG;
+  sfx_mesh* m;
+  sfx_status st = mesh_alloc(ctx, nx, ny, nz, &m);
+  if (st) return st;
+  const double h[3] = {1.0 / nx, 1.0 / ny, 1.0 / nz};
+  uint64_t draw = 0;
+  for (int64_t I = 0; I <= nx; ++I)
+    for (int64_t J = 0; J <= ny; ++J)
+      for (int64_t K = 0; K <= nz; ++K) {
+        double* v = &m->xyz[(size_t)(((I * (ny + 1) + J) * (nz + 1) + K) * 3)];
+        v[0] = (double)I / nx;
+        v[1] = (double)J / ny;
+        v[2] = (double)K / nz;
+        bool interior = I > 0 && I < nx && J > 0 && J < ny && K > 0 && K < nz;
+        if (interior && perturb != 0.0) {
+          for (int d = 0; d < 3; ++d) {
+            double u = (double)(splitmix64_at(seed, draw++) >> 11) * 0x1.0p-53;
+            v[d] += perturb * h[d] * (2.0 * u - 1.0);
+          }
+        }
+      }
+  st = mesh_finish(m);
+  if (st) { sfx_mesh_destroy(m); return st; }
+  *out = m;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_mesh_create_structured(sfx_ctx* ctx, int nx, int ny, int nz, const double* xyz,
+                                                 sfx_mesh** out) {
+  if (!xyz) return SFX_ERR_ARG;
+  sfx_mesh* m;
+  sfx_status st = mesh_alloc(ctx, nx, ny, nz, &m);
+  if (st) return st;
+  std::memcpy(m->xyz.data(), xyz, m->xyz.size() * sizeof(double));
+  st = mesh_finish(m);
+  if (st) { sfx_mesh_destroy(m); return st; }
+  *out = m;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_mesh_info(const sfx_mesh* m, int64_t* nvert, int64_t* ncell, const double** xyz) {
+  if (!m) return SFX_ERR_ARG;
+  if (nvert) *nvert = m->nvert;
+  if (ncell) *ncell = m->ncell;
+  if (xyz) *xyz = m->xyz.data();
+  return SFX_OK;
+}
+
+extern "C" void sfx_mesh_destroy(sfx_mesh* m) {
+  if (!m) return;
+  if (m->d_xyz) cudaFree(m->d_xyz);
+  if (m->d_vmap) cudaFree(m->d_vmap);
+  delete m;
+}
+
+// -------------------------------------------------------------------- space
+namespace {
+
+// One tensor-product block of a family: per-axis node count and whether the
+// factor is continuous (shared between neighbouring cells).
+struct Block {
+  int cnt[3];
+  bool cont[3];
+  int64_t ext[3];  // global grid extent per axis
+  int loff;
+  int64_t goff;
+};
+
+int blocks_of(sfx_family fam, int p, const int64_t N[3], Block* B, int64_t* ndof, int* nloc) {
+  int n = p + 1;
+  if (fam == SFX_Q || fam == SFX_VQ) {
+    int nb = fam == SFX_VQ ? 3 : 1;
+    int64_t per = 1;
+    for (int d = 0; d < 3; ++d) per *= p * N[d] + 1;
+    for (int c = 0; c < nb; ++c) {
+      for (int d = 0; d < 3; ++d) { B[c].cnt[d] = n; B[c].cont[d] = true; B[c].ext[d] = p * N[d] + 1; }
+      B[c].loff = c * n * n * n;
+      B[c].goff = c * per;
+    }
+    *ndof = nb * per;
+    *nloc = nb * n * n * n;
+    return nb;
+  }
+  if (fam == SFX_DQ) {
+    *nloc = n * n * n;
+    *ndof = N[0] * N[1] * N[2] * (int64_t)(*nloc);
+    return 0;  // cell-major, no grid blocks
+  }
+  int64_t goff = 0;
+  int loff = 0;
+  for (int c = 0; c < 3; ++c) {
+    int64_t tot = 1;
+    int cnt = 1;
+    for (int d = 0; d < 3; ++d) {
+      bool cont = (fam == SFX_NCF) ? (d == c) : (d != c);
+      B[c].cont[d] = cont;
+      B[c].cnt[d] = cont ? p + 1 : p;
+      B[c].ext[d] = cont ? p * N[d] + 1 : p * N[d];
+      tot *= B[c].ext[d];
+      cnt *= B[c].cnt[d];
+    }
+    B[c].loff = loff;
+    B[c].goff = goff;
+    loff += cnt;
+    goff += tot;
+  }
+  *ndof = goff;
+  *nloc = loff;
+  return 3;
+}
+
+}  // namespace
+
+extern "C" sfx_status sfx_space_create(const sfx_mesh* mesh, sfx_family fam, int p, sfx_space** out) {
+  if (!mesh || !out || !family_ok(fam)) return SFX_ERR_ARG;
+  *out = nullptr;
+  if (p < 1 || p > kMaxDeg) return SFX_ERR_UNSUPPORTED;
+  const int64_t N[3] = {mesh->nx, mesh->ny, mesh->nz};
+  Block B[3];
+  int64_t ndof;
+  int nloc;
+  int nb = blocks_of(fam, p, N, B, &ndof, &nloc);
+  if (ndof >= (1LL << 31) - 1) return SFX_ERR_RANGE;
+  sfx_space* s = new (std::nothrow) sfx_space;
+  if (!s) return SFX_ERR_ALLOC;
+  s->mesh = mesh;
+  s->family = fam;
+  s->p = p;
+  s->nloc = nloc;
+  s->ndof = ndof;
+  const int64_t ncell = mesh->ncell;
+  try { s->map.resize((size_t)ncell * nloc); } catch (...) { delete s; return SFX_ERR_ALLOC; }
+  for (int64_t c = 0; c < ncell; ++c) {
+    int32_t* row = &s->map[(size_t)c * nloc];
+    if (fam == SFX_DQ) {
+      for (int l = 0; l < nloc; ++l) row[l] = (int32_t)(c * nloc + l);
+      continue;
+    }
+    int64_t ci[3] = {c / (N[1] * N[2]), (c / N[2]) % N[1], c % N[2]};
+    for (int b = 0; b < nb; ++b) {
+      int l = B[b].loff;
+      for (int i1 = 0; i1 < B[b].cnt[0]; ++i1)
+        for (int i2 = 0; i2 < B[b].cnt[1]; ++i2)
+          for (int i3 = 0; i3 < B[b].cnt[2]; ++i3) {
+            int ii[3] = {i1, i2, i3};
+            int64_t g[3];
+            for (int d = 0; d < 3; ++d) g[d] = (B[b].cont[d] ? B[b].cnt[d] - 1 : B[b].cnt[d]) * ci[d] + ii[d];
+            row[l++] = (int32_t)(B[b].goff + (g[0] * B[b].ext[1] + g[1]) * B[b].ext[2] + g[2]);
+          }
+    }
+  }
+  // colouring: cells with the same parity in every axis share no vertex
+  std::vector<int32_t> cells((size_t)ncell);
+  if (fam == SFX_DQ) {
+    s->ncolour = 1;
+    for (int64_t c = 0; c < ncell; ++c) cells[c] = (int32_t)c;
+    s->colour_off = {0, ncell};
+  } else {
+    s->ncolour = 8;
+    s->colour_off.assign(9, 0);
+    for (int64_t c = 0; c < ncell; ++c) {
+      int col = (int)(((c / (N[1] * N[2])) & 1) * 4 + (((c / N[2]) % N[1]) & 1) * 2 + ((c % N[2]) & 1));
+      s->colour_off[col + 1]++;
+    }
+    for (int k = 0; k < 8; ++k) s->colour_off[k + 1] += s->colour_off[k];
+    std::vector<int64_t> pos(s->colour_off.begin(), s->colour_off.end() - 1);
+    for (int64_t c = 0; c < ncell; ++c) {
+      int col = (int)(((c / (N[1] * N[2])) & 1) * 4 + (((c / N[2]) % N[1]) & 1) * 2 + ((c % N[2]) & 1));
+      cells[pos[col]++] = (int32_t)c;
+    }
+  }
+  make_tab1d(p, &s->tab);
+  if (mesh->ctx->device < 0) {
+    *out = s;
+    return SFX_OK;
+  }
+  if (upload_tables(&s->tab) != 0) { sfx_space_destroy(s); return SFX_ERR_CUDA; }
+  sfx_status st = to_device(s->map.data(), s->map.size(), &s->d_map);
+  if (!st) st = to_device(cells.data(), cells.size(), &s->d_cells);
+  if (st) { sfx_space_destroy(s); return st; }
+  *out = s;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_space_info(const sfx_space* s, int64_t* ndof, int* nloc, int64_t* ncell,
+                                     const int32_t** host_map) {
+  if (!s) return SFX_ERR_ARG;
+  if (ndof) *ndof = s->ndof;
+  if (nloc) *nloc = s->nloc;
+  if (ncell) *ncell = s->mesh->ncell;
+  if (host_map) *host_map = s->map.data();
+  return SFX_OK;
+}
+
+extern "C" void sfx_space_destroy(sfx_space* s) {
+  if (!s) return;
+  if (s->d_map) cudaFree(s->d_map);
+  if (s->d_cells) cudaFree(s->d_cells);
+  if (s->d_naive) cudaFree(s->d_naive);
+  delete s;
+}
+
+// --------------------------------------------------------------- tabulation
+extern "C" sfx_status sfx_tabulate_1d(sfx_nodes nodes, int ndof1d, sfx_nodes qrule, int nq, int deriv,
+                                      double* points, double* weights, double* table) {
+  if (ndof1d < 1 || ndof1d > 32 || nq < 1 || nq > 32) return SFX_ERR_ARG;
+  if ((nodes != SFX_NODES_GLL && nodes != SFX_NODES_GL) || (qrule != SFX_NODES_GLL && qrule != SFX_NODES_GL))
+    return SFX_ERR_ARG;
+  if ((nodes == SFX_NODES_GLL && ndof1d < 2) || (qrule == SFX_NODES_GLL && nq < 2)) return SFX_ERR_ARG;
+  if (deriv != 0 && deriv != 1) return SFX_ERR_ARG;
+  double xq[32], wq[32], xn[32], wn[32];
+  if (qrule == SFX_NODES_GL) gauss_legendre(nq, xq, wq); else gauss_lobatto(nq, xq, wq);
+  if (nodes == SFX_NODES_GL) gauss_legendre(ndof1d, xn, wn); else gauss_lobatto(ndof1d, xn, wn);
+  if (points) std::memcpy(points, xq, nq * sizeof(double));
+  if (weights) std::memcpy(weights, wq, nq * sizeof(double));
+  if (table) lagrange_table(xn, ndof1d, xq, nq, deriv, table);
+  return SFX_OK;
+}
+
+// ----------------------------------------------------------------- assembly
+extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                          const sfx_space* sp, const double* x, double* y, int nrhs,
+                                          int accumulate, sfx_precision prec, sfx_algo algo, void* stream) {
+  if (!ctx || !sp || !x || !y || nrhs < 1 || nrhs > 64 || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
+  if (!form_ok(sp->family, form)) return SFX_ERR_ARG;
+  if (x == y) return SFX_ERR_ARG;
+  if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3 || (algo != SFX_ALGO_SUMFACT && algo != SFX_ALGO_NAIVE))
+    return SFX_ERR_ARG;
+  sfx_form_params pr = params ? *params : default_params(form);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!accumulate) {
+    if (cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess) return SFX_ERR_CUDA;
+  }
+  ActArgs a{};
+  a.map = sp->d_map;
+  a.vmap = sp->mesh->d_vmap;
+  a.xyz = sp->mesh->d_xyz;
+  a.x = x;
+  a.y = y;
+  a.nrhs = nrhs;
+  a.cell_vectors = 0;
+  a.alpha = pr.alpha; a.beta = pr.beta; a.mu = pr.mu; a.lambda = pr.lambda;
+  a.status = ctx->d_status;
+  for (int col = 0; col < sp->ncolour; ++col) {
+    a.cells = sp->d_cells + sp->colour_off[col];
+    a.ncells = sp->colour_off[col + 1] - sp->colour_off[col];
+    if (a.ncells == 0) continue;
+    int e;
+    if (sp->family == SFX_Q || sp->family == SFX_DQ) e = launch_action_scalar(sp, form, prec, algo, a, stream);
+    else if (algo != SFX_ALGO_SUMFACT) return SFX_ERR_UNSUPPORTED;
+    else if (sp->family == SFX_VQ) e = launch_action_elastic(sp, form, prec, a, stream);
+    else e = launch_action_hdivcurl(sp, form, prec, a, stream);
+    if (e == -1) return SFX_ERR_UNSUPPORTED;
+    if (e) return SFX_ERR_CUDA;
+  }
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                                const sfx_space* sp, const double* x, int nrhs,
+                                                const int64_t* cells, int64_t ncells, double* b,
+                                                sfx_precision prec, void* stream) {
+  if (!ctx || !sp || !x || !b || nrhs < 1 || nrhs > 64 || ncells < 0 || ctx->device < 0 || !sp->d_map)
+    return SFX_ERR_ARG;
+  if (ncells > 0 && !cells) return SFX_ERR_ARG;
+  if (!form_ok(sp->family, form)) return SFX_ERR_ARG;
+  if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3) return SFX_ERR_ARG;
+  if (ncells == 0) return SFX_OK;
+  sfx_form_params pr = params ? *params : default_params(form);
+  ActArgs a{};
+  a.map = sp->d_map;
+  a.cells = nullptr;
+  a.cells64 = cells;
+  a.ncells = ncells;
+  a.vmap = sp->mesh->d_vmap;
+  a.xyz = sp->mesh->d_xyz;
+  a.x = x;
+  a.y = b;
+  a.nrhs = nrhs;
+  a.cell_vectors = 1;
+  a.alpha = pr.alpha; a.beta = pr.beta; a.mu = pr.mu; a.lambda = pr.lambda;
+  a.status = ctx->d_status;
+  int e;
+  if (sp->family == SFX_Q || sp->family == SFX_DQ) e = launch_action_scalar(sp, form, prec, SFX_ALGO_SUMFACT, a, stream);
+  else if (sp->family == SFX_VQ) e = launch_action_elastic(sp, form, prec, a, stream);
+  else e = launch_action_hdivcurl(sp, form, prec, a, stream);
+  if (e == -1) return SFX_ERR_UNSUPPORTED;
+  return e ? SFX_ERR_CUDA : SFX_OK;
+}
+
+extern "C" sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                                 const sfx_space* sp, int64_t cell_begin, int64_t cell_end,
+                                                 double* A, sfx_precision prec, sfx_algo algo, void* stream) {
+  if (!ctx || !sp || !A || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
+  if (!form_ok(sp->family, form) || form == SFX_NEOHOOKE || form == SFX_SVK) return SFX_ERR_ARG;
+  if (cell_begin < 0 || cell_end > sp->mesh->ncell || cell_begin > cell_end) return SFX_ERR_ARG;
+  if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
+  if (algo != SFX_ALGO_SUMFACT && algo != SFX_ALGO_NAIVE) return SFX_ERR_ARG;
+  if (cell_end == cell_begin) return SFX_OK;
+  sfx_form_params pr = params ? *params : default_params(form);
+  MatArgs a{};
+  a.vmap = sp->mesh->d_vmap;
+  a.xyz = sp->mesh->d_xyz;
+  a.cell_begin = cell_begin;
+  a.ncells = cell_end - cell_begin;
+  a.A = A;
+  a.alpha = pr.alpha;
+  a.beta = pr.beta;
+  a.status = ctx->d_status;
+  int e = launch_cell_matrices(sp, form, algo, a, stream);
+  if (e == -1) return SFX_ERR_UNSUPPORTED;
+  return e ? SFX_ERR_CUDA : SFX_OK;
+}

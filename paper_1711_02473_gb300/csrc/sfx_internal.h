@@ -1,0 +1,110 @@
+// sfx_internal.h -- objects and kernel-argument structs shared by the host code
+// (sfx_host.cpp) and the CUDA kernels.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/sfx.h"
+
+namespace sfx {
+
+constexpr int kMaxDeg = 8;          // p <= 8
+constexpr int kMaxN = kMaxDeg + 1;  // 1D nodes per axis
+constexpr int kMaxQ = kMaxDeg + 1;  // 1D quadrature points per axis (q = p + 1)
+
+// 1D tables on [0,1] for one degree, passed by value to kernels (constant bank).
+//   w, x     Gauss rule with q = p+1 points
+//   Bc, Dc   GLL Lagrange basis (p+1 nodes) values / derivatives at the points  [q][p+1]
+//   Bd, Dd   Gauss-node Lagrange basis with p nodes (the dP_{p-1} factor)       [q][p]
+//   Dq       collocation derivative on the Gauss points themselves              [q][q]
+//            (Dq[a][b] = l_b'(x_a), l_b the Lagrange basis on the q points)
+//   vq       (1 - x, x): the trilinear coordinate element's 1D factors at the points
+struct Tab1D {
+  int p, q;
+  double w[kMaxQ], x[kMaxQ];
+  double Bc[kMaxQ][kMaxN], Dc[kMaxQ][kMaxN];
+  double Bd[kMaxQ][kMaxN], Dd[kMaxQ][kMaxN];
+  double Dq[kMaxQ][kMaxQ];
+};
+
+// 1D rules and Lagrange tables (host, double).  Newton iteration on the
+// Legendre recurrence; barycentric Lagrange evaluation.
+void gauss_legendre(int n, double* x, double* w);
+void gauss_lobatto(int n, double* x, double* w);
+void lagrange_table(const double* nodes, int n, const double* pts, int q, int deriv, double* out /*q x n*/);
+void make_tab1d(int p, Tab1D* t);
+
+}  // namespace sfx
+
+struct sfx_ctx {
+  int device = 0;
+  uint32_t* d_status = nullptr;  // device status word (SFX_DEV_* bits)
+};
+
+struct sfx_mesh {
+  sfx_ctx* ctx = nullptr;
+  int nx = 0, ny = 0, nz = 0;
+  int64_t nvert = 0, ncell = 0;
+  std::vector<double> xyz;         // host, nvert x 3
+  double* d_xyz = nullptr;         // device copy
+  int32_t* d_vmap = nullptr;       // device, ncell x 8 (cell -> vertices, corner (a,b,c) at 4a+2b+c)
+};
+
+struct sfx_space {
+  const sfx_mesh* mesh = nullptr;
+  sfx_family family = SFX_Q;
+  int p = 1, nloc = 0;
+  int64_t ndof = 0;
+  std::vector<int32_t> map;        // host, ncell x nloc
+  int32_t* d_map = nullptr;        // device copy
+  // conflict-free scatter: cells grouped by colour (8 colours for shared-dof
+  // families, 1 for DQ); d_cells holds the cell ids colour by colour.
+  int ncolour = 1;
+  double* d_naive = nullptr;       // dense 3D tabulation for the naive kernels (built on first use)
+  std::vector<int64_t> colour_off; // ncolour + 1 offsets into d_cells
+  int32_t* d_cells = nullptr;
+  sfx::Tab1D tab;                  // 1D tables of degree p
+};
+
+// ----------------------------------------------------------------- kernels
+namespace sfx {
+
+// Arguments of one action launch (one colour, or a cell list).
+struct ActArgs {
+  const int32_t* map;     // ncell x nloc
+  const int32_t* cells;   // cell ids of this launch (colour list), or
+  const int64_t* cells64; // caller's cell list (bounds-checked on the device); both null: slot == cell
+  int64_t ncells;         // cells in this launch
+  const int32_t* vmap;    // ncell x 8
+  const double* xyz;      // nvert x 3
+  const double* x;        // ndof x nrhs
+  double* y;              // ndof x nrhs (scatter) or ncells x nloc x nrhs (cell vectors)
+  int nrhs;
+  int cell_vectors;       // 1: write b^K per slot instead of scattering
+  double alpha, beta, mu, lambda;
+  uint32_t* status;
+};
+
+// Launchers (defined in the .cu files).  Return a cudaError_t as int.
+int launch_action_scalar(const sfx_space* sp, sfx_form form, sfx_precision prec, sfx_algo algo,
+                         const ActArgs& a, void* stream);
+int launch_action_hdivcurl(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
+                           void* stream);
+int launch_action_elastic(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
+                          void* stream);
+
+struct MatArgs {
+  const int32_t* vmap;
+  const double* xyz;
+  int64_t cell_begin, ncells;
+  double* A;              // ncells x nloc x nloc
+  double alpha, beta;
+  uint32_t* status;
+};
+int launch_cell_matrices(const sfx_space* sp, sfx_form form, sfx_algo algo, const MatArgs& a, void* stream);
+
+// Each kernel file keeps its own constant-memory copy of the 1D tables.
+int upload_tab_scalar(const Tab1D* t);
+
+}  // namespace sfx

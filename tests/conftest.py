@@ -17,3 +17,15 @@ def orc():
     import oracle
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """(sfx module, torch, Context on cuda:0) -- GPU tests only."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1711_02473_gb300 as sfx
+    sfx.build()
+    ctx = sfx.Context(0)
+    yield sfx, torch, ctx

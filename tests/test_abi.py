@@ -1,0 +1,119 @@
+"""The C-ABI library loads, exports every symbol include/sfx.h declares, and
+its host-side logic (1D rules and tables, box coordinates, dof maps,
+argument checking) agrees with the oracle and the input generator -- all
+without a GPU (host-only context, device = -1)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1711_02473_gb300 as sfx
+from paper_1711_02473_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    sfx.build()
+    return sfx.lib()
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "sfx.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sfx_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(L):
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(L, s), s
+    assert sorted(sfx.EXPORTS) == syms
+
+
+def test_status_strings(L):
+    for code, text in sfx.STATUS.items():
+        assert L.sfx_status_string(code).decode() == text
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 16])
+def test_tabulate_matches_oracle(L, orc, n):
+    """The library's Newton/barycentric rules and tables against the oracle's
+    Golub-Welsch rules and product-formula Lagrange polynomials."""
+    x, w, _ = sfx.sfx_tabulate_1d("GL", max(n, 1), "GL", n)
+    xo, wo = orc.gauss_legendre(n)
+    np.testing.assert_allclose(x, xo, atol=2e-16)
+    np.testing.assert_allclose(w, wo, atol=2e-16)
+    if n >= 2:
+        x, w, _ = sfx.sfx_tabulate_1d("GLL", n, "GLL", n)
+        xo, wo = orc.gauss_lobatto(n)
+        np.testing.assert_allclose(x, xo, atol=2e-16)
+        np.testing.assert_allclose(w, wo, atol=2e-16)
+    for nodes in ("GLL", "GL"):
+        if nodes == "GLL" and n < 2:
+            continue
+        xn = (orc.gauss_lobatto if nodes == "GLL" else orc.gauss_legendre)(n)[0]
+        for deriv in (0, 1):
+            for q in (n, n + 1):
+                pts, _, tab = sfx.sfx_tabulate_1d(nodes, n, "GL", q, deriv)
+                ref = np.array([[orc.lagrange(xn, i, t, deriv=bool(deriv)) for i in range(n)] for t in pts])
+                np.testing.assert_allclose(tab, ref, atol=1e-13 * max(1.0, np.abs(ref).max()))
+    # collocated table (nodes = points) is the identity (Sec. 2.5, Eq. colocated)
+    _, _, tab = sfx.sfx_tabulate_1d("GL", n, "GL", n, 0)
+    np.testing.assert_array_equal(tab, np.eye(n))
+
+
+def test_tabulate_rejects_bad_arguments(L):
+    P = C.c_void_p
+    assert L.sfx_tabulate_1d(0, 1, 1, 3, 0, None, None, None) == -1  # GLL needs 2 nodes
+    assert L.sfx_tabulate_1d(1, 3, 0, 1, 0, None, None, None) == -1  # GLL rule needs 2 points
+    assert L.sfx_tabulate_1d(1, 3, 1, 0, 0, None, None, None) == -1
+    assert L.sfx_tabulate_1d(1, 3, 1, 3, 2, None, None, None) == -1
+    assert L.sfx_tabulate_1d(7, 3, 1, 3, 0, None, None, None) == -1
+
+
+@pytest.fixture(scope="module")
+def host_ctx(L):
+    return sfx.Context(-1)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (4, 3, 5), (8, 8, 8)])
+def test_box_coords_bit_identical(host_ctx, dims):
+    m = sfx.Mesh.box(host_ctx, *dims, perturb=0.1, seed=0)
+    np.testing.assert_array_equal(m.coords(), inputs.box_coords(*dims, perturb=0.1, seed=0))
+    m2 = sfx.Mesh.box(host_ctx, *dims, perturb=0.05, seed=77)
+    np.testing.assert_array_equal(m2.coords(), inputs.box_coords(*dims, perturb=0.05, seed=77))
+
+
+@pytest.mark.parametrize("fam", ["Q", "DQ", "VQ", "NCF", "NCE"])
+@pytest.mark.parametrize("p", [1, 2, 5, 8])
+def test_cell_maps_bit_identical(host_ctx, orc, fam, p):
+    dims = (3, 2, 4)
+    m = sfx.Mesh.box(host_ctx, *dims)
+    s = sfx.Space(m, fam, p)
+    ndof, nloc = orc.space_size(fam, p, dims)
+    assert (s.ndof, s.nloc, s.ncell) == (ndof, nloc, 24)
+    np.testing.assert_array_equal(s.cell_map(), orc.cell_map(fam, p, dims))
+
+
+def test_argument_errors(L, host_ctx):
+    h = C.c_void_p()
+    assert L.sfx_ctx_create(0, None) == -1
+    assert L.sfx_ctx_create(-2, C.byref(h)) == -1
+    assert L.sfx_mesh_create_box(host_ctx.h, 0, 1, 1, 0.1, 0, C.byref(h)) == -1
+    assert L.sfx_mesh_create_box(host_ctx.h, 1, 1, 1, 0.5, 0, C.byref(h)) == -1
+    assert L.sfx_mesh_create_box(None, 1, 1, 1, 0.1, 0, C.byref(h)) == -1
+    m = sfx.Mesh.box(host_ctx, 2, 2, 2)
+    assert L.sfx_space_create(m.h, 9, 2, C.byref(h)) == -1
+    assert L.sfx_space_create(m.h, 0, 0, C.byref(h)) == -2
+    assert L.sfx_space_create(m.h, 0, 9, C.byref(h)) == -2
+    s = sfx.Space(m, "Q", 2)
+    # assembly on a host-only context is an argument error, not a crash
+    assert L.sfx_assemble_action(host_ctx.h, 1, None, s.h, C.c_void_p(8), C.c_void_p(16), 1, 0, 0, 0, None) == -1
+    bits = C.c_uint32()
+    assert L.sfx_sync_status(host_ctx.h, None, C.byref(bits)) == -1
+    assert L.sfx_assemble_cell_matrices(host_ctx.h, 5, None, s.h, 0, 1, C.c_void_p(8), 0, 0, None) == -1
