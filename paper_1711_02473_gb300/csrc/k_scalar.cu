@@ -62,14 +62,14 @@ __global__ void __launch_bounds__(256) k_action_scalar_fp64(const ActArgs a, con
   const int64_t slot = (int64_t)blockIdx.x * cb + team;
   const bool active = team < cb && slot_cell(a, slot, ncell_total, &cell);
   if (t == 0) *bad = 0;
-  if (t < 8) {
+  for (int c = t; c < 8; c += N2) {  // a team may have fewer than 8 threads (p = 1)
     if (active) {
-      const int v = a.vmap[(int64_t)cell * 8 + t];
-      X[t][0] = a.xyz[(int64_t)v * 3 + 0];
-      X[t][1] = a.xyz[(int64_t)v * 3 + 1];
-      X[t][2] = a.xyz[(int64_t)v * 3 + 2];
+      const int v = a.vmap[(int64_t)cell * 8 + c];
+      X[c][0] = a.xyz[(int64_t)v * 3 + 0];
+      X[c][1] = a.xyz[(int64_t)v * 3 + 1];
+      X[c][2] = a.xyz[(int64_t)v * 3 + 2];
     } else {  // idle team: unit cube keeps the arithmetic finite
-      X[t][0] = (t >> 2) & 1; X[t][1] = (t >> 1) & 1; X[t][2] = t & 1;
+      X[c][0] = (c >> 2) & 1; X[c][1] = (c >> 1) & 1; X[c][2] = c & 1;
     }
   }
   __syncthreads();
