@@ -27,6 +27,7 @@ FORMS = ("mass", "laplace", "helmholtz")
 HELM = (1.0, -1.0, 0.0, 0.0)  # alpha * laplace + beta * mass, beta = -k^2, k = 1
 FP64_PEAK_GFLOPS = 1250.0     # nominal GB300 FP64 (FMA pipe), see the design doc
 L2_FLUSH_BYTES = 256 << 20
+METRIC = "DoFs/s of the operator action (config-2 sweep)"
 
 
 def parse():
@@ -37,7 +38,8 @@ def parse():
     ap.add_argument("--impl", default="sfx", choices=["sfx", "reference"])
     ap.add_argument("--degrees", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--families", default="Q,DQ")
-    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--precision", default="tf32x3,fp64",
+                    help="comma list; the first is the headline, the others are timed beside it")
     ap.add_argument("--dims", default="64,64,64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -176,13 +178,14 @@ def run_reference(args):
         vals.append(v)
     wall = time.perf_counter() - t0
     val = float(np.median(vals))
-    out = {"impl": "reference", "metric": "DoFs/s (sum-factorised action; FP64 oracle, naive quadrature, CPU)",
+    out = {"impl": "reference", "metric": METRIC,
            "value": val, "unit": "DoF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": wall / max(1, args.steps) * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "config-2 action sweep: mass/laplace/helmholtz on Q_p and DQ_p, "
-                                  "p=%s, %dx%dx%d perturbed hex mesh" % (args.degrees, *dims),
-                      "families": args.families, "degrees": args.degrees},
+                                  "p=%s, %dx%dx%d perturbed hex mesh, (p+1)^3 Gauss points" % (args.degrees, *dims),
+                      "precision": "fp64 (CPU oracle, naive quadrature)", "families": args.families,
+                      "degrees": args.degrees},
            "cpu_baseline": {"value": val, "unit": "DoF/s", "cores": thr, "kind": "oracle", "sample": desc},
            "e2e": {"value": val, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -214,8 +217,77 @@ def main():
             ys[(fam, p)] = torch.empty_like(xs[(fam, p)])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    prec = args.precision
+    precs = args.precision.split(",")
+    arms = {pr: time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, pr, flush, stream, ws, local)
+            for pr in precs}
+    prec = precs[0]
+    head = arms[prec]
+    ms_step = head["ms_step"]
+    dofs_step = sum(spaces[(f, p)].ndof for f, p, _ in wl)
+    value = dofs_step * ws / (ms_step * 1e-3)
+    # error of each arm against the FP64 arm, per case (the FP64 path matches
+    # the oracle to <= 1e-12 in the GPU tests)
+    if "fp64" in arms and prec != "fp64":
+        for c_head, c64 in zip(head["per_case"], arms["fp64"]["per_case"]):
+            c_head["rel_err_vs_fp64"] = rel_err_case(sfx, torch, ctx, spaces, xs, c_head, prec)
+    mesh_cells = dims[0] * dims[1] * dims[2]
+    dom = max(head["per_case"], key=lambda c: c["ms"])
+    fam, p, form = dom["family"], dom["p"], dom["form"]
+    if prec == "fp64":
+        fl = flops_per_cell(fam, p, form) * mesh_cells
+        achieved = fl / (dom["ms"] * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": "k_action_scalar_fp64 %s p=%d %s" % (fam, p, form),
+                    "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                    "note": "FP64 flops per action (all colour launches) / event time; peak = nominal FP64 "
+                            "(152 SMs x 4 FP64 flop/clk x 2.07 GHz, of nominal)"}
+    else:
+        fl = geometry_flops_per_cell(fam, p, form) * mesh_cells
+        achieved = fl / (dom["ms"] * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": "k_action_scalar_mixed %s p=%d %s %s" % (fam, p, form, prec),
+                    "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                    "note": "binding resource = FP64 pipe (geometry J, det J, adj J, w/S per point and the "
+                            "FP64 scatter); achieved = those FP64 flops / event time, of nominal"}
 
+    out = {"metric": METRIC, "value": value, "unit": "DoF/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "config-2 action sweep: mass/laplace/helmholtz on Q_p and DQ_p, p=%s, "
+                                  "%dx%dx%d perturbed hex mesh, (p+1)^3 Gauss points" % (args.degrees, *dims),
+                      "precision": prec, "families": args.families, "degrees": args.degrees,
+                      "l2": "flushed between cases (256 MiB write)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+           "gpu_launches": sum(launches_per_action(f) for f, _, _ in wl) * args.steps * len(precs),
+           "clocks": head["clocks"], "roofline": roofline, "per_case": head["per_case"],
+           "arms": {pr: {"value": dofs_step * ws / (arms[pr]["ms_step"] * 1e-3), "ms_per_step": arms[pr]["ms_step"],
+                         "clocks": arms[pr]["clocks"]} for pr in precs}}
+    if "fp64" in arms and prec != "fp64":
+        out["arms"]["fp64"]["per_case"] = arms["fp64"]["per_case"]
+        out["speedup_vs_fp64"] = arms["fp64"]["ms_step"] / ms_step
+
+    if not args.no_e2e:
+        out["e2e"] = e2e(args, sfx, torch, ctx, spaces, wl, prec, stream)
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as orc
+        X = mesh.coords()
+        v, desc, thr = cpu_sample(orc, inputs, wl, dims, X, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": "DoF/s", "cores": thr, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def geometry_flops_per_cell(fam, p, form):
+    """FP64 flops per cell left in the mixed kernel: the per-point geometry
+    (Laplace part 73 flops, mass part 17) plus the FP64 scatter (1 per dof)."""
+    n = p + 1
+    lap = form != "mass"
+    return ((73 if lap else 17) + 1) * n ** 3
+
+
+def time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, prec, flush, stream, ws, local):
     def run_case(fam, p, form):
         sfx.sfx_assemble_action(ctx, form, spaces[(fam, p)], xs[(fam, p)], ys[(fam, p)], precision=prec,
                                 params=HELM if form == "helmholtz" else None, stream=stream)
@@ -259,54 +331,26 @@ def main():
         tt = torch.tensor([ms_total], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         ms_total = tt.item()
-    ms_step = ms_total / args.steps
-    dofs_step = sum(spaces[(f, p)].ndof for f, p, _ in wl)
-    value = dofs_step * ws / (ms_step * 1e-3)
-
-    per_case, dom, dom_t = [], None, -1.0
-    ncell = mesh_cells = dims[0] * dims[1] * dims[2]
+    ncell = next(iter(spaces.values())).ncell
+    per_case = []
     for c in wl:
-        ts = [a.elapsed_time(b) for a, b in ev[c]]
-        t = float(np.median(ts))
+        t = float(np.median([a.elapsed_time(b) for a, b in ev[c]]))
         fam, p, form = c
         nd = spaces[(fam, p)].ndof
-        fl = flops_per_cell(fam, p, form) * ncell
-        per_case.append({"family": fam, "p": p, "form": form, "ms": round(t, 4),
-                         "dofs_per_s": nd / (t * 1e-3), "gflops": fl / (t * 1e-3) / 1e9})
-        if t > dom_t:
-            dom_t, dom = t, c
-    fam, p, form = dom
-    nl = launches_per_action(fam)
-    fl = flops_per_cell(fam, p, form) * mesh_cells
-    achieved = fl / (dom_t * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "k_action_scalar_fp64 %s p=%d %s" % dom,
-                "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
-                "note": "FP64 flops per action (all %d colour launches) / event time; peak = nominal FP64 "
-                        "(152 SMs x 4 FP64 flop/clk x 2.07 GHz, of nominal)" % nl}
+        per_case.append({"family": fam, "p": p, "form": form, "ms": round(t, 4), "dofs_per_s": nd / (t * 1e-3),
+                         "gflops_fp64_alg": flops_per_cell(fam, p, form) * ncell / (t * 1e-3) / 1e9})
+    return {"ms_step": ms_total / args.steps, "per_case": per_case, "clocks": clocks}
 
-    out = {"metric": "DoFs/s (sum-factorised action, %s)" % prec, "value": value, "unit": "DoF/s",
-           "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
-           "config": {"workload": "config-2 action sweep: mass/laplace/helmholtz on Q_p and DQ_p, p=%s, "
-                                  "%dx%dx%d perturbed hex mesh, (p+1)^3 Gauss points" % (args.degrees, *dims),
-                      "precision": prec, "families": args.families, "degrees": args.degrees,
-                      "l2": "flushed between cases (256 MiB write)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
-           "gpu_launches": sum(launches_per_action(f) for f, _, _ in wl) * args.steps,
-           "clocks": clocks, "roofline": roofline, "per_case": per_case}
 
-    if not args.no_e2e:
-        out["e2e"] = e2e(args, sfx, torch, ctx, spaces, wl, prec, stream)
-    if rank == 0 and not args.no_cpu_baseline:
-        import oracle as orc
-        X = mesh.coords()
-        v, desc, thr = cpu_sample(orc, inputs, wl, dims, X, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": v, "unit": "DoF/s", "cores": thr, "kind": "oracle", "sample": desc}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+def rel_err_case(sfx, torch, ctx, spaces, xs, case, prec):
+    """Normwise (inf) relative error of the `prec` action against the FP64 one."""
+    fam, p, form = case["family"], case["p"], case["form"]
+    sp, x = spaces[(fam, p)], xs[(fam, p)]
+    prm = HELM if form == "helmholtz" else None
+    y64, ym = torch.empty_like(x), torch.empty_like(x)
+    sfx.sfx_assemble_action(ctx, form, sp, x, y64, params=prm)
+    sfx.sfx_assemble_action(ctx, form, sp, x, ym, precision=prec, params=prm)
+    return float((ym - y64).abs().max() / y64.abs().max())
 
 
 def e2e(args, sfx, torch, ctx, spaces, wl, prec, stream):

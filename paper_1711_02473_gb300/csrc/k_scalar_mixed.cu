@@ -1,0 +1,392 @@
+// k_scalar_mixed.cu -- scalar-form actions (mass, Laplace, Helmholtz; Q_p and
+// DQ_p) with the 1D contractions on the tensor cores as split-precision
+// products, and the geometry / weight scaling / scatter in FP64.
+//
+// Same algorithm as k_scalar.cu (Sec. 3.3, Eqs. coeff_eval and form_eval with
+// the sum factorisation of Sec. 3.2).  What changes is where the arithmetic runs:
+//   - J, det J, adj J and the factor P = w S G G^T are computed in FP64, once
+//     per cell, then rounded to FP32;
+//   - every 1D contraction (B, Dq and their transposes) is one batched matrix
+//     product per CTA: the table (q x n, padded to 16 x 8k) times the fibers of
+//     all cells held by the CTA (n x (cells*n^2)), on mma.sync with FP32
+//     accumulation.  Each operand is split into a high and a low part in the
+//     input format (TF32: 11 significant bits each; BF16: 8 each) and three
+//     products hi*hi + hi*lo + lo*hi are accumulated (the lo*lo term is dropped);
+//   - the flux P grad u is formed in FP32 from the rounded factors;
+//   - b^K is widened to FP64 and added into y in FP64.
+// Error model: each stage carries the FP32 accumulator's ~2^-24 relative
+// rounding plus the split's representation error (TF32x3 ~2^-22, BF16x3 ~2^-16).
+#include <cuda_bf16.h>
+
+#include "kern_common.cuh"
+
+namespace sfx {
+
+SFX_DEFINE_TAB_UPLOAD(upload_tab_scalar_mixed)
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ uint32_t tf32_bits(float v) { return __float_as_uint(v) & 0xffffe000u; }
+
+// split v into tf32 hi + tf32 lo (both as b32 registers)
+__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_bits(v);
+  lo = tf32_bits(v - __uint_as_float(hi));
+}
+// split v into bf16 hi + bf16 lo (returned in the high 16 bits of a b32)
+__device__ __forceinline__ void split_bf16(float v, uint32_t& hi, uint32_t& lo) {
+  hi = __float_as_uint(v) & 0xffff0000u;
+  lo = __float_as_uint(v - __uint_as_float(hi)) & 0xffff0000u;
+}
+__device__ __forceinline__ uint32_t pack_bf16(uint32_t first, uint32_t second) {
+  return (first >> 16) | (second & 0xffff0000u);
+}
+
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// FP32 copy of a 1D table, zero-padded to 16 x 16, row = output index.
+struct TabF {
+  float v[16][16];
+};
+
+// Address of element (fiber f of cell c, index k along AX) in a [cells][N][N][N] array.
+template <int N, int AX>
+__device__ __forceinline__ int faddr(int c, int f, int k) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int f0 = f / N, f1 = f - (f / N) * N;
+  if (AX == 0) return c * N3 + k * N2 + f0 * N + f1;
+  if (AX == 1) return c * N3 + f0 * N2 + k * N + f1;
+  return c * N3 + f0 * N2 + f1 * N + k;
+}
+
+// out[c, .., r, ..] (+)= sum_k M[r][k] in[c, .., k, ..] along axis AX for every
+// fiber of every cell in the CTA (TRANS: M[k][r]).  One warp owns 8 fibers at a
+// time (the n dimension of the mma); in-place use is safe because a warp reads
+// all of its fibers before writing them and no other warp touches them.
+template <int N, int AX, bool TRANS, bool ACC, int PREC>
+__device__ __forceinline__ void tc_contract(const float* in, float* out, const TabF& M, int ncell) {
+  constexpr int N2 = N * N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int nfib = ncell * N2;
+  const int ntiles = (nfib + 7) >> 3;
+  auto A = [&](int r, int k) -> float { return TRANS ? M.v[k][r] : M.v[r][k]; };
+  if (PREC == SFX_PREC_TF32X3) {
+    constexpr int KS = (N + 7) / 8;
+    uint32_t ah[KS][4], al[KS][4];
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      const int k0 = ks * 8 + tq;
+      split_tf32(A(g, k0), ah[ks][0], al[ks][0]);
+      split_tf32(A(g + 8, k0), ah[ks][1], al[ks][1]);
+      split_tf32(A(g, k0 + 4), ah[ks][2], al[ks][2]);
+      split_tf32(A(g + 8, k0 + 4), ah[ks][3], al[ks][3]);
+    }
+    for (int tile = warp; tile < ntiles; tile += kWarps) {
+      const int fb = tile * 8 + g;
+      const bool vb = fb < nfib;
+      const int cb = vb ? fb / N2 : 0, lb = vb ? fb - cb * N2 : 0;
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const int k0 = ks * 8 + tq, k1 = k0 + 4;
+        const float v0 = (vb && k0 < N) ? in[faddr<N, AX>(cb, lb, k0)] : 0.f;
+        const float v1 = (vb && k1 < N) ? in[faddr<N, AX>(cb, lb, k1)] : 0.f;
+        uint32_t h0, l0, h1, l1;
+        split_tf32(v0, h0, l0);
+        split_tf32(v1, h1, l1);
+        mma_tf32(c, ah[ks], h0, h1);
+        mma_tf32(c, ah[ks], l0, l1);
+        mma_tf32(c, al[ks], h0, h1);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = g + ((e >> 1) << 3);
+        const int fc = tile * 8 + 2 * tq + (e & 1);
+        if (r < N && fc < nfib) {
+          const int cc = fc / N2, lc = fc - cc * N2;
+          const int ad = faddr<N, AX>(cc, lc, r);
+          out[ad] = ACC ? out[ad] + c[e] : c[e];
+        }
+      }
+    }
+  } else {  // BF16x3, m16n8k16: one k-step covers n <= 16
+    uint32_t ah[4], al[4];
+    {
+      uint32_t h[8], l[8];
+      const int rr[8] = {g, g, g + 8, g + 8, g, g, g + 8, g + 8};
+      const int kk[8] = {2 * tq, 2 * tq + 1, 2 * tq, 2 * tq + 1, 2 * tq + 8, 2 * tq + 9, 2 * tq + 8, 2 * tq + 9};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) split_bf16(A(rr[e], kk[e]), h[e], l[e]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ah[q] = pack_bf16(h[2 * q], h[2 * q + 1]);
+        al[q] = pack_bf16(l[2 * q], l[2 * q + 1]);
+      }
+    }
+    for (int tile = warp; tile < ntiles; tile += kWarps) {
+      const int fb = tile * 8 + g;
+      const bool vb = fb < nfib;
+      const int cb = vb ? fb / N2 : 0, lb = vb ? fb - cb * N2 : 0;
+      float v[4];
+      const int kk[4] = {2 * tq, 2 * tq + 1, 2 * tq + 8, 2 * tq + 9};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = (vb && kk[e] < N) ? in[faddr<N, AX>(cb, lb, kk[e])] : 0.f;
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split_bf16(v[e], h[e], l[e]);
+      const uint32_t bh0 = pack_bf16(h[0], h[1]), bh1 = pack_bf16(h[2], h[3]);
+      const uint32_t bl0 = pack_bf16(l[0], l[1]), bl1 = pack_bf16(l[2], l[3]);
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16(c, ah, bh0, bh1);
+      mma_bf16(c, ah, bl0, bl1);
+      mma_bf16(c, al, bh0, bh1);
+      __syncwarp();
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = g + ((e >> 1) << 3);
+        const int fc = tile * 8 + 2 * tq + (e & 1);
+        if (r < N && fc < nfib) {
+          const int cc = fc / N2, lc = fc - cc * N2;
+          const int ad = faddr<N, AX>(cc, lc, r);
+          out[ad] = ACC ? out[ad] + c[e] : c[e];
+        }
+      }
+    }
+  }
+}
+
+template <int N, int FORM>
+struct MixedShape {
+  static constexpr int N2 = N * N, N3 = N2 * N;
+  static constexpr bool LAP = FORM != SFX_MASS;
+  static constexpr bool MAS = FORM != SFX_LAPLACE;
+  // per-cell floats: U, G0..G2 (LAP), K[6] (LAP), WS (MAS)
+  static constexpr int CELLF = N3 + (LAP ? 9 * N3 : 0) + (MAS ? N3 : 0);
+  // per-cell doubles: corners (24) + Jacobian column tables (9 N^2)
+  static constexpr int CELLD = 24 + 9 * N2;
+  static constexpr int BYTES_PER_CELL = CELLF * 4 + CELLD * 8 + 4;
+};
+
+template <int N, bool DQ, int FORM, int PREC>
+__global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs a, const int64_t ncell_total,
+                                                                  const int cb) {
+  using Sh = MixedShape<N, FORM>;
+  constexpr int N2 = Sh::N2, N3 = Sh::N3;
+  constexpr bool LAP = Sh::LAP, MAS = Sh::MAS;
+  const Tab1D& T = c_tab[N - 1];
+  extern __shared__ double smd[];
+  // layout: [tables: 4 TabF][W3: N3 doubles][xq: 16 doubles][cells: doubles][cells: floats][flags]
+  TabF* tabs = reinterpret_cast<TabF*>(smd);  // 0: B, 1: Dq
+  double* W3 = smd + (2 * sizeof(TabF)) / 8;
+  double* xq = W3 + N3;
+  double* cd = xq + 16;                       // per-cell doubles
+  float* cf = reinterpret_cast<float*>(cd + (size_t)cb * Sh::CELLD);
+  float* U = cf;
+  float* G0 = U + cb * N3;
+  float* G1 = G0 + cb * N3;
+  float* G2 = G1 + cb * N3;
+  float* K = LAP ? G2 + cb * N3 : U + cb * N3;  // K[j][cell][qp]
+  float* WS = K + (LAP ? 6 * cb * N3 : 0);
+  int* flags = reinterpret_cast<int*>(WS + (MAS ? cb * N3 : 0));  // per cell: cell id or -1, bad
+
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 16 * 16; i += kThreads) {
+    const int r = i / 16, k = i % 16;
+    tabs[0].v[r][k] = (r < N && k < N) ? (float)T.Bc[r][k] : 0.f;
+    tabs[1].v[r][k] = (r < N && k < N) ? (float)T.Dq[r][k] : 0.f;
+  }
+  for (int i = tid; i < N3; i += kThreads) W3[i] = T.w[i / N2] * T.w[(i / N) % N] * T.w[i % N];
+  if (tid < N) xq[tid] = T.x[tid];
+  for (int c = tid; c < cb; c += kThreads) {
+    int cell = -1;
+    if (!slot_cell(a, (int64_t)blockIdx.x * cb + c, ncell_total, &cell)) cell = -1;
+    flags[2 * c] = cell;
+    flags[2 * c + 1] = 0;
+  }
+  __syncthreads();
+  // corners
+  for (int i = tid; i < cb * 24; i += kThreads) {
+    const int c = i / 24, v = (i % 24) / 3, k = i % 3;
+    const int cell = flags[2 * c];
+    double* X = cd + (size_t)c * Sh::CELLD;
+    X[v * 3 + k] = cell >= 0 ? a.xyz[(int64_t)a.vmap[(int64_t)cell * 8 + v] * 3 + k] : (double)((v >> (2 - k)) & 1);
+  }
+  __syncthreads();
+  for (int i = tid; i < cb * N2; i += kThreads) {
+    const int c = i / N2, t = i - c * N2;
+    double* X = cd + (size_t)c * Sh::CELLD;
+    jacobian_columns<N>(reinterpret_cast<const double(*)[3]>(X), xq, reinterpret_cast<double(*)[N2][3]>(X + 24), t);
+  }
+  __syncthreads();
+  // geometric factors in FP64, stored rounded to FP32
+  const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
+  const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
+  for (int i = tid; i < cb * N3; i += kThreads) {
+    const int c = i / N3, qp = i - c * N3;
+    const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
+    const double(*Jc)[N2][3] = reinterpret_cast<const double(*)[N2][3]>(cd + (size_t)c * Sh::CELLD + 24);
+    const double* c0 = Jc[0][q2 * N + q3];
+    const double* c1 = Jc[1][q1 * N + q3];
+    const double* c2 = Jc[2][q1 * N + q2];
+    double r0[3];
+    cross3(c1, c2, r0);
+    const double S = dot3(c0, r0);
+    if (!(S > 0.0)) flags[2 * c + 1] = 1;
+    if (LAP) {
+      double r1[3], r2[3];
+      cross3(c2, c0, r1);
+      cross3(c0, c1, r2);
+      const double ws = alpha * W3[qp] / S;
+      K[(0 * cb + c) * N3 + qp] = (float)(ws * dot3(r0, r0));
+      K[(1 * cb + c) * N3 + qp] = (float)(ws * dot3(r1, r1));
+      K[(2 * cb + c) * N3 + qp] = (float)(ws * dot3(r2, r2));
+      K[(3 * cb + c) * N3 + qp] = (float)(ws * dot3(r0, r1));
+      K[(4 * cb + c) * N3 + qp] = (float)(ws * dot3(r0, r2));
+      K[(5 * cb + c) * N3 + qp] = (float)(ws * dot3(r1, r2));
+    }
+    if (MAS) WS[c * N3 + qp] = (float)(beta * W3[qp] * S);
+  }
+  __syncthreads();
+  for (int c = tid; c < cb; c += kThreads)
+    if (flags[2 * c] >= 0 && flags[2 * c + 1]) set_flag(a.status, SFX_DEV_INVERTED);
+
+#pragma unroll 1
+  for (int r = 0; r < a.nrhs; ++r) {
+    for (int i = tid; i < cb * N3; i += kThreads) {
+      const int c = i / N3, l = i - c * N3;
+      const int cell = flags[2 * c];
+      const bool ok = cell >= 0 && !flags[2 * c + 1];
+      U[i] = ok ? (float)a.x[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r] : 0.f;
+    }
+    __syncthreads();
+    if (!DQ) {
+      tc_contract<N, 0, false, false, PREC>(U, U, tabs[0], cb);
+      __syncthreads();
+      tc_contract<N, 1, false, false, PREC>(U, U, tabs[0], cb);
+      __syncthreads();
+      tc_contract<N, 2, false, false, PREC>(U, U, tabs[0], cb);
+      __syncthreads();
+    }
+    if (LAP) {
+      tc_contract<N, 0, false, false, PREC>(U, G0, tabs[1], cb);
+      tc_contract<N, 1, false, false, PREC>(U, G1, tabs[1], cb);
+      tc_contract<N, 2, false, false, PREC>(U, G2, tabs[1], cb);
+      __syncthreads();
+    }
+    for (int i = tid; i < cb * N3; i += kThreads) {
+      const int c = i / N3, qp = i - c * N3;
+      if (LAP) {
+        const float g0 = G0[i], g1 = G1[i], g2 = G2[i];
+        const float k00 = K[(0 * cb + c) * N3 + qp], k11 = K[(1 * cb + c) * N3 + qp];
+        const float k22 = K[(2 * cb + c) * N3 + qp], k01 = K[(3 * cb + c) * N3 + qp];
+        const float k02 = K[(4 * cb + c) * N3 + qp], k12 = K[(5 * cb + c) * N3 + qp];
+        G0[i] = k00 * g0 + k01 * g1 + k02 * g2;
+        G1[i] = k01 * g0 + k11 * g1 + k12 * g2;
+        G2[i] = k02 * g0 + k12 * g1 + k22 * g2;
+      }
+      if (MAS) U[i] = WS[i] * U[i];
+    }
+    __syncthreads();
+    if (LAP) {
+      tc_contract<N, 0, true, MAS, PREC>(G0, U, tabs[1], cb);
+      __syncthreads();
+      tc_contract<N, 1, true, true, PREC>(G1, U, tabs[1], cb);
+      __syncthreads();
+      tc_contract<N, 2, true, true, PREC>(G2, U, tabs[1], cb);
+      __syncthreads();
+    }
+    if (!DQ) {
+      tc_contract<N, 0, true, false, PREC>(U, U, tabs[0], cb);
+      __syncthreads();
+      tc_contract<N, 1, true, false, PREC>(U, U, tabs[0], cb);
+      __syncthreads();
+      tc_contract<N, 2, true, false, PREC>(U, U, tabs[0], cb);
+      __syncthreads();
+    }
+    for (int i = tid; i < cb * N3; i += kThreads) {
+      const int c = i / N3, l = i - c * N3;
+      const int cell = flags[2 * c];
+      if (cell < 0) continue;
+      const int64_t slot = (int64_t)blockIdx.x * cb + c;
+      const bool ok = !flags[2 * c + 1];
+      if (a.cell_vectors) {
+        a.y[(slot * N3 + l) * a.nrhs + r] = ok ? (double)U[i] : 0.0;
+      } else if (ok) {
+        a.y[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r] += (double)U[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int N, bool DQ, int FORM, int PREC>
+int launch_mixed(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
+  using Sh = MixedShape<N, FORM>;
+  const size_t fixed = 2 * sizeof(TabF) + (Sh::N3 + 16) * 8;
+  const size_t budget = 200 * 1024;
+  int cb = (int)((budget - fixed) / Sh::BYTES_PER_CELL);
+  const int want = (N <= 3) ? 32 : 16;  // enough fibers for dense tiles
+  if (cb > want) cb = want;
+  if (cb < 1) cb = 1;
+  const size_t smem = fixed + (size_t)cb * Sh::CELLD * 8 + (size_t)cb * Sh::CELLF * 4 + (size_t)cb * 8 + 16;
+  auto kern = k_action_scalar_mixed<N, DQ, FORM, PREC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  const int64_t grid = (a.ncells + cb - 1) / cb;
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(a, ncell_total, cb);
+  return (int)cudaGetLastError();
+}
+
+template <int N, bool DQ, int PREC>
+int dispatch_form(sfx_form form, const ActArgs& a, int64_t nc, cudaStream_t s) {
+  switch (form) {
+    case SFX_MASS: return launch_mixed<N, DQ, SFX_MASS, PREC>(a, nc, s);
+    case SFX_LAPLACE: return launch_mixed<N, DQ, SFX_LAPLACE, PREC>(a, nc, s);
+    case SFX_HELMHOLTZ: return launch_mixed<N, DQ, SFX_HELMHOLTZ, PREC>(a, nc, s);
+    default: return -1;
+  }
+}
+
+template <int N>
+int dispatch(bool dq, sfx_precision prec, sfx_form form, const ActArgs& a, int64_t nc, cudaStream_t s) {
+  if (prec == SFX_PREC_TF32X3)
+    return dq ? dispatch_form<N, true, SFX_PREC_TF32X3>(form, a, nc, s) : dispatch_form<N, false, SFX_PREC_TF32X3>(form, a, nc, s);
+  return dq ? dispatch_form<N, true, SFX_PREC_BF16X3>(form, a, nc, s) : dispatch_form<N, false, SFX_PREC_BF16X3>(form, a, nc, s);
+}
+
+}  // namespace
+
+int launch_action_scalar_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
+                               void* stream) {
+  if (prec != SFX_PREC_TF32X3 && prec != SFX_PREC_BF16X3) return -1;
+  const bool dq = sp->family == SFX_DQ;
+  const int64_t nc = sp->mesh->ncell;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (sp->p) {
+    case 1: return dispatch<2>(dq, prec, form, a, nc, s);
+    case 2: return dispatch<3>(dq, prec, form, a, nc, s);
+    case 3: return dispatch<4>(dq, prec, form, a, nc, s);
+    case 4: return dispatch<5>(dq, prec, form, a, nc, s);
+    case 5: return dispatch<6>(dq, prec, form, a, nc, s);
+    case 6: return dispatch<7>(dq, prec, form, a, nc, s);
+    case 7: return dispatch<8>(dq, prec, form, a, nc, s);
+    case 8: return dispatch<9>(dq, prec, form, a, nc, s);
+  }
+  return -1;
+}
+
+}  // namespace sfx

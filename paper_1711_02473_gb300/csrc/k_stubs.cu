@@ -1,7 +1,6 @@
 // k_stubs.cu -- launchers not implemented yet report "unsupported" (-1).
 #include "kern_common.cuh"
 namespace sfx {
-int launch_action_scalar_mixed(const sfx_space*, sfx_form, sfx_precision, const ActArgs&, void*) { return -1; }
 int launch_action_scalar_naive(const sfx_space*, sfx_form, const ActArgs&, void*) { return -1; }
 int launch_action_hdivcurl(const sfx_space*, sfx_form, sfx_precision, const ActArgs&, void*) { return -1; }
 int launch_action_elastic(const sfx_space*, sfx_form, sfx_precision, const ActArgs&, void*) { return -1; }

@@ -190,6 +190,7 @@ void make_tab1d(int p, Tab1D* t) {
 // Copy the 1D tables of one degree into every kernel file's constant memory.
 static int upload_tables(const Tab1D* t) {
   int e = upload_tab_scalar(t);
+  if (!e) e = upload_tab_scalar_mixed(t);
   return e;
 }
 
