@@ -191,6 +191,8 @@ void make_tab1d(int p, Tab1D* t) {
 static int upload_tables(const Tab1D* t) {
   int e = upload_tab_scalar(t);
   if (!e) e = upload_tab_scalar_mixed(t);
+  if (!e) e = upload_tab_hdivcurl(t);
+  if (!e) e = upload_tab_elastic(t);
   return e;
 }
 

@@ -107,5 +107,7 @@ int launch_cell_matrices(const sfx_space* sp, sfx_form form, sfx_algo algo, cons
 // Each kernel file keeps its own constant-memory copy of the 1D tables.
 int upload_tab_scalar(const Tab1D* t);
 int upload_tab_scalar_mixed(const Tab1D* t);
+int upload_tab_hdivcurl(const Tab1D* t);
+int upload_tab_elastic(const Tab1D* t);
 
 }  // namespace sfx
