@@ -193,6 +193,8 @@ static int upload_tables(const Tab1D* t) {
   if (!e) e = upload_tab_scalar_mixed(t);
   if (!e) e = upload_tab_hdivcurl(t);
   if (!e) e = upload_tab_elastic(t);
+  if (!e) e = upload_tab_matrix(t);
+  if (!e) e = upload_tab_naive(t);
   return e;
 }
 

@@ -93,6 +93,9 @@ int launch_action_hdivcurl(const sfx_space* sp, sfx_form form, sfx_precision pre
                            void* stream);
 int launch_action_elastic(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
                           void* stream);
+int launch_action_scalar_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
+                               void* stream);
+int launch_action_scalar_naive(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
 
 struct MatArgs {
   const int32_t* vmap;
@@ -109,5 +112,7 @@ int upload_tab_scalar(const Tab1D* t);
 int upload_tab_scalar_mixed(const Tab1D* t);
 int upload_tab_hdivcurl(const Tab1D* t);
 int upload_tab_elastic(const Tab1D* t);
+int upload_tab_matrix(const Tab1D* t);
+int upload_tab_naive(const Tab1D* t);
 
 }  // namespace sfx
