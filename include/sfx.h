@@ -196,6 +196,39 @@ sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_for
                                       const sfx_space* space, int64_t cell_begin, int64_t cell_end,
                                       double* A, sfx_precision prec, sfx_algo algo, void* stream);
 
+/* ------------------------------------------------------ batched execution */
+
+/* A plan for repeated actions on a p-adaptive DQ mesh: cell c carries
+ * DQ_{p_c} (1 <= p_c <= 8, Gauss nodes, cell-major numbering: cell c owns the
+ * (p_c+1)^3 dofs starting at offset(c) = sum_{c' < c} (p_c'+1)^3), with up to 4
+ * scalar forms (MASS / LAPLACE / HELMHOLTZ) applied to the same nrhs
+ * right-hand sides.  Cells of different degree share no dofs, so the cells
+ * are independent (no conforming hp constraints).
+ *   degree   host, ncell int32 (copied);  forms/params host, nforms each
+ *            (params may be NULL for the defaults).
+ * The plan owns its tile list (cells sorted by degree, cut into one-CTA tiles,
+ * largest degree first), a 4-byte tile counter and a private capture stream.
+ * Errors: SFX_ERR_ARG, SFX_ERR_UNSUPPORTED (form), SFX_ERR_RANGE, SFX_ERR_ALLOC,
+ * SFX_ERR_CUDA. */
+typedef struct sfx_plan sfx_plan;
+sfx_status sfx_plan_create_padaptive(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree, int nforms,
+                                     const sfx_form* forms, const sfx_form_params* params, int nrhs,
+                                     sfx_plan** out);
+/* Total dofs, number of tiles and a host view of the ncell+1 dof offsets. */
+sfx_status sfx_plan_info(const sfx_plan* plan, int64_t* ndof, int64_t* ntiles, const int64_t** cell_offset);
+
+/* GRAPH: every tile of every form and all right-hand sides in ONE persistent
+ * kernel launch (CTAs take tiles from the counter), captured once into a CUDA
+ * graph per (x, y) pointer set and replayed.  PER_LAUNCH: one launch per
+ * (form, degree, right-hand side), for comparison.
+ *   x   device, ndof x nrhs;  y  host array of nforms device pointers, each
+ *       ndof x nrhs (overwritten).
+ * Launches of one plan must not overlap on the device (they share the tile
+ * counter).  Errors: SFX_ERR_ARG, SFX_ERR_CUDA. */
+typedef enum { SFX_EXEC_GRAPH = 0, SFX_EXEC_PER_LAUNCH = 1 } sfx_exec_mode;
+sfx_status sfx_plan_execute(sfx_plan* plan, const double* x, double* const* y, sfx_exec_mode mode, void* stream);
+void sfx_plan_destroy(sfx_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,9 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported combination", -3: "C
 EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_string",
            "sfx_mesh_create_box", "sfx_mesh_create_structured", "sfx_mesh_info", "sfx_mesh_destroy",
            "sfx_space_create", "sfx_space_info", "sfx_space_destroy", "sfx_tabulate_1d",
-           "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices"]
+           "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices",
+           "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy"]
+EXEC = {"graph": 0, "per_launch": 1}
 
 
 class SfxError(RuntimeError):
@@ -78,6 +80,11 @@ def lib():
         L.sfx_assemble_action.argtypes = [P, i, C.POINTER(_Params), P, P, P, i, i, i, i, P]
         L.sfx_assemble_cell_vectors.argtypes = [P, i, C.POINTER(_Params), P, P, i, P, i64, P, i, P]
         L.sfx_assemble_cell_matrices.argtypes = [P, i, C.POINTER(_Params), P, i64, i64, P, i, i, P]
+        L.sfx_plan_create_padaptive.argtypes = [P, P, P, i, P, P, i, C.POINTER(P)]
+        L.sfx_plan_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(P)]
+        L.sfx_plan_execute.argtypes = [P, P, P, i, P]
+        L.sfx_plan_destroy.argtypes = [P]
+        L.sfx_plan_destroy.restype = None
         for name in EXPORTS:
             f = getattr(L, name)
             if f.restype is C.c_int:
@@ -240,3 +247,47 @@ def sfx_assemble_cell_matrices(ctx, form, space, cell_begin, cell_end, A, precis
                                             _dptr(A, "float64"), PRECISION[precision], ALGO[algo],
                                             _stream(stream)), "sfx_assemble_cell_matrices")
     return A
+
+
+class Plan:
+    """Batched actions on a p-adaptive DQ mesh (sfx_plan_*): one persistent,
+    graph-captured launch for all forms and right-hand sides."""
+
+    def __init__(self, ctx, mesh, degree, forms, nrhs=1, params=None):
+        degree = np.ascontiguousarray(degree, dtype=np.int32)
+        self.ctx, self.mesh, self.forms, self.nrhs = ctx, mesh, list(forms), nrhs
+        fa = (C.c_int * len(forms))(*[FORM[f] for f in forms])
+        pa = None
+        if params is not None:
+            arr = (_Params * len(forms))(*[_Params(*(tuple(p) + (0.0,) * (4 - len(p)))) for p in params])
+            pa = C.cast(arr, C.c_void_p)
+        self.h = C.c_void_p()
+        _check(lib().sfx_plan_create_padaptive(ctx.h, mesh.h, degree.ctypes.data_as(C.c_void_p), len(forms),
+                                               C.cast(fa, C.c_void_p), pa, nrhs, C.byref(self.h)),
+               "sfx_plan_create_padaptive")
+        nd, nt, off = C.c_int64(), C.c_int64(), C.c_void_p()
+        _check(lib().sfx_plan_info(self.h, C.byref(nd), C.byref(nt), C.byref(off)), "sfx_plan_info")
+        self.ndof, self.ntiles = nd.value, nt.value
+        self.cell_offset = np.ctypeslib.as_array(C.cast(off, C.POINTER(C.c_int64)), shape=(len(degree) + 1,)).copy()
+
+    def execute(self, x, ys, mode="graph", stream=None):
+        if len(ys) != len(self.forms):
+            raise ValueError("one output per form")
+        for t in [x] + list(ys):
+            if t.numel() != self.ndof * self.nrhs:
+                raise ValueError("vectors must hold ndof * nrhs doubles")
+        yp = (C.c_void_p * len(ys))(*[_dptr(y, "float64").value for y in ys])
+        _check(lib().sfx_plan_execute(self.h, _dptr(x, "float64"), C.cast(yp, C.c_void_p), EXEC[mode],
+                                      _stream(stream)), "sfx_plan_execute")
+        return ys
+
+    def close(self):
+        if self.h:
+            lib().sfx_plan_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

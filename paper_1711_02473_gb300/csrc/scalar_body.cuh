@@ -1,0 +1,186 @@
+// scalar_body.cuh -- device body of the FP64 scalar-form action (mass,
+// Laplace, Helmholtz on Q_p / DQ_p), shared by the per-colour kernels
+// (k_scalar.cu) and the persistent batched kernel (k_batched.cu).
+//
+// Per cell (Sec. 3.3, Eqs. coeff_def / coeff_eval / form_eval):
+//   1. gather U^K through the cell-node map;
+//   2. interpolate to the (p+1)^3 Gauss points with three 1D contractions by
+//      the GLL->Gauss table B (x, then y, then z; Sec. 3.2 sum factorisation;
+//      for DQ_p the nodes are the Gauss points and B = I, Sec. 2.5 Eq. colocated);
+//   3. reference gradient at the points: one 1D contraction per axis with the
+//      collocation derivative Dq on the Gauss points (exact: Q_p restricted to
+//      a line is a degree-p polynomial, fixed by its p+1 Gauss values);
+//   4. pointwise: geometry from the trilinear coordinate field (J, S = det J,
+//      adj J) and the geometric factor P = w S G G^T (the P^(k,l) of Sec. 3.2);
+//      flux f = P grad u (Laplace) and/or w S u (mass);
+//   5. transposed contractions Dq^T then B^T;
+//   6. add b^K into y through the map (conflict-free within one colour).
+// Geometry is computed once per cell and reused for all right-hand sides.
+#pragma once
+#include "kern_common.cuh"
+
+namespace sfx {
+namespace {
+
+template <int N, int FORM>
+struct ScalarShape {
+  static constexpr int N2 = N * N, N3 = N * N * N;
+  static constexpr bool LAP = FORM != SFX_MASS;
+  static constexpr bool MAS = FORM != SFX_LAPLACE;
+  // per-team shared doubles: U, G0..G2 (LAP), K[6] (LAP), WS (MAS), corners, Jc
+  static constexpr int TEAM = N3 + (LAP ? 3 * N3 + 6 * N3 : 0) + (MAS ? N3 : 0) + 24 + 9 * N2 + 1;
+  static constexpr int MAXCB = (256 / N2) > 0 ? 256 / N2 : 1;
+};
+
+// One tile: the cb cells of slots slot0 .. slot0+cb-1, one team of N^2 threads
+// per cell (threads of teams >= cb idle but take part in the barriers).
+template <int N, bool DQ, int FORM>
+__device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t ncell_total, const int64_t slot0,
+                                                 const int cb, double* sm) {
+  using Sh = ScalarShape<N, FORM>;
+  constexpr int N2 = Sh::N2, N3 = Sh::N3;
+  constexpr bool LAP = Sh::LAP, MAS = Sh::MAS;
+  const Tab1D& T = c_tab[N - 1];
+  // Threads beyond the cb teams (the persistent kernel runs 256 threads for
+  // every degree) only take part in the barriers: they alias team 0's shared
+  // memory for pointer arithmetic but never read or write it.
+  const int team_raw = threadIdx.x / N2;
+  const bool member = team_raw < cb;
+  const int team = member ? team_raw : 0;
+  const int t = threadIdx.x - team_raw * N2;
+  double* W3 = sm;              // 3D quadrature weights
+  double* xq = sm + N3;         // 1D points (padded to 16)
+  double* base = sm + N3 + 16 + team * Sh::TEAM;
+  double* U = base;
+  double* G0 = U + N3;
+  double* G1 = G0 + N3;
+  double* G2 = G1 + N3;
+  double* K = LAP ? G2 + N3 : U + N3;  // K[c][qp], c = 00,11,22,01,02,12
+  double* WS = K + (LAP ? 6 * N3 : 0);
+  double(*X)[3] = reinterpret_cast<double(*)[3]>(WS + (MAS ? N3 : 0));
+  double(*Jc)[N2][3] = reinterpret_cast<double(*)[N2][3]>(&X[8][0]);
+  int* bad = reinterpret_cast<int*>(&Jc[3][0][0]);
+
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) W3[i] = T.w[i / N2] * T.w[(i / N) % N] * T.w[i % N];
+  if (threadIdx.x < N) xq[threadIdx.x] = T.x[threadIdx.x];
+
+  int cell = 0;
+  const int64_t slot = slot0 + team;
+  const bool active = member && slot_cell(a, slot, ncell_total, &cell);
+  if (member && t == 0) *bad = 0;
+  for (int c = member ? t : 8; c < 8; c += N2) {  // a team may have fewer than 8 threads (p = 1)
+    if (active) {
+      const int v = a.vmap[(int64_t)cell * 8 + c];
+      X[c][0] = a.xyz[(int64_t)v * 3 + 0];
+      X[c][1] = a.xyz[(int64_t)v * 3 + 1];
+      X[c][2] = a.xyz[(int64_t)v * 3 + 2];
+    } else {  // idle team: unit cube keeps the arithmetic finite
+      X[c][0] = (c >> 2) & 1; X[c][1] = (c >> 1) & 1; X[c][2] = c & 1;
+    }
+  }
+  __syncthreads();
+  if (member) jacobian_columns<N>(X, xq, Jc, t);
+  __syncthreads();
+
+  // geometric factors at the thread's points qp = k*N2 + t, k = q1
+  const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
+  const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
+#pragma unroll 1
+  for (int k = 0; k < (member ? N : 0); ++k) {
+    const int qp = k * N2 + t;
+    const int q2 = t / N, q3 = t - (t / N) * N;
+    const double* c0 = Jc[0][t];
+    const double* c1 = Jc[1][k * N + q3];
+    const double* c2 = Jc[2][k * N + q2];
+    double r0[3];
+    cross3(c1, c2, r0);
+    const double S = dot3(c0, r0);
+    if (!(S > 0.0)) *bad = 1;
+    if (LAP) {
+      double r1[3], r2[3];
+      cross3(c2, c0, r1);
+      cross3(c0, c1, r2);
+      const double ws = alpha * W3[qp] / S;  // P = w S G G^T = (w/S) adj(J) adj(J)^T
+      K[0 * N3 + qp] = ws * dot3(r0, r0);
+      K[1 * N3 + qp] = ws * dot3(r1, r1);
+      K[2 * N3 + qp] = ws * dot3(r2, r2);
+      K[3 * N3 + qp] = ws * dot3(r0, r1);
+      K[4 * N3 + qp] = ws * dot3(r0, r2);
+      K[5 * N3 + qp] = ws * dot3(r1, r2);
+    }
+    if (MAS) WS[qp] = beta * W3[qp] * S;
+  }
+  __syncthreads();
+  const bool ok = active && !*bad;
+  if (active && *bad && t == 0) set_flag(a.status, SFX_DEV_INVERTED);
+  const int tl = member ? t : N3;  // first index of this thread's strided loops (none for non-members)
+
+  // dof of local l: the space's map, or cell offset + l for p-adaptive DQ
+  const int32_t* mrow = a.map ? a.map + (int64_t)cell * N3 : nullptr;
+  const int64_t doff = a.dq_off ? a.dq_off[cell] : 0;
+  auto dof = [&](int l) -> int64_t { return mrow ? (int64_t)mrow[l] : doff + l; };
+#pragma unroll 1
+  for (int r = a.r0; r < a.r1; ++r) {
+    for (int l = tl; l < N3; l += N2) U[l] = ok ? a.x[dof(l) * a.nrhs + r] : 0.0;
+    __syncthreads();
+    if (!DQ) {
+      if (member) contract<N, N, N, 0, N, false, false, kMaxN>(U, U, T.Bc, t);
+      __syncthreads();
+      if (member) contract<N, N, N, 1, N, false, false, kMaxN>(U, U, T.Bc, t);
+      __syncthreads();
+      if (member) contract<N, N, N, 2, N, false, false, kMaxN>(U, U, T.Bc, t);
+      __syncthreads();
+    }
+    if (LAP) {
+      if (member) {
+        contract<N, N, N, 0, N, false, false, kMaxQ>(U, G0, T.Dq, t);
+        contract<N, N, N, 1, N, false, false, kMaxQ>(U, G1, T.Dq, t);
+        contract<N, N, N, 2, N, false, false, kMaxQ>(U, G2, T.Dq, t);
+      }
+      __syncthreads();
+    }
+#pragma unroll 1
+    for (int k = 0; k < (member ? N : 0); ++k) {
+      const int qp = k * N2 + t;
+      if (LAP) {
+        const double g0 = G0[qp], g1 = G1[qp], g2 = G2[qp];
+        const double k00 = K[qp], k11 = K[N3 + qp], k22 = K[2 * N3 + qp];
+        const double k01 = K[3 * N3 + qp], k02 = K[4 * N3 + qp], k12 = K[5 * N3 + qp];
+        G0[qp] = k00 * g0 + k01 * g1 + k02 * g2;
+        G1[qp] = k01 * g0 + k11 * g1 + k12 * g2;
+        G2[qp] = k02 * g0 + k12 * g1 + k22 * g2;
+      }
+      if (MAS) U[qp] = WS[qp] * U[qp];
+    }
+    __syncthreads();
+    if (LAP) {
+      if (member) contract<N, N, N, 0, N, true, MAS, kMaxQ>(G0, U, T.Dq, t);
+      __syncthreads();
+      if (member) contract<N, N, N, 1, N, true, true, kMaxQ>(G1, U, T.Dq, t);
+      __syncthreads();
+      if (member) contract<N, N, N, 2, N, true, true, kMaxQ>(G2, U, T.Dq, t);
+      __syncthreads();
+    }
+    if (!DQ) {
+      if (member) contract<N, N, N, 0, N, true, false, kMaxN>(U, U, T.Bc, t);
+      __syncthreads();
+      if (member) contract<N, N, N, 1, N, true, false, kMaxN>(U, U, T.Bc, t);
+      __syncthreads();
+      if (member) contract<N, N, N, 2, N, true, false, kMaxN>(U, U, T.Bc, t);
+      __syncthreads();
+    }
+    if (ok) {  // ok implies member
+      if (a.cell_vectors) {
+        for (int l = t; l < N3; l += N2) a.y[(slot * N3 + l) * a.nrhs + r] = U[l];
+      } else {
+        for (int l = t; l < N3; l += N2) a.y[dof(l) * a.nrhs + r] += U[l];
+      }
+    } else if (active && a.cell_vectors) {
+      for (int l = t; l < N3; l += N2) a.y[(slot * N3 + l) * a.nrhs + r] = 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+}  // namespace sfx

@@ -2,6 +2,7 @@
 // colouring), 1D tabulation, argument validation and kernel dispatch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -195,6 +196,7 @@ static int upload_tables(const Tab1D* t) {
   if (!e) e = upload_tab_elastic(t);
   if (!e) e = upload_tab_matrix(t);
   if (!e) e = upload_tab_naive(t);
+  if (!e) e = upload_tab_batched(t);
   return e;
 }
 
@@ -522,6 +524,8 @@ extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx
   a.x = x;
   a.y = y;
   a.nrhs = nrhs;
+  a.r0 = 0;
+  a.r1 = nrhs;
   a.cell_vectors = 0;
   a.alpha = pr.alpha; a.beta = pr.beta; a.mu = pr.mu; a.lambda = pr.lambda;
   a.status = ctx->d_status;
@@ -561,6 +565,8 @@ extern "C" sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, con
   a.x = x;
   a.y = b;
   a.nrhs = nrhs;
+  a.r0 = 0;
+  a.r1 = nrhs;
   a.cell_vectors = 1;
   a.alpha = pr.alpha; a.beta = pr.beta; a.mu = pr.mu; a.lambda = pr.lambda;
   a.status = ctx->d_status;
@@ -594,4 +600,194 @@ extern "C" sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, co
   int e = launch_cell_matrices(sp, form, algo, a, stream);
   if (e == -1) return SFX_ERR_UNSUPPORTED;
   return e ? SFX_ERR_CUDA : SFX_OK;
+}
+
+// -------------------------------------------------------------------- plans
+struct sfx_plan {
+  sfx_ctx* ctx = nullptr;
+  const sfx_mesh* mesh = nullptr;
+  int nforms = 0, nrhs = 1;
+  sfx_form forms[4];
+  sfx_form_params params[4];
+  int64_t ndof = 0;
+  std::vector<int64_t> off;          // host dof offset of every cell (ncell + 1)
+  int64_t* d_off = nullptr;
+  int32_t* d_sorted = nullptr;       // cells sorted by degree
+  int64_t deg_begin[kMaxDeg + 2] = {0}, deg_end[kMaxDeg + 2] = {0};
+  std::vector<BatchTile> tiles;
+  BatchTile* d_tiles = nullptr;
+  int* d_counter = nullptr;
+  int cb[kMaxDeg + 1] = {0};
+  size_t smem = 0;
+  int grid = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const double* gx = nullptr;
+  double* gy[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+extern "C" void sfx_plan_destroy(sfx_plan* pl) {
+  if (!pl) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->cap) cudaStreamDestroy(pl->cap);
+  if (pl->d_off) cudaFree(pl->d_off);
+  if (pl->d_sorted) cudaFree(pl->d_sorted);
+  if (pl->d_tiles) cudaFree(pl->d_tiles);
+  if (pl->d_counter) cudaFree(pl->d_counter);
+  delete pl;
+}
+
+extern "C" sfx_status sfx_plan_create_padaptive(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree,
+                                                int nforms, const sfx_form* forms, const sfx_form_params* params,
+                                                int nrhs, sfx_plan** out) {
+  if (!ctx || !mesh || !degree || !forms || !out || nforms < 1 || nforms > 4 || nrhs < 1 || nrhs > 64)
+    return SFX_ERR_ARG;
+  if (ctx->device < 0 || mesh->ctx != ctx || !mesh->d_vmap) return SFX_ERR_ARG;
+  *out = nullptr;
+  for (int f = 0; f < nforms; ++f)
+    if (forms[f] != SFX_MASS && forms[f] != SFX_LAPLACE && forms[f] != SFX_HELMHOLTZ) return SFX_ERR_UNSUPPORTED;
+  const int64_t ncell = mesh->ncell;
+  for (int64_t c = 0; c < ncell; ++c)
+    if (degree[c] < 1 || degree[c] > kMaxDeg) return SFX_ERR_ARG;
+  sfx_plan* pl = new (std::nothrow) sfx_plan;
+  if (!pl) return SFX_ERR_ALLOC;
+  pl->ctx = ctx;
+  pl->mesh = mesh;
+  pl->nforms = nforms;
+  pl->nrhs = nrhs;
+  for (int f = 0; f < nforms; ++f) {
+    pl->forms[f] = forms[f];
+    pl->params[f] = params ? params[f] : default_params(forms[f]);
+  }
+  // dof offsets (cell-major DQ numbering: cell c owns (p_c+1)^3 consecutive dofs)
+  pl->off.resize((size_t)ncell + 1);
+  pl->off[0] = 0;
+  for (int64_t c = 0; c < ncell; ++c) {
+    const int64_t n = degree[c] + 1;
+    pl->off[c + 1] = pl->off[c] + n * n * n;
+  }
+  pl->ndof = pl->off[ncell];
+  if (pl->ndof * nrhs >= (1LL << 40)) { sfx_plan_destroy(pl); return SFX_ERR_RANGE; }
+  // cells sorted by degree (stable), per-degree ranges
+  std::vector<int32_t> sorted;
+  sorted.reserve((size_t)ncell);
+  for (int p = 1; p <= kMaxDeg; ++p) {
+    pl->deg_begin[p] = (int64_t)sorted.size();
+    for (int64_t c = 0; c < ncell; ++c)
+      if (degree[c] == p) sorted.push_back((int32_t)c);
+    pl->deg_end[p] = (int64_t)sorted.size();
+  }
+  sfx_status st = SFX_OK;
+  if (batched_config(pl->cb, &pl->smem, &pl->grid) != 0) st = SFX_ERR_CUDA;
+  // tiles: largest degree first, then form, then cells
+  for (int p = kMaxDeg; p >= 1 && !st; --p)
+    for (int f = 0; f < nforms; ++f)
+      for (int64_t c0 = pl->deg_begin[p]; c0 < pl->deg_end[p]; c0 += pl->cb[p]) {
+        BatchTile t;
+        t.p = p;
+        t.form = f;
+        t.first = (int32_t)c0;
+        t.count = (int32_t)std::min<int64_t>(pl->cb[p], pl->deg_end[p] - c0);
+        pl->tiles.push_back(t);
+      }
+  if (!st) st = to_device(pl->off.data(), pl->off.size(), &pl->d_off);
+  if (!st) st = to_device(sorted.data(), sorted.size(), &pl->d_sorted);
+  if (!st && !pl->tiles.empty()) st = to_device(pl->tiles.data(), pl->tiles.size(), &pl->d_tiles);
+  if (!st && cudaMalloc(&pl->d_counter, sizeof(int)) != cudaSuccess) st = SFX_ERR_ALLOC;
+  if (!st && cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking) != cudaSuccess) st = SFX_ERR_CUDA;
+  if (!st) {
+    for (int p = 1; p <= kMaxDeg && !st; ++p) {  // constant tables for every degree
+      Tab1D t;
+      make_tab1d(p, &t);
+      if (upload_tables(&t) != 0) st = SFX_ERR_CUDA;
+    }
+  }
+  if (st) { sfx_plan_destroy(pl); return st; }
+  *out = pl;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_plan_info(const sfx_plan* pl, int64_t* ndof, int64_t* ntiles, const int64_t** cell_offset) {
+  if (!pl) return SFX_ERR_ARG;
+  if (ndof) *ndof = pl->ndof;
+  if (ntiles) *ntiles = (int64_t)pl->tiles.size();
+  if (cell_offset) *cell_offset = pl->off.data();
+  return SFX_OK;
+}
+
+static ActArgs plan_args(const sfx_plan* pl, const double* x) {
+  ActArgs a{};
+  a.map = nullptr;
+  a.dq_off = pl->d_off;
+  a.vmap = pl->mesh->d_vmap;
+  a.xyz = pl->mesh->d_xyz;
+  a.x = x;
+  a.nrhs = pl->nrhs;
+  a.r0 = 0;
+  a.r1 = pl->nrhs;
+  a.status = pl->ctx->d_status;
+  return a;
+}
+
+extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* const* y, sfx_exec_mode mode,
+                                       void* stream) {
+  if (!pl || !x || !y) return SFX_ERR_ARG;
+  for (int f = 0; f < pl->nforms; ++f)
+    if (!y[f] || y[f] == x) return SFX_ERR_ARG;
+  const size_t ybytes = (size_t)pl->ndof * pl->nrhs * sizeof(double);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (mode == SFX_EXEC_PER_LAUNCH) {
+    for (int f = 0; f < pl->nforms; ++f) {
+      if (cudaMemsetAsync(y[f], 0, ybytes, s) != cudaSuccess) return SFX_ERR_CUDA;
+      for (int p = 1; p <= kMaxDeg; ++p) {
+        const int64_t cnt = pl->deg_end[p] - pl->deg_begin[p];
+        if (cnt == 0) continue;
+        for (int r = 0; r < pl->nrhs; ++r) {
+          ActArgs a = plan_args(pl, x);
+          a.cells = pl->d_sorted + pl->deg_begin[p];
+          a.ncells = cnt;
+          a.y = y[f];
+          a.r0 = r;
+          a.r1 = r + 1;
+          a.alpha = pl->params[f].alpha;
+          a.beta = pl->params[f].beta;
+          if (launch_scalar_fp64_degree(p, true, pl->forms[f], a, pl->mesh->ncell, stream) != 0) return SFX_ERR_CUDA;
+        }
+      }
+    }
+    return SFX_OK;
+  }
+  if (mode != SFX_EXEC_GRAPH) return SFX_ERR_ARG;
+  bool same = pl->exec && pl->gx == x;
+  for (int f = 0; f < pl->nforms && same; ++f) same = pl->gy[f] == y[f];
+  if (!same) {
+    if (pl->exec) { cudaGraphExecDestroy(pl->exec); pl->exec = nullptr; }
+    BatchArgs b{};
+    b.base = plan_args(pl, x);
+    b.sorted_cells = pl->d_sorted;
+    b.tiles = pl->d_tiles;
+    b.ntiles = (int)pl->tiles.size();
+    b.counter = pl->d_counter;
+    b.ncell_total = pl->mesh->ncell;
+    for (int f = 0; f < pl->nforms; ++f) {
+      b.y[f] = y[f];
+      b.alpha[f] = pl->params[f].alpha;
+      b.beta[f] = pl->params[f].beta;
+      b.form_id[f] = pl->forms[f];
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SFX_ERR_CUDA;
+    int e = 0;
+    for (int f = 0; f < pl->nforms && !e; ++f) e = (int)cudaMemsetAsync(y[f], 0, ybytes, pl->cap);
+    if (!e) e = (int)cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
+    if (!e && b.ntiles > 0) e = batched_launch(b, pl->grid, pl->smem, pl->cap);
+    cudaError_t ee = cudaStreamEndCapture(pl->cap, &g);
+    if (e || ee != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); return SFX_ERR_CUDA; }
+    ee = cudaGraphInstantiate(&pl->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ee != cudaSuccess) { pl->exec = nullptr; return SFX_ERR_CUDA; }
+    pl->gx = x;
+    for (int f = 0; f < pl->nforms; ++f) pl->gy[f] = y[f];
+  }
+  return cudaGraphLaunch(pl->exec, s) == cudaSuccess ? SFX_OK : SFX_ERR_CUDA;
 }

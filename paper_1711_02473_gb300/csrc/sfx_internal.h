@@ -81,6 +81,8 @@ struct ActArgs {
   const double* x;        // ndof x nrhs
   double* y;              // ndof x nrhs (scatter) or ncells x nloc x nrhs (cell vectors)
   int nrhs;
+  int r0, r1;             // right-hand sides handled by this launch: [r0, r1)
+  const int64_t* dq_off;  // p-adaptive DQ: dof of (cell, l) = dq_off[cell] + l (map unused)
   int cell_vectors;       // 1: write b^K per slot instead of scattering
   double alpha, beta, mu, lambda;
   uint32_t* status;
@@ -107,6 +109,28 @@ struct MatArgs {
 };
 int launch_cell_matrices(const sfx_space* sp, sfx_form form, sfx_algo algo, const MatArgs& a, void* stream);
 
+// FP64 scalar action over an explicit cell list for one degree (DQ, p-adaptive
+// plans); also used by the per-launch comparison mode.
+int launch_scalar_fp64_degree(int p, bool dq, sfx_form form, const ActArgs& a, int64_t ncell_total, void* stream);
+
+// Persistent batched launch over a tile list (k_batched.cu).
+struct BatchTile {
+  int32_t p, form, first, count;  // degree, form slot, range in the degree-sorted cell list
+};
+struct BatchArgs {
+  ActArgs base;                   // x, vmap, xyz, nrhs, dq_off, status (cells/y/ncells per tile)
+  const int32_t* sorted_cells;
+  const BatchTile* tiles;
+  int ntiles;
+  int* counter;                   // tile counter, zeroed before each launch
+  double* y[4];
+  double alpha[4], beta[4];
+  int form_id[4];
+  int64_t ncell_total;
+};
+int batched_config(int* cb_per_degree /*[kMaxDeg+1]*/, size_t* smem, int* grid);
+int batched_launch(const BatchArgs& b, int grid, size_t smem, void* stream);
+
 // Each kernel file keeps its own constant-memory copy of the 1D tables.
 int upload_tab_scalar(const Tab1D* t);
 int upload_tab_scalar_mixed(const Tab1D* t);
@@ -114,5 +138,6 @@ int upload_tab_hdivcurl(const Tab1D* t);
 int upload_tab_elastic(const Tab1D* t);
 int upload_tab_matrix(const Tab1D* t);
 int upload_tab_naive(const Tab1D* t);
+int upload_tab_batched(const Tab1D* t);
 
 }  // namespace sfx
