@@ -229,6 +229,33 @@ typedef enum { SFX_EXEC_GRAPH = 0, SFX_EXEC_PER_LAUNCH = 1 } sfx_exec_mode;
 sfx_status sfx_plan_execute(sfx_plan* plan, const double* x, double* const* y, sfx_exec_mode mode, void* stream);
 void sfx_plan_destroy(sfx_plan* plan);
 
+/* ------------------------------------------------- action without allocation */
+
+/* The p-adaptive DQ action of one scalar form for callers that cannot
+ * allocate device memory when they need it (a memory pool owns the device,
+ * allocation is allowed only at start-up, or a solve phase forbids it).  It
+ * does what sfx_plan_execute(GRAPH) does for one form, but builds the
+ * degree-sorted cell list and tile list on the device, in a fixed scratch
+ * array inside the library, and calls no cudaMalloc, cudaFree or allocating
+ * routine.  The paper has no counterpart: this is an interface for callers.
+ *   degree       device, ncell int32, each in 1..8 (others are skipped and
+ *                flagged SFX_DEV_BADCELL)
+ *   cell_offset  device, ncell+1 int64: cell c owns dofs [off[c], off[c+1]),
+ *                off[c+1] - off[c] = (degree[c]+1)^3
+ *   x, y         device, ndof x nrhs (y overwritten); 1 <= nrhs <= 64
+ * Limit: ncell <= 262144 (SFX_ERR_RANGE beyond).  The scratch (about 5 MB) is
+ * a static device array that every GPU loading the library holds until exit;
+ * it keeps the last call's contents, and the call clears what must start at
+ * zero.  All calls share it, so calls that overlap on the GPU (different
+ * streams, or threads) race: serialise them.  The first call on a device, with
+ * that device current, looks up the scratch address and uploads the 1D
+ * tables; make that first call before any stream capture.
+ * Errors: SFX_ERR_ARG (also: ctx's device not current on the first call),
+ * SFX_ERR_UNSUPPORTED (form), SFX_ERR_RANGE, SFX_ERR_CUDA. */
+sfx_status sfx_padaptive_action_noalloc(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree,
+                                        const int64_t* cell_offset, sfx_form form, const sfx_form_params* params,
+                                        const double* x, double* y, int nrhs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

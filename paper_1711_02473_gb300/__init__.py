@@ -31,7 +31,8 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_mesh_create_box", "sfx_mesh_create_structured", "sfx_mesh_info", "sfx_mesh_destroy",
            "sfx_space_create", "sfx_space_info", "sfx_space_destroy", "sfx_tabulate_1d",
            "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices",
-           "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy"]
+           "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy",
+           "sfx_padaptive_action_noalloc"]
 EXEC = {"graph": 0, "per_launch": 1}
 
 
@@ -85,6 +86,7 @@ def lib():
         L.sfx_plan_execute.argtypes = [P, P, P, i, P]
         L.sfx_plan_destroy.argtypes = [P]
         L.sfx_plan_destroy.restype = None
+        L.sfx_padaptive_action_noalloc.argtypes = [P, P, P, P, i, C.POINTER(_Params), P, P, i, P]
         for name in EXPORTS:
             f = getattr(L, name)
             if f.restype is C.c_int:
@@ -247,6 +249,17 @@ def sfx_assemble_cell_matrices(ctx, form, space, cell_begin, cell_end, A, precis
                                             _dptr(A, "float64"), PRECISION[precision], ALGO[algo],
                                             _stream(stream)), "sfx_assemble_cell_matrices")
     return A
+
+
+def sfx_padaptive_action_noalloc(ctx, mesh, degree, cell_offset, form, x, y, nrhs=1, params=None, stream=None):
+    """p-adaptive DQ action that allocates nothing (see include/sfx.h): for
+    callers that cannot allocate device memory at the point of the call.
+    degree: int32 CUDA tensor (ncell); cell_offset: int64 CUDA tensor (ncell+1)."""
+    _check(lib().sfx_padaptive_action_noalloc(ctx.h, mesh.h, _dptr(degree, "int32"), _dptr(cell_offset, "int64"),
+                                              FORM[form], _params(params), _dptr(x, "float64"),
+                                              _dptr(y, "float64"), nrhs, _stream(stream)),
+           "sfx_padaptive_action_noalloc")
+    return y
 
 
 class Plan:

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kBT) k_batched_dq_fp64(const BatchArgs b) {
     __syncthreads();
     const int tix = s_tile;
     __syncthreads();
-    if (tix >= b.ntiles) break;
+    if (tix >= (b.ntiles_dev ? *b.ntiles_dev : b.ntiles)) break;
     const BatchTile tl = b.tiles[tix];
     ActArgs a = b.base;
     a.cells = b.sorted_cells + tl.first;
@@ -97,6 +97,13 @@ int batched_config(int* cb, size_t* smem, int* grid) {
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batched_dq_fp64, kBT, kBudget)) != cudaSuccess)
     return (int)e;
   *grid = sms * (per > 0 ? per : 1);
+  return 0;
+}
+
+int batched_tile_sizes(int* cb) {
+  cb[0] = 0;
+  cb[1] = cb_min<2>(7); cb[2] = cb_min<3>(7); cb[3] = cb_min<4>(7); cb[4] = cb_min<5>(7);
+  cb[5] = cb_min<6>(7); cb[6] = cb_min<7>(7); cb[7] = cb_min<8>(7); cb[8] = cb_min<9>(7);
   return 0;
 }
 

@@ -200,6 +200,19 @@ static int upload_tables(const Tab1D* t) {
   return e;
 }
 
+namespace sfx {
+// Tables of every degree into every kernel file (used by the no-alloc entry
+// point, which has no space or plan to trigger the upload).
+int upload_all_tables() {
+  for (int p = 1; p <= kMaxDeg; ++p) {
+    Tab1D t;
+    make_tab1d(p, &t);
+    if (upload_tables(&t) != 0) return 1;
+  }
+  return 0;
+}
+}  // namespace sfx
+
 // ------------------------------------------------------------------ context
 extern "C" sfx_status sfx_ctx_create(int device, sfx_ctx** out) {
   if (!out || device < -1) return SFX_ERR_ARG;

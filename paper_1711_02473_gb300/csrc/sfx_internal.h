@@ -122,6 +122,7 @@ struct BatchArgs {
   const int32_t* sorted_cells;
   const BatchTile* tiles;
   int ntiles;
+  const int* ntiles_dev;          // if set, the tile count is read from the device
   int* counter;                   // tile counter, zeroed before each launch
   double* y[4];
   double alpha[4], beta[4];
@@ -130,6 +131,7 @@ struct BatchArgs {
 };
 int batched_config(int* cb_per_degree /*[kMaxDeg+1]*/, size_t* smem, int* grid);
 int batched_launch(const BatchArgs& b, int grid, size_t smem, void* stream);
+int batched_tile_sizes(int* cb_per_degree /*[kMaxDeg+1]*/);
 
 // Each kernel file keeps its own constant-memory copy of the 1D tables.
 int upload_tab_scalar(const Tab1D* t);
