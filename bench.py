@@ -38,12 +38,17 @@ def parse():
     ap.add_argument("--impl", default="sfx", choices=["sfx", "reference"])
     ap.add_argument("--degrees", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--families", default="Q,DQ")
-    ap.add_argument("--precision", default="tf32x3,fp64",
-                    help="comma list; the first is the headline, the others are timed beside it")
+    ap.add_argument("--precision", default="tf32x3,fp64,tf32x3:stored,fp64:stored",
+                    help="comma list of arms; the first is the headline, the others are timed beside it. "
+                         "':stored' arms apply the operator with geometric factors stored once per space "
+                         "(their setup time is reported separately)")
     ap.add_argument("--dims", default="64,64,64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the measurements of the other configurations (structured elements, "
+                         "p-adaptive batching, naive kernels, element matrices)")
     return ap.parse_args()
 
 
@@ -229,7 +234,7 @@ def main():
     # the oracle to <= 1e-12 in the GPU tests)
     if "fp64" in arms and prec != "fp64":
         for c_head, c64 in zip(head["per_case"], arms["fp64"]["per_case"]):
-            c_head["rel_err_vs_fp64"] = rel_err_case(sfx, torch, ctx, spaces, xs, c_head, prec)
+            c_head["rel_err_vs_fp64"] = rel_err_case(sfx, torch, ctx, spaces, xs, c_head, prec.split(":")[0])
     mesh_cells = dims[0] * dims[1] * dims[2]
     dom = max(head["per_case"], key=lambda c: c["ms"])
     fam, p, form = dom["family"], dom["p"], dom["form"]
@@ -261,13 +266,21 @@ def main():
            "gpu_launches": sum(launches_per_action(f) for f, _, _ in wl) * args.steps * len(precs),
            "clocks": head["clocks"], "roofline": roofline, "per_case": head["per_case"],
            "arms": {pr: {"value": dofs_step * ws / (arms[pr]["ms_step"] * 1e-3), "ms_per_step": arms[pr]["ms_step"],
-                         "clocks": arms[pr]["clocks"]} for pr in precs}}
+                         "clocks": arms[pr]["clocks"], "speedup_vs_fp64": (arms["fp64"]["ms_step"] / arms[pr]["ms_step"]
+                                                                           if "fp64" in arms else None),
+                         **({"geometry_setup_ms": arms[pr]["geometry_setup_ms"]} if "geometry_setup_ms" in arms[pr]
+                            else {})} for pr in precs}}
+    for pr in precs[1:]:
+        out["arms"][pr]["per_case"] = arms[pr]["per_case"]
     if "fp64" in arms and prec != "fp64":
-        out["arms"]["fp64"]["per_case"] = arms["fp64"]["per_case"]
         out["speedup_vs_fp64"] = arms["fp64"]["ms_step"] / ms_step
 
     if not args.no_e2e:
         out["e2e"] = e2e(args, sfx, torch, ctx, spaces, wl, prec, stream)
+    if not args.no_extras and ws == 1:
+        del spaces, xs, ys
+        torch.cuda.empty_cache()
+        out["extras"] = run_extras(sfx, torch, ctx, inputs, flush, stream)
     if rank == 0 and not args.no_cpu_baseline:
         import oracle as orc
         X = mesh.coords()
@@ -287,10 +300,25 @@ def geometry_flops_per_cell(fam, p, form):
     return ((73 if lap else 17) + 1) * n ** 3
 
 
-def time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, prec, flush, stream, ws, local):
+def time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, arm, flush, stream, ws, local):
+    prec, _, mode = arm.partition(":")
+    stored = mode == "stored"
+    qd, setup_ms = {}, 0.0
+    if stored:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for key, sp in spaces.items():
+            qd[key] = sfx.QData(ctx, sp, "fp64" if prec == "fp64" else "fp32", stream=stream)
+        setup_ms = (time.perf_counter() - t0) * 1e3
+
     def run_case(fam, p, form):
-        sfx.sfx_assemble_action(ctx, form, spaces[(fam, p)], xs[(fam, p)], ys[(fam, p)], precision=prec,
-                                params=HELM if form == "helmholtz" else None, stream=stream)
+        prm = HELM if form == "helmholtz" else None
+        if stored:
+            sfx.sfx_assemble_action_stored(ctx, form, spaces[(fam, p)], qd[(fam, p)], xs[(fam, p)], ys[(fam, p)],
+                                           precision=prec, params=prm, stream=stream)
+        else:
+            sfx.sfx_assemble_action(ctx, form, spaces[(fam, p)], xs[(fam, p)], ys[(fam, p)], precision=prec,
+                                    params=prm, stream=stream)
 
     ev = {c: [] for c in wl}
 
@@ -339,7 +367,12 @@ def time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, prec, flush, stream, ws,
         nd = spaces[(fam, p)].ndof
         per_case.append({"family": fam, "p": p, "form": form, "ms": round(t, 4), "dofs_per_s": nd / (t * 1e-3),
                          "gflops_fp64_alg": flops_per_cell(fam, p, form) * ncell / (t * 1e-3) / 1e9})
-    return {"ms_step": ms_total / args.steps, "per_case": per_case, "clocks": clocks}
+    for q in qd.values():
+        q.close()
+    out = {"ms_step": ms_total / args.steps, "per_case": per_case, "clocks": clocks}
+    if stored:
+        out["geometry_setup_ms"] = setup_ms
+    return out
 
 
 def rel_err_case(sfx, torch, ctx, spaces, xs, case, prec):
@@ -351,6 +384,136 @@ def rel_err_case(sfx, torch, ctx, spaces, xs, case, prec):
     sfx.sfx_assemble_action(ctx, form, sp, x, y64, params=prm)
     sfx.sfx_assemble_action(ctx, form, sp, x, ym, precision=prec, params=prm)
     return float((ym - y64).abs().max() / y64.abs().max())
+
+
+def _time(torch, stream, flush, fn, reps=3, warm=2):
+    """median CUDA-event time (ms) of fn(), L2 flushed before every run"""
+    for _ in range(warm):
+        flush.fill_(1.0)
+        fn()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def dq_multi_flops(p, form, nrhs):
+    """FP64 flops of the DQ action for one cell and nrhs right-hand sides
+    (geometry once, contractions and flux per RHS)."""
+    n = p + 1
+    lap = form != "mass"
+    contr = (6 if lap else 0) * 2 * n ** 4
+    geo = (73 if lap else 0) + (17 if not lap else 4)
+    flux = 15 if lap else 1
+    return (contr + flux * n ** 3) * nrhs + geo * n ** 3
+
+
+def matrix_flops(p, fam):
+    """FP64 flops of the sum-factorised element matrix of the scalar Laplace
+    form per cell: stages q1 (9 terms, n^5), q2 (9 terms, n^6), q3 (4 groups,
+    n^7), 3 flops per multiply-add with a table product."""
+    n = p + 1
+    return 3 * (9 * n ** 5 + 9 * n ** 6 + 4 * n ** 7)
+
+
+def run_extras(sfx, torch, ctx, inputs, flush, stream):
+    ex = {}
+    # --- structured elements (NCF/NCE on 32^3, p=1..6; neo-Hookean on 48^3, p=2..6)
+    rows = []
+    for fam, form, dims, ps in [("NCF", "ncf_mass_divdiv", (32, 32, 32), range(1, 7)),
+                                ("NCE", "nce_curlcurl", (32, 32, 32), range(1, 7)),
+                                ("VQ", "neohooke", (48, 48, 48), range(2, 7))]:
+        mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+        for p in ps:
+            sp = sfx.Space(mesh, fam, p)
+            x = (inputs.displacement(sp.ndof, p, dims[0], seed=1) if fam == "VQ"
+                 else inputs.random_vector(sp.ndof, 1, seed=1))
+            xd = torch.from_numpy(x).cuda()
+            yd = torch.empty_like(xd)
+            t = _time(torch, stream, flush, lambda: sfx.sfx_assemble_action(ctx, form, sp, xd, yd, stream=stream))
+            rows.append({"family": fam, "form": form, "p": p, "mesh": "%dx%dx%d" % dims, "ndof": sp.ndof,
+                         "ms": round(t, 4), "dofs_per_s": sp.ndof / (t * 1e-3)})
+            del xd, yd, sp
+        del mesh
+    ex["structured_fp64"] = rows
+    if ctx.sync_status() != 0:
+        ex["structured_status"] = "device status flagged"
+    # --- p-adaptive batching: 200,000 cells (40x50x100), p in 1..8 with P(p) ~ 1/p,
+    #     DQ_p per cell, Laplace + mass on 16 RHS (seeds 0..15)
+    dims = (40, 50, 100)
+    mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    deg = inputs.padaptive_degrees(int(np.prod(dims)), 8, seed=2)
+    forms, R = ["laplace", "mass"], 16
+    plan = sfx.Plan(ctx, mesh, deg, forms, nrhs=R)
+    x = np.stack([inputs.random_vector(plan.ndof, 1, seed=r) for r in range(R)], axis=1)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda().reshape(-1)
+    del x
+    ys = [torch.empty_like(xd) for _ in forms]
+    tg = _time(torch, stream, flush, lambda: plan.execute(xd, ys, mode="graph", stream=stream))
+    tl = _time(torch, stream, flush, lambda: plan.execute(xd, ys, mode="per_launch", stream=stream), reps=2, warm=1)
+    work = plan.ndof * R * len(forms)
+    ndeg = len(np.unique(deg))
+    fl = sum(dq_multi_flops(int(p), f, R) * int((deg == p).sum()) for p in np.unique(deg) for f in forms)
+    ex["padaptive_batched_fp64"] = {
+        "cells": int(np.prod(dims)), "ndof": int(plan.ndof), "nrhs": R, "forms": forms, "tiles": int(plan.ntiles),
+        "graph_ms": round(tg, 3), "per_launch_ms": round(tl, 3),
+        "graph_dofs_per_s": work / (tg * 1e-3), "per_launch_dofs_per_s": work / (tl * 1e-3),
+        "speedup_graph_vs_per_launch": tl / tg, "launches_graph": 1, "launches_per_launch": ndeg * R * len(forms),
+        "roofline": {"bound": "alu", "achieved": round(fl / (tg * 1e-3) / 1e9, 2), "peak": FP64_PEAK_GFLOPS,
+                     "unit": "GFLOP/s", "frac": round(fl / (tg * 1e-3) / 1e9 / FP64_PEAK_GFLOPS, 4)}}
+    del xd, ys, plan, mesh
+    torch.cuda.empty_cache()
+    # --- naive (un-factorised) vs sum-factorised action, Q_p Laplace, 32^3
+    mesh = sfx.Mesh.box(ctx, 32, 32, 32, perturb=0.1, seed=0)
+    rows = []
+    for p in range(1, 9):
+        sp = sfx.Space(mesh, "Q", p)
+        xd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
+        yd = torch.empty_like(xd)
+        ts = _time(torch, stream, flush, lambda: sfx.sfx_assemble_action(ctx, "laplace", sp, xd, yd, stream=stream))
+        tn = _time(torch, stream, flush, lambda: sfx.sfx_assemble_action(ctx, "laplace", sp, xd, yd, algo="naive",
+                                                                         stream=stream), reps=2, warm=1)
+        rows.append({"p": p, "sumfact_ms": round(ts, 4), "naive_ms": round(tn, 4), "speedup": tn / ts,
+                     "sumfact_dofs_per_s": sp.ndof / (ts * 1e-3), "naive_dofs_per_s": sp.ndof / (tn * 1e-3)})
+        del xd, yd, sp
+    ex["naive_vs_sumfact_Q_laplace_32cube"] = rows
+    # --- element matrices (FP64): Q_p Laplace p=1..8 and NCF/NCE p=1..5 on 32^3,
+    #     on a chunk of cells sized to ~1 GB of output; sum-factorised and, p <= 4, naive
+    rows = []
+    for fam, form, ps in [("Q", "laplace", range(1, 9)), ("NCF", "ncf_mass_divdiv", range(1, 6)),
+                          ("NCE", "nce_curlcurl", range(1, 6))]:
+        for p in ps:
+            sp = sfx.Space(mesh, fam, p)
+            nc = int(min(sp.ncell, max(8, (1 << 30) // (sp.nloc * sp.nloc * 8))))
+            A = torch.empty(nc * sp.nloc * sp.nloc, dtype=torch.float64, device="cuda")
+            t = _time(torch, stream, flush,
+                      lambda: sfx.sfx_assemble_cell_matrices(ctx, form, sp, 0, nc, A, stream=stream), reps=2, warm=1)
+            row = {"family": fam, "form": form, "p": p, "cells": nc, "nloc": sp.nloc, "ms": round(t, 4),
+                   "cells_per_s": nc / (t * 1e-3),
+                   "dofs_per_s_paper": sp.ndof * (nc / sp.ncell) / (t * 1e-3),
+                   "gb_per_s_written": nc * sp.nloc ** 2 * 8 / (t * 1e-3) / 1e9}
+            if fam == "Q":
+                row["gflops_fp64"] = matrix_flops(p, fam) * nc / (t * 1e-3) / 1e9
+            if p <= 4:
+                tn = _time(torch, stream, flush,
+                           lambda: sfx.sfx_assemble_cell_matrices(ctx, form, sp, 0, nc, A, algo="naive",
+                                                                  stream=stream), reps=1, warm=1)
+                row["naive_ms"] = round(tn, 4)
+                row["speedup_vs_naive"] = tn / t
+            rows.append(row)
+            del A, sp
+            torch.cuda.empty_cache()
+    ex["cell_matrices_fp64_32cube"] = rows
+    ex["note"] = ("extras are measured once per configuration with CUDA events (median of 1-3 runs, L2 "
+                  "flushed); DoFs/s follows the paper's N/t; dofs_per_s_paper for matrices scales N by the "
+                  "fraction of cells assembled")
+    return ex
 
 
 def e2e(args, sfx, torch, ctx, spaces, wl, prec, stream):

@@ -196,6 +196,33 @@ sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_for
                                       const sfx_space* space, int64_t cell_begin, int64_t cell_end,
                                       double* A, sfx_precision prec, sfx_algo algo, void* stream);
 
+/* ----------------------------------------------- stored geometric factors */
+
+/* Geometric factors at the quadrature points of every cell of a Q_p / DQ_p
+ * space, computed once in FP64 (the argument-factorised P^(k,l) of Sec. 3.2
+ * with weight and |J| folded in: P = w S G G^T, 6 symmetric entries, and w S)
+ * and kept on the device, as double (SFX_QDATA_FP64) and/or float
+ * (SFX_QDATA_FP32); 7 q^3 values per cell.  The stored actions read them
+ * instead of recomputing J, det J and J^{-1} at every point: a trade of memory
+ * traffic (56 or 28 bytes per point) for FP64 arithmetic, worthwhile when the
+ * same operator is applied many times.  Synchronous.  The space must outlive
+ * the factors.  Errors: SFX_ERR_ARG, SFX_ERR_UNSUPPORTED (family),
+ * SFX_ERR_ALLOC, SFX_ERR_CUDA; an inverted cell sets SFX_DEV_INVERTED. */
+typedef struct sfx_qdata sfx_qdata;
+#define SFX_QDATA_FP64 1
+#define SFX_QDATA_FP32 2
+sfx_status sfx_qdata_create(sfx_ctx* ctx, const sfx_space* space, int formats, void* stream, sfx_qdata** out);
+void sfx_qdata_destroy(sfx_qdata* qdata);
+
+/* sfx_assemble_action for MASS / LAPLACE / HELMHOLTZ on the space of `qdata`
+ * using the stored factors: prec FP64 needs SFX_QDATA_FP64 (same arithmetic as
+ * the on-the-fly FP64 action), TF32X3 / BF16X3 need SFX_QDATA_FP32 (no FP64
+ * geometry left in the kernel).  Other arguments and errors as
+ * sfx_assemble_action. */
+sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                      const sfx_space* space, const sfx_qdata* qdata, const double* x, double* y,
+                                      int nrhs, int accumulate, sfx_precision prec, void* stream);
+
 /* ------------------------------------------------------ batched execution */
 
 /* A plan for repeated actions on a p-adaptive DQ mesh: cell c carries

@@ -32,7 +32,9 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_space_create", "sfx_space_info", "sfx_space_destroy", "sfx_tabulate_1d",
            "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices",
            "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy",
-           "sfx_padaptive_action_noalloc"]
+           "sfx_padaptive_action_noalloc", "sfx_qdata_create", "sfx_qdata_destroy",
+           "sfx_assemble_action_stored"]
+QDATA = {"fp64": 1, "fp32": 2, "both": 3}
 EXEC = {"graph": 0, "per_launch": 1}
 
 
@@ -86,6 +88,10 @@ def lib():
         L.sfx_plan_execute.argtypes = [P, P, P, i, P]
         L.sfx_plan_destroy.argtypes = [P]
         L.sfx_plan_destroy.restype = None
+        L.sfx_qdata_create.argtypes = [P, P, i, P, C.POINTER(P)]
+        L.sfx_qdata_destroy.argtypes = [P]
+        L.sfx_qdata_destroy.restype = None
+        L.sfx_assemble_action_stored.argtypes = [P, i, C.POINTER(_Params), P, P, P, P, i, i, i, P]
         L.sfx_padaptive_action_noalloc.argtypes = [P, P, P, P, i, C.POINTER(_Params), P, P, i, P]
         for name in EXPORTS:
             f = getattr(L, name)
@@ -249,6 +255,38 @@ def sfx_assemble_cell_matrices(ctx, form, space, cell_begin, cell_end, A, precis
                                             _dptr(A, "float64"), PRECISION[precision], ALGO[algo],
                                             _stream(stream)), "sfx_assemble_cell_matrices")
     return A
+
+
+class QData:
+    """Stored geometric factors of a Q_p / DQ_p space (sfx_qdata_*)."""
+
+    def __init__(self, ctx, space, formats="both", stream=None):
+        self.space = space
+        self.h = C.c_void_p()
+        _check(lib().sfx_qdata_create(ctx.h, space.h, QDATA[formats], _stream(stream), C.byref(self.h)),
+               "sfx_qdata_create")
+
+    def close(self):
+        if self.h:
+            lib().sfx_qdata_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sfx_assemble_action_stored(ctx, form, space, qdata, x, y, nrhs=None, accumulate=False, precision="fp64",
+                               params=None, stream=None):
+    nrhs = nrhs if nrhs is not None else (1 if x.dim() == 1 else x.shape[1])
+    if x.numel() != space.ndof * nrhs or y.numel() != space.ndof * nrhs:
+        raise ValueError("x and y must hold ndof * nrhs doubles")
+    _check(lib().sfx_assemble_action_stored(ctx.h, FORM[form], _params(params), space.h, qdata.h,
+                                            _dptr(x, "float64"), _dptr(y, "float64"), nrhs, int(bool(accumulate)),
+                                            PRECISION[precision], _stream(stream)), "sfx_assemble_action_stored")
+    return y
 
 
 def sfx_padaptive_action_noalloc(ctx, mesh, degree, cell_offset, form, x, y, nrhs=1, params=None, stream=None):

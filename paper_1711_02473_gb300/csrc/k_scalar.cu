@@ -8,11 +8,11 @@ SFX_DEFINE_TAB_UPLOAD(upload_tab_scalar)
 
 namespace {
 
-template <int N, bool DQ, int FORM>
+template <int N, bool DQ, int FORM, bool STORED>
 __global__ void __launch_bounds__(256) k_action_scalar_fp64(const ActArgs a, const int64_t ncell_total) {
   extern __shared__ double sm[];
   const int cb = blockDim.x / (N * N);
-  scalar_tile_fp64<N, DQ, FORM>(a, ncell_total, (int64_t)blockIdx.x * cb, cb, sm);
+  scalar_tile_fp64<N, DQ, FORM, STORED>(a, ncell_total, (int64_t)blockIdx.x * cb, cb, sm);
 }
 
 template <int N, bool DQ, int FORM>
@@ -24,7 +24,7 @@ int launch_fp64(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   int cb = Sh::MAXCB;
   while (cb > 1 && fixed + cb * per_team > budget) --cb;
   const size_t smem = fixed + cb * per_team;
-  auto kern = k_action_scalar_fp64<N, DQ, FORM>;
+  auto kern = a.qd64 ? k_action_scalar_fp64<N, DQ, FORM, true> : k_action_scalar_fp64<N, DQ, FORM, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int64_t grid = (a.ncells + cb - 1) / cb;
@@ -48,6 +48,16 @@ int dispatch_family(bool dq, sfx_form form, const ActArgs& a, int64_t nc, cudaSt
 }
 
 }  // namespace
+
+int launch_action_scalar_mixed_tf32(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+int launch_action_scalar_mixed_bf16(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+
+int launch_action_scalar_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
+                               void* stream) {
+  if (prec == SFX_PREC_TF32X3) return launch_action_scalar_mixed_tf32(sp, form, a, stream);
+  if (prec == SFX_PREC_BF16X3) return launch_action_scalar_mixed_bf16(sp, form, a, stream);
+  return -1;
+}
 
 int launch_scalar_fp64_degree(int p, bool dq, sfx_form form, const ActArgs& a, int64_t nc, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;

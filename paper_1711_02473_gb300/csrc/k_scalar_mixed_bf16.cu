@@ -1,0 +1,63 @@
+// k_scalar_mixed_bf16.cu -- BF16x3 instantiation of the split-precision scalar
+// actions (body in scalar_mixed_body.cuh).
+#include "scalar_mixed_body.cuh"
+
+namespace sfx {
+
+SFX_DEFINE_TAB_UPLOAD(upload_tab_scalar_mixed_bf16)
+
+namespace {
+
+template <int N, bool DQ, int FORM, int PREC>
+int launch_mixed(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
+  using Sh = MixedShape<N, FORM>;
+  const size_t fixed = 2 * sizeof(TabF) + (Sh::N3 + 16) * 8;
+  const size_t budget = 200 * 1024;
+  int cb = (int)((budget - fixed) / Sh::BYTES_PER_CELL);
+  const int want = (N <= 3) ? 32 : 16;  // enough fibers for dense tiles
+  if (cb > want) cb = want;
+  if (cb < 1) cb = 1;
+  const size_t smem = fixed + (size_t)cb * Sh::CELLD * 8 + (size_t)cb * Sh::CELLF * 4 + (size_t)cb * 8 + 16;
+  auto kern = a.qd32 ? k_action_scalar_mixed<N, DQ, FORM, PREC, true> : k_action_scalar_mixed<N, DQ, FORM, PREC, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  const int64_t grid = (a.ncells + cb - 1) / cb;
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(a, ncell_total, cb);
+  return (int)cudaGetLastError();
+}
+
+template <int N, bool DQ>
+int dispatch_form(sfx_form form, const ActArgs& a, int64_t nc, cudaStream_t s) {
+  switch (form) {
+    case SFX_MASS: return launch_mixed<N, DQ, SFX_MASS, SFX_PREC_BF16X3>(a, nc, s);
+    case SFX_LAPLACE: return launch_mixed<N, DQ, SFX_LAPLACE, SFX_PREC_BF16X3>(a, nc, s);
+    case SFX_HELMHOLTZ: return launch_mixed<N, DQ, SFX_HELMHOLTZ, SFX_PREC_BF16X3>(a, nc, s);
+    default: return -1;
+  }
+}
+
+template <int N>
+int dispatch(bool dq, sfx_form form, const ActArgs& a, int64_t nc, cudaStream_t s) {
+  return dq ? dispatch_form<N, true>(form, a, nc, s) : dispatch_form<N, false>(form, a, nc, s);
+}
+
+}  // namespace
+
+int launch_action_scalar_mixed_bf16(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream) {
+  const bool dq = sp->family == SFX_DQ;
+  const int64_t nc = sp->mesh->ncell;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (sp->p) {
+    case 1: return dispatch<2>(dq, form, a, nc, s);
+    case 2: return dispatch<3>(dq, form, a, nc, s);
+    case 3: return dispatch<4>(dq, form, a, nc, s);
+    case 4: return dispatch<5>(dq, form, a, nc, s);
+    case 5: return dispatch<6>(dq, form, a, nc, s);
+    case 6: return dispatch<7>(dq, form, a, nc, s);
+    case 7: return dispatch<8>(dq, form, a, nc, s);
+    case 8: return dispatch<9>(dq, form, a, nc, s);
+  }
+  return -1;
+}
+
+}  // namespace sfx

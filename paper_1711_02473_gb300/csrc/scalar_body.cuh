@@ -34,7 +34,9 @@ struct ScalarShape {
 
 // One tile: the cb cells of slots slot0 .. slot0+cb-1, one team of N^2 threads
 // per cell (threads of teams >= cb idle but take part in the barriers).
-template <int N, bool DQ, int FORM>
+// STORED: the geometric factors come from a.qd64 (sfx_qdata) instead of
+// being computed from the coordinates.
+template <int N, bool DQ, int FORM, bool STORED = false>
 __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t ncell_total, const int64_t slot0,
                                                  const int cb, double* sm) {
   using Sh = ScalarShape<N, FORM>;
@@ -68,6 +70,20 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
   const int64_t slot = slot0 + team;
   const bool active = member && slot_cell(a, slot, ncell_total, &cell);
   if (member && t == 0) *bad = 0;
+  const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
+  const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
+  if (STORED) {
+    // stored factors: K = alpha P, WS = beta w S at the thread's points
+#pragma unroll 1
+    for (int k = 0; k < (member ? N : 0); ++k) {
+      const int qp = k * N2 + t;
+      const double* qd = a.qd64 + (int64_t)cell * 7 * N3;
+      if (LAP)
+        for (int j = 0; j < 6; ++j) K[j * N3 + qp] = active ? alpha * qd[j * N3 + qp] : 0.0;
+      if (MAS) WS[qp] = active ? beta * qd[6 * N3 + qp] : 0.0;
+    }
+    __syncthreads();
+  } else {
   for (int c = member ? t : 8; c < 8; c += N2) {  // a team may have fewer than 8 threads (p = 1)
     if (active) {
       const int v = a.vmap[(int64_t)cell * 8 + c];
@@ -83,8 +99,6 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
   __syncthreads();
 
   // geometric factors at the thread's points qp = k*N2 + t, k = q1
-  const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
-  const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
 #pragma unroll 1
   for (int k = 0; k < (member ? N : 0); ++k) {
     const int qp = k * N2 + t;
@@ -111,6 +125,7 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
     if (MAS) WS[qp] = beta * W3[qp] * S;
   }
   __syncthreads();
+  }
   const bool ok = active && !*bad;
   if (active && *bad && t == 0) set_flag(a.status, SFX_DEV_INVERTED);
   const int tl = member ? t : N3;  // first index of this thread's strided loops (none for non-members)

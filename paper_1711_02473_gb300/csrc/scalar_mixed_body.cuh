@@ -1,6 +1,8 @@
-// k_scalar_mixed.cu -- scalar-form actions (mass, Laplace, Helmholtz; Q_p and
-// DQ_p) with the 1D contractions on the tensor cores as split-precision
-// products, and the geometry / weight scaling / scatter in FP64.
+#pragma once
+// scalar_mixed_body.cuh -- scalar-form actions (mass, Laplace, Helmholtz; Q_p
+// and DQ_p) with the 1D contractions on the tensor cores as split-precision
+// products, and the geometry / weight scaling / scatter in FP64.  Instantiated
+// once per input format in k_scalar_mixed_tf32.cu and k_scalar_mixed_bf16.cu.
 //
 // Same algorithm as k_scalar.cu (Sec. 3.3, Eqs. coeff_eval and form_eval with
 // the sum factorisation of Sec. 3.2).  What changes is where the arithmetic runs:
@@ -21,9 +23,6 @@
 #include "kern_common.cuh"
 
 namespace sfx {
-
-SFX_DEFINE_TAB_UPLOAD(upload_tab_scalar_mixed)
-
 namespace {
 
 constexpr int kThreads = 256;
@@ -181,7 +180,9 @@ struct MixedShape {
   static constexpr int BYTES_PER_CELL = CELLF * 4 + CELLD * 8 + 4;
 };
 
-template <int N, bool DQ, int FORM, int PREC>
+// STORED: the FP32 geometric factors come from a.qd32 (sfx_qdata) and no
+// FP64 geometry runs in the kernel.
+template <int N, bool DQ, int FORM, int PREC, bool STORED>
 __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs a, const int64_t ncell_total,
                                                                   const int cb) {
   using Sh = MixedShape<N, FORM>;
@@ -218,6 +219,20 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
     flags[2 * c + 1] = 0;
   }
   __syncthreads();
+  const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
+  const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
+  if (STORED) {
+    const float fa = (float)alpha, fb = (float)beta;
+    for (int i = tid; i < cb * N3; i += kThreads) {
+      const int c = i / N3, qp = i - c * N3;
+      const int cell = flags[2 * c];
+      const float* qd = a.qd32 + (int64_t)(cell >= 0 ? cell : 0) * 7 * N3;
+      if (LAP)
+        for (int j = 0; j < 6; ++j) K[(j * cb + c) * N3 + qp] = cell >= 0 ? fa * qd[j * N3 + qp] : 0.f;
+      if (MAS) WS[c * N3 + qp] = cell >= 0 ? fb * qd[6 * N3 + qp] : 0.f;
+    }
+    __syncthreads();
+  } else {
   // corners
   for (int i = tid; i < cb * 24; i += kThreads) {
     const int c = i / 24, v = (i % 24) / 3, k = i % 3;
@@ -233,8 +248,6 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
   }
   __syncthreads();
   // geometric factors in FP64, stored rounded to FP32
-  const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
-  const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
   for (int i = tid; i < cb * N3; i += kThreads) {
     const int c = i / N3, qp = i - c * N3;
     const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
@@ -264,6 +277,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
   for (int c = tid; c < cb; c += kThreads)
     if (flags[2 * c] >= 0 && flags[2 * c + 1]) set_flag(a.status, SFX_DEV_INVERTED);
 
+  }
 #pragma unroll 1
   for (int r = 0; r < a.nrhs; ++r) {
     for (int i = tid; i < cb * N3; i += kThreads) {
@@ -333,60 +347,5 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
   }
 }
 
-template <int N, bool DQ, int FORM, int PREC>
-int launch_mixed(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
-  using Sh = MixedShape<N, FORM>;
-  const size_t fixed = 2 * sizeof(TabF) + (Sh::N3 + 16) * 8;
-  const size_t budget = 200 * 1024;
-  int cb = (int)((budget - fixed) / Sh::BYTES_PER_CELL);
-  const int want = (N <= 3) ? 32 : 16;  // enough fibers for dense tiles
-  if (cb > want) cb = want;
-  if (cb < 1) cb = 1;
-  const size_t smem = fixed + (size_t)cb * Sh::CELLD * 8 + (size_t)cb * Sh::CELLF * 4 + (size_t)cb * 8 + 16;
-  auto kern = k_action_scalar_mixed<N, DQ, FORM, PREC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return (int)e;
-  const int64_t grid = (a.ncells + cb - 1) / cb;
-  kern<<<(unsigned)grid, kThreads, smem, s>>>(a, ncell_total, cb);
-  return (int)cudaGetLastError();
-}
-
-template <int N, bool DQ, int PREC>
-int dispatch_form(sfx_form form, const ActArgs& a, int64_t nc, cudaStream_t s) {
-  switch (form) {
-    case SFX_MASS: return launch_mixed<N, DQ, SFX_MASS, PREC>(a, nc, s);
-    case SFX_LAPLACE: return launch_mixed<N, DQ, SFX_LAPLACE, PREC>(a, nc, s);
-    case SFX_HELMHOLTZ: return launch_mixed<N, DQ, SFX_HELMHOLTZ, PREC>(a, nc, s);
-    default: return -1;
-  }
-}
-
-template <int N>
-int dispatch(bool dq, sfx_precision prec, sfx_form form, const ActArgs& a, int64_t nc, cudaStream_t s) {
-  if (prec == SFX_PREC_TF32X3)
-    return dq ? dispatch_form<N, true, SFX_PREC_TF32X3>(form, a, nc, s) : dispatch_form<N, false, SFX_PREC_TF32X3>(form, a, nc, s);
-  return dq ? dispatch_form<N, true, SFX_PREC_BF16X3>(form, a, nc, s) : dispatch_form<N, false, SFX_PREC_BF16X3>(form, a, nc, s);
-}
-
 }  // namespace
-
-int launch_action_scalar_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
-                               void* stream) {
-  if (prec != SFX_PREC_TF32X3 && prec != SFX_PREC_BF16X3) return -1;
-  const bool dq = sp->family == SFX_DQ;
-  const int64_t nc = sp->mesh->ncell;
-  cudaStream_t s = (cudaStream_t)stream;
-  switch (sp->p) {
-    case 1: return dispatch<2>(dq, prec, form, a, nc, s);
-    case 2: return dispatch<3>(dq, prec, form, a, nc, s);
-    case 3: return dispatch<4>(dq, prec, form, a, nc, s);
-    case 4: return dispatch<5>(dq, prec, form, a, nc, s);
-    case 5: return dispatch<6>(dq, prec, form, a, nc, s);
-    case 6: return dispatch<7>(dq, prec, form, a, nc, s);
-    case 7: return dispatch<8>(dq, prec, form, a, nc, s);
-    case 8: return dispatch<9>(dq, prec, form, a, nc, s);
-  }
-  return -1;
-}
-
 }  // namespace sfx

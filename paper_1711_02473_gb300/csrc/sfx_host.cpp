@@ -191,7 +191,9 @@ void make_tab1d(int p, Tab1D* t) {
 // Copy the 1D tables of one degree into every kernel file's constant memory.
 static int upload_tables(const Tab1D* t) {
   int e = upload_tab_scalar(t);
-  if (!e) e = upload_tab_scalar_mixed(t);
+  if (!e) e = upload_tab_scalar_mixed_tf32(t);
+  if (!e) e = upload_tab_scalar_mixed_bf16(t);
+  if (!e) e = upload_tab_qdata(t);
   if (!e) e = upload_tab_hdivcurl(t);
   if (!e) e = upload_tab_elastic(t);
   if (!e) e = upload_tab_matrix(t);
@@ -803,4 +805,75 @@ extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* co
     for (int f = 0; f < pl->nforms; ++f) pl->gy[f] = y[f];
   }
   return cudaGraphLaunch(pl->exec, s) == cudaSuccess ? SFX_OK : SFX_ERR_CUDA;
+}
+
+// ---------------------------------------------------- stored geometry factors
+extern "C" void sfx_qdata_destroy(sfx_qdata* q) {
+  if (!q) return;
+  if (q->d64) cudaFree(q->d64);
+  if (q->d32) cudaFree(q->d32);
+  delete q;
+}
+
+extern "C" sfx_status sfx_qdata_create(sfx_ctx* ctx, const sfx_space* sp, int formats, void* stream, sfx_qdata** out) {
+  if (!ctx || !sp || !out || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
+  if ((formats & ~(SFX_QDATA_FP64 | SFX_QDATA_FP32)) || !formats) return SFX_ERR_ARG;
+  *out = nullptr;
+  if (sp->family != SFX_Q && sp->family != SFX_DQ) return SFX_ERR_UNSUPPORTED;
+  sfx_qdata* q = new (std::nothrow) sfx_qdata;
+  if (!q) return SFX_ERR_ALLOC;
+  q->space = sp;
+  const int64_t n = sp->p + 1;
+  const size_t cnt = (size_t)sp->mesh->ncell * 7 * n * n * n;
+  if ((formats & SFX_QDATA_FP64) && cudaMalloc(&q->d64, cnt * sizeof(double)) != cudaSuccess) {
+    q->d64 = nullptr; sfx_qdata_destroy(q); return SFX_ERR_ALLOC;
+  }
+  if ((formats & SFX_QDATA_FP32) && cudaMalloc(&q->d32, cnt * sizeof(float)) != cudaSuccess) {
+    q->d32 = nullptr; sfx_qdata_destroy(q); return SFX_ERR_ALLOC;
+  }
+  q->fp32 = (formats & SFX_QDATA_FP32) != 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (launch_qdata(sp, q, ctx->d_status, stream) != 0 || cudaStreamSynchronize(s) != cudaSuccess) {
+    sfx_qdata_destroy(q);
+    return SFX_ERR_CUDA;
+  }
+  *out = q;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                                 const sfx_space* sp, const sfx_qdata* q, const double* x, double* y,
+                                                 int nrhs, int accumulate, sfx_precision prec, void* stream) {
+  if (!ctx || !sp || !q || !x || !y || x == y || nrhs < 1 || nrhs > 64 || ctx->device < 0 || !sp->d_map)
+    return SFX_ERR_ARG;
+  if (q->space != sp) return SFX_ERR_ARG;
+  if (form != SFX_MASS && form != SFX_LAPLACE && form != SFX_HELMHOLTZ) return SFX_ERR_ARG;
+  if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3) return SFX_ERR_ARG;
+  if ((prec == SFX_PREC_FP64 && !q->d64) || (prec != SFX_PREC_FP64 && !q->d32)) return SFX_ERR_ARG;
+  sfx_form_params pr = params ? *params : default_params(form);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!accumulate && cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess)
+    return SFX_ERR_CUDA;
+  ActArgs a{};
+  a.map = sp->d_map;
+  a.vmap = sp->mesh->d_vmap;
+  a.xyz = sp->mesh->d_xyz;
+  a.x = x;
+  a.y = y;
+  a.nrhs = nrhs;
+  a.r0 = 0;
+  a.r1 = nrhs;
+  a.alpha = pr.alpha;
+  a.beta = pr.beta;
+  a.status = ctx->d_status;
+  if (prec == SFX_PREC_FP64) a.qd64 = q->d64; else a.qd32 = q->d32;
+  for (int col = 0; col < sp->ncolour; ++col) {
+    a.cells = sp->d_cells + sp->colour_off[col];
+    a.ncells = sp->colour_off[col + 1] - sp->colour_off[col];
+    if (a.ncells == 0) continue;
+    const int e = launch_action_scalar(sp, form, prec, SFX_ALGO_SUMFACT, a, stream);
+    if (e == -1) return SFX_ERR_UNSUPPORTED;
+    if (e) return SFX_ERR_CUDA;
+  }
+  return SFX_OK;
 }

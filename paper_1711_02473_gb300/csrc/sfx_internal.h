@@ -67,6 +67,16 @@ struct sfx_space {
   sfx::Tab1D tab;                  // 1D tables of degree p
 };
 
+// Geometric factors at the quadrature points of every cell, computed once in
+// FP64: per cell 7 arrays of q^3 values, P = w S G G^T (00,11,22,01,02,12) and
+// w S.  Kept in FP64 (d64) or rounded to FP32 (d32).
+struct sfx_qdata {
+  const sfx_space* space = nullptr;
+  int fp32 = 0;
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+};
+
 // ----------------------------------------------------------------- kernels
 namespace sfx {
 
@@ -83,6 +93,8 @@ struct ActArgs {
   int nrhs;
   int r0, r1;             // right-hand sides handled by this launch: [r0, r1)
   const int64_t* dq_off;  // p-adaptive DQ: dof of (cell, l) = dq_off[cell] + l (map unused)
+  const double* qd64;     // stored geometric factors (FP64), [cell][7][q^3], or null
+  const float* qd32;      // stored geometric factors (FP32), [cell][7][q^3], or null
   int cell_vectors;       // 1: write b^K per slot instead of scattering
   double alpha, beta, mu, lambda;
   uint32_t* status;
@@ -132,14 +144,17 @@ struct BatchArgs {
 int batched_config(int* cb_per_degree /*[kMaxDeg+1]*/, size_t* smem, int* grid);
 int batched_launch(const BatchArgs& b, int grid, size_t smem, void* stream);
 int batched_tile_sizes(int* cb_per_degree /*[kMaxDeg+1]*/);
+int launch_qdata(const sfx_space* sp, sfx_qdata* q, uint32_t* status, void* stream);
 
 // Each kernel file keeps its own constant-memory copy of the 1D tables.
 int upload_tab_scalar(const Tab1D* t);
-int upload_tab_scalar_mixed(const Tab1D* t);
+int upload_tab_scalar_mixed_tf32(const Tab1D* t);
+int upload_tab_scalar_mixed_bf16(const Tab1D* t);
 int upload_tab_hdivcurl(const Tab1D* t);
 int upload_tab_elastic(const Tab1D* t);
 int upload_tab_matrix(const Tab1D* t);
 int upload_tab_naive(const Tab1D* t);
 int upload_tab_batched(const Tab1D* t);
+int upload_tab_qdata(const Tab1D* t);
 
 }  // namespace sfx
