@@ -125,6 +125,24 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def reduce_max_ms(ms, ws, device="cuda"):
+    """Max over ranks of a rank's timed interval (the slowest rank sets the
+    job's time); identity on one rank."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(dofs_per_step, ws, ms_step):
+    """Whole-job throughput: every rank processes dofs_per_step per step
+    (replicas, weak scaling)."""
+    return dofs_per_step * ws / (ms_step * 1e-3)
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -229,7 +247,7 @@ def main():
     head = arms[prec]
     ms_step = head["ms_step"]
     dofs_step = sum(spaces[(f, p)].ndof for f, p, _ in wl)
-    value = dofs_step * ws / (ms_step * 1e-3)
+    value = job_value(dofs_step, ws, ms_step)
     # error of each arm against the FP64 arm, per case (the FP64 path matches
     # the oracle to <= 1e-12 in the GPU tests)
     if "fp64" in arms and prec != "fp64":
@@ -354,11 +372,7 @@ def time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, arm, flush, stream, ws, 
     if ws > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    ms_total = t0.elapsed_time(t1)
-    if ws > 1:
-        tt = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_total = tt.item()
+    ms_total = reduce_max_ms(t0.elapsed_time(t1), ws)
     ncell = next(iter(spaces.values())).ncell
     per_case = []
     for c in wl:
