@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in cells-per-CTA instead of tuning them first (untimed)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the measurements of the other configurations (structured elements, "
                          "p-adaptive batching, naive kernels, element matrices)")
@@ -241,6 +243,13 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     precs = args.precision.split(",")
+    tuning = None
+    if not args.no_autotune:
+        from paper_1711_02473_gb300 import autotune
+        kinds = sorted({("fp64" if pr.startswith("fp64") else ("mixed_stored" if pr.endswith(":stored") else "mixed"))
+                        for pr in precs} - {"fp64"} | ({"fp64"} if any(pr.startswith("fp64") for pr in precs) else set()))
+        degrees = sorted({p for _, p, _ in wl})
+        tuning = autotune.tune(ctx, degrees=degrees, kinds=kinds)
     arms = {pr: time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, pr, flush, stream, ws, local)
             for pr in precs}
     prec = precs[0]
@@ -283,6 +292,8 @@ def main():
                       "l2": "flushed between cases (256 MiB write)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
            "gpu_launches": sum(launches_per_action(f) for f, _, _ in wl) * args.steps * len(precs),
            "clocks": head["clocks"], "roofline": roofline, "per_case": head["per_case"],
+           "autotune": ({k: {str(p): v["best"] for p, v in per.items()} for k, per in tuning.items()}
+                        if tuning else None),
            "arms": {pr: {"value": dofs_step * ws / (arms[pr]["ms_step"] * 1e-3), "ms_per_step": arms[pr]["ms_step"],
                          "clocks": arms[pr]["clocks"], "speedup_vs_fp64": (arms["fp64"]["ms_step"] / arms[pr]["ms_step"]
                                                                            if "fp64" in arms else None),

@@ -223,6 +223,18 @@ sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_for
                                       const sfx_space* space, const sfx_qdata* qdata, const double* x, double* y,
                                       int nrhs, int accumulate, sfx_precision prec, void* stream);
 
+/* ------------------------------------------------------------------ tuning */
+
+/* Cells per CTA of the scalar action kernels, per kernel kind and degree
+ * (1..8): 0 restores the built-in choice.  Kinds: 0 = FP64 (capped at the
+ * 256-thread team limit, 256 / (p+1)^2), 1 = split precision with on-the-fly
+ * geometry, 2 = split precision with stored factors.  Every kernel reduces
+ * the value further if its shared memory would not fit.  Values are chosen by
+ * measurement (paper_1711_02473_gb300/autotune.py) and are process-wide.
+ * Errors: SFX_ERR_ARG. */
+sfx_status sfx_tune_set_cells_per_cta(int kernel, int degree, int cells);
+sfx_status sfx_tune_get_cells_per_cta(int kernel, int degree, int* cells);
+
 /* ------------------------------------------------------ batched execution */
 
 /* A plan for repeated actions on a p-adaptive DQ mesh: cell c carries

@@ -33,7 +33,8 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices",
            "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy",
            "sfx_padaptive_action_noalloc", "sfx_qdata_create", "sfx_qdata_destroy",
-           "sfx_assemble_action_stored"]
+           "sfx_assemble_action_stored", "sfx_tune_set_cells_per_cta", "sfx_tune_get_cells_per_cta"]
+TUNE_KERNEL = {"fp64": 0, "mixed": 1, "mixed_stored": 2}
 QDATA = {"fp64": 1, "fp32": 2, "both": 3}
 EXEC = {"graph": 0, "per_launch": 1}
 
@@ -92,6 +93,8 @@ def lib():
         L.sfx_qdata_destroy.argtypes = [P]
         L.sfx_qdata_destroy.restype = None
         L.sfx_assemble_action_stored.argtypes = [P, i, C.POINTER(_Params), P, P, P, P, i, i, i, P]
+        L.sfx_tune_set_cells_per_cta.argtypes = [i, i, i]
+        L.sfx_tune_get_cells_per_cta.argtypes = [i, i, C.POINTER(i)]
         L.sfx_padaptive_action_noalloc.argtypes = [P, P, P, P, i, C.POINTER(_Params), P, P, i, P]
         for name in EXPORTS:
             f = getattr(L, name)
@@ -255,6 +258,16 @@ def sfx_assemble_cell_matrices(ctx, form, space, cell_begin, cell_end, A, precis
                                             _dptr(A, "float64"), PRECISION[precision], ALGO[algo],
                                             _stream(stream)), "sfx_assemble_cell_matrices")
     return A
+
+
+def sfx_tune_set_cells_per_cta(kernel, degree, cells):
+    _check(lib().sfx_tune_set_cells_per_cta(TUNE_KERNEL[kernel], degree, cells), "sfx_tune_set_cells_per_cta")
+
+
+def sfx_tune_get_cells_per_cta(kernel, degree):
+    v = C.c_int()
+    _check(lib().sfx_tune_get_cells_per_cta(TUNE_KERNEL[kernel], degree, C.byref(v)), "sfx_tune_get_cells_per_cta")
+    return v.value
 
 
 class QData:

@@ -1,0 +1,111 @@
+"""Autotuner for the cells-per-CTA of the scalar action kernels.
+
+For each kernel kind ("fp64", "mixed", "mixed_stored") and degree it times
+the Q_p Laplace action on a tuning mesh for every candidate value (median of a
+few CUDA-event timings, L2 flushed between runs), keeps the fastest, and sets
+it in the library with sfx_tune_set_cells_per_cta.  The table can be saved per
+GPU name and re-applied.  Only launch geometry changes: results are the same
+sums (the per-cell arithmetic does not depend on how many cells share a CTA).
+"""
+import json
+import os
+
+import numpy as np
+
+from . import (Context, Mesh, QData, Space, TUNE_KERNEL, sfx_assemble_action, sfx_assemble_action_stored,
+               sfx_tune_set_cells_per_cta)
+from . import inputs
+
+_BUILD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build")
+
+
+def candidates(kind, p):
+    n2 = (p + 1) ** 2
+    if kind == "fp64":
+        top = max(1, 256 // n2)
+        return sorted({max(1, top // d) for d in (1, 2, 3, 4, 6)})
+    return [2, 4, 6, 8, 12, 16, 24, 32] if p <= 2 else [1, 2, 3, 4, 6, 8, 12, 16]
+
+
+def _time(torch, fn, reps, flush):
+    fn()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims=(32, 32, 32), reps=3):
+    """Returns {kind: {p: {"best": cb, "ms": {cb: t}}}} and applies the winners."""
+    import torch
+    mesh = Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device="cuda")
+    table = {}
+    for p in degrees:
+        sp = Space(mesh, "Q", p)
+        x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
+        y = torch.empty_like(x)
+        qd = QData(ctx, sp, "fp32") if "mixed_stored" in kinds else None
+        for kind in kinds:
+            if kind == "fp64":
+                fn = lambda: sfx_assemble_action(ctx, "laplace", sp, x, y)
+            elif kind == "mixed":
+                fn = lambda: sfx_assemble_action(ctx, "laplace", sp, x, y, precision="tf32x3")
+            else:
+                fn = lambda: sfx_assemble_action_stored(ctx, "laplace", sp, qd, x, y, precision="tf32x3")
+            res = {}
+            for cb in candidates(kind, p):
+                sfx_tune_set_cells_per_cta(kind, p, cb)
+                res[cb] = _time(torch, fn, reps, flush)
+            best = min(res, key=res.get)
+            sfx_tune_set_cells_per_cta(kind, p, best)
+            table.setdefault(kind, {})[p] = {"best": best, "ms": {str(k): round(v, 4) for k, v in res.items()}}
+        if qd is not None:
+            qd.close()
+        del x, y, sp
+    return table
+
+
+def apply(table):
+    for kind, per in table.items():
+        for p, rec in per.items():
+            sfx_tune_set_cells_per_cta(kind, int(p), int(rec["best"]))
+
+
+def cache_path(gpu_name):
+    safe = "".join(c if c.isalnum() else "_" for c in gpu_name)
+    return os.path.join(_BUILD, "autotune_%s.json" % safe)
+
+
+def save(table, gpu_name):
+    os.makedirs(_BUILD, exist_ok=True)
+    with open(cache_path(gpu_name), "w") as f:
+        json.dump({"gpu": gpu_name, "table": table}, f, indent=1)
+
+
+def load(gpu_name):
+    path = cache_path(gpu_name)
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)["table"]
+
+
+def ensure(ctx, gpu_name, **kw):
+    """Load the cached table for this GPU, or tune and cache it; apply it."""
+    table = load(gpu_name)
+    if table is None:
+        table = tune(ctx, **kw)
+        save(table, gpu_name)
+    else:
+        apply(table)
+    return table
+
+
+__all__ = ["tune", "apply", "save", "load", "ensure", "candidates", "TUNE_KERNEL", "Context"]

@@ -31,9 +31,10 @@ constexpr int cb_of() {
 template <int N>
 __device__ __forceinline__ void run_tile(int form, const ActArgs& a, int64_t nc, double* sm) {
   switch (form) {
-    case SFX_MASS: scalar_tile_fp64<N, true, SFX_MASS>(a, nc, 0, cb_of<N, SFX_MASS>(), sm); break;
-    case SFX_LAPLACE: scalar_tile_fp64<N, true, SFX_LAPLACE>(a, nc, 0, cb_of<N, SFX_LAPLACE>(), sm); break;
-    default: scalar_tile_fp64<N, true, SFX_HELMHOLTZ>(a, nc, 0, cb_of<N, SFX_HELMHOLTZ>(), sm); break;
+    // tiles serve every RHS: the factors are staged once per cell (geo_once)
+    case SFX_MASS: scalar_tile_fp64<N, true, SFX_MASS>(a, nc, 0, cb_of<N, SFX_MASS>(), sm, true); break;
+    case SFX_LAPLACE: scalar_tile_fp64<N, true, SFX_LAPLACE>(a, nc, 0, cb_of<N, SFX_LAPLACE>(), sm, true); break;
+    default: scalar_tile_fp64<N, true, SFX_HELMHOLTZ>(a, nc, 0, cb_of<N, SFX_HELMHOLTZ>(), sm, true); break;
   }
 }
 

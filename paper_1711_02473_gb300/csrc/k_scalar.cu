@@ -9,26 +9,30 @@ SFX_DEFINE_TAB_UPLOAD(upload_tab_scalar)
 namespace {
 
 template <int N, bool DQ, int FORM, bool STORED>
-__global__ void __launch_bounds__(256) k_action_scalar_fp64(const ActArgs a, const int64_t ncell_total) {
+__global__ void __launch_bounds__(256) k_action_scalar_fp64(const ActArgs a, const int64_t ncell_total,
+                                                           const bool geo_once) {
   extern __shared__ double sm[];
   const int cb = blockDim.x / (N * N);
-  scalar_tile_fp64<N, DQ, FORM, STORED>(a, ncell_total, (int64_t)blockIdx.x * cb, cb, sm);
+  scalar_tile_fp64<N, DQ, FORM, STORED>(a, ncell_total, (int64_t)blockIdx.x * cb, cb, sm, geo_once);
 }
 
 template <int N, bool DQ, int FORM>
 int launch_fp64(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   using Sh = ScalarShape<N, FORM>;
-  const size_t per_team = Sh::TEAM * sizeof(double);
+  // several RHS: stage the factors once per cell; one RHS: form them at the point
+  const bool geo_once = a.r1 - a.r0 > 1;
+  const size_t per_team = (size_t)Sh::team_doubles(geo_once) * sizeof(double);
   const size_t fixed = (Sh::N3 + 16) * sizeof(double);
   const size_t budget = 200 * 1024;
-  int cb = Sh::MAXCB;
+  int cb = tuned_cells_per_cta(SFX_TUNE_SCALAR_FP64, N - 1, Sh::MAXCB);
+  if (cb > Sh::MAXCB) cb = Sh::MAXCB;  // one team of N^2 threads per cell, <= 256 threads
   while (cb > 1 && fixed + cb * per_team > budget) --cb;
   const size_t smem = fixed + cb * per_team;
   auto kern = a.qd64 ? k_action_scalar_fp64<N, DQ, FORM, true> : k_action_scalar_fp64<N, DQ, FORM, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int64_t grid = (a.ncells + cb - 1) / cb;
-  kern<<<(unsigned)grid, cb * Sh::N2, smem, s>>>(a, ncell_total);
+  kern<<<(unsigned)grid, cb * Sh::N2, smem, s>>>(a, ncell_total, geo_once);
   return (int)cudaGetLastError();
 }
 

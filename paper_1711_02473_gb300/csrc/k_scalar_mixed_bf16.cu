@@ -11,18 +11,20 @@ namespace {
 template <int N, bool DQ, int FORM, int PREC>
 int launch_mixed(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   using Sh = MixedShape<N, FORM>;
-  const size_t fixed = 2 * sizeof(TabF) + (Sh::N3 + 16) * 8;
+  const bool stored = a.qd32 != nullptr;
+  const bool geo_once = a.nrhs > 1;
   const size_t budget = 200 * 1024;
-  int cb = (int)((budget - fixed) / Sh::BYTES_PER_CELL);
-  const int want = (N <= 3) ? 32 : 16;  // enough fibers for dense tiles
-  if (cb > want) cb = want;
+  // cells per CTA: the autotuned value, else enough fibers for dense tiles
+  int cb = tuned_cells_per_cta(stored ? SFX_TUNE_SCALAR_MIXED_STORED : SFX_TUNE_SCALAR_MIXED, N - 1,
+                               (N <= 3) ? 32 : 16);
   if (cb < 1) cb = 1;
-  const size_t smem = fixed + (size_t)cb * Sh::CELLD * 8 + (size_t)cb * Sh::CELLF * 4 + (size_t)cb * 8 + 16;
-  auto kern = a.qd32 ? k_action_scalar_mixed<N, DQ, FORM, PREC, true> : k_action_scalar_mixed<N, DQ, FORM, PREC, false>;
+  while (cb > 1 && Sh::bytes(cb, geo_once, stored) > budget) --cb;
+  const size_t smem = Sh::bytes(cb, geo_once, stored);
+  auto kern = stored ? k_action_scalar_mixed<N, DQ, FORM, PREC, true> : k_action_scalar_mixed<N, DQ, FORM, PREC, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int64_t grid = (a.ncells + cb - 1) / cb;
-  kern<<<(unsigned)grid, kThreads, smem, s>>>(a, ncell_total, cb);
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(a, ncell_total, cb, geo_once);
   return (int)cudaGetLastError();
 }
 

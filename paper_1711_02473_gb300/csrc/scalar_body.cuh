@@ -15,7 +15,12 @@
 //      flux f = P grad u (Laplace) and/or w S u (mass);
 //   5. transposed contractions Dq^T then B^T;
 //   6. add b^K into y through the map (conflict-free within one colour).
-// Geometry is computed once per cell and reused for all right-hand sides.
+// Where the factors P and w S come from:
+//   - geo_once (several right-hand sides): computed once per cell into shared
+//     memory and reused for every RHS;
+//   - otherwise at the point, when the flux is formed (no shared copy: a
+//     smaller footprint, more resident warps);
+//   - STORED: read from sfx_qdata instead of computed.
 #pragma once
 #include "kern_common.cuh"
 
@@ -27,18 +32,49 @@ struct ScalarShape {
   static constexpr int N2 = N * N, N3 = N * N * N;
   static constexpr bool LAP = FORM != SFX_MASS;
   static constexpr bool MAS = FORM != SFX_LAPLACE;
-  // per-team shared doubles: U, G0..G2 (LAP), K[6] (LAP), WS (MAS), corners, Jc
-  static constexpr int TEAM = N3 + (LAP ? 3 * N3 + 6 * N3 : 0) + (MAS ? N3 : 0) + 24 + 9 * N2 + 1;
+  // per-team shared doubles: U, G0..G2 (LAP), corners, Jacobian columns, flag
+  static constexpr int LEAN = N3 + (LAP ? 3 * N3 : 0) + 24 + 9 * N2 + 1;
+  // plus the staged factors K[6] (LAP) and WS (MAS) when geo_once
+  static constexpr int FULL = LEAN + (LAP ? 6 * N3 : 0) + (MAS ? N3 : 0);
+  static constexpr int TEAM = FULL;
   static constexpr int MAXCB = (256 / N2) > 0 ? 256 / N2 : 1;
+  static constexpr int team_doubles(bool geo_once) { return geo_once ? FULL : LEAN; }
 };
+
+// The factors at point qp of a cell: P (6 symmetric entries, scaled by alpha)
+// and w S (scaled by beta), from the Jacobian column tables.  Returns S.
+template <int N, bool LAP, bool MAS>
+__device__ __forceinline__ double point_factors(const double (*Jc)[N * N][3], const double* W3, int qp,
+                                                double alpha, double beta, double* K, double* ws_mass) {
+  constexpr int N2 = N * N;
+  const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
+  const double* c0 = Jc[0][q2 * N + q3];
+  const double* c1 = Jc[1][q1 * N + q3];
+  const double* c2 = Jc[2][q1 * N + q2];
+  double r0[3];
+  cross3(c1, c2, r0);
+  const double S = dot3(c0, r0);
+  if (LAP) {
+    double r1[3], r2[3];
+    cross3(c2, c0, r1);
+    cross3(c0, c1, r2);
+    const double ws = alpha * W3[qp] / S;  // P = w S G G^T = (w/S) adj(J) adj(J)^T
+    K[0] = ws * dot3(r0, r0);
+    K[1] = ws * dot3(r1, r1);
+    K[2] = ws * dot3(r2, r2);
+    K[3] = ws * dot3(r0, r1);
+    K[4] = ws * dot3(r0, r2);
+    K[5] = ws * dot3(r1, r2);
+  }
+  if (MAS) *ws_mass = beta * W3[qp] * S;
+  return S;
+}
 
 // One tile: the cb cells of slots slot0 .. slot0+cb-1, one team of N^2 threads
 // per cell (threads of teams >= cb idle but take part in the barriers).
-// STORED: the geometric factors come from a.qd64 (sfx_qdata) instead of
-// being computed from the coordinates.
 template <int N, bool DQ, int FORM, bool STORED = false>
 __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t ncell_total, const int64_t slot0,
-                                                 const int cb, double* sm) {
+                                                 const int cb, double* sm, const bool geo_once) {
   using Sh = ScalarShape<N, FORM>;
   constexpr int N2 = Sh::N2, N3 = Sh::N3;
   constexpr bool LAP = Sh::LAP, MAS = Sh::MAS;
@@ -52,16 +88,17 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
   const int t = threadIdx.x - team_raw * N2;
   double* W3 = sm;              // 3D quadrature weights
   double* xq = sm + N3;         // 1D points (padded to 16)
-  double* base = sm + N3 + 16 + team * Sh::TEAM;
+  double* base = sm + N3 + 16 + team * Sh::team_doubles(geo_once);
   double* U = base;
   double* G0 = U + N3;
   double* G1 = G0 + N3;
   double* G2 = G1 + N3;
-  double* K = LAP ? G2 + N3 : U + N3;  // K[c][qp], c = 00,11,22,01,02,12
-  double* WS = K + (LAP ? 6 * N3 : 0);
-  double(*X)[3] = reinterpret_cast<double(*)[3]>(WS + (MAS ? N3 : 0));
-  double(*Jc)[N2][3] = reinterpret_cast<double(*)[N2][3]>(&X[8][0]);
-  int* bad = reinterpret_cast<int*>(&Jc[3][0][0]);
+  double* X0 = LAP ? G2 + N3 : U + N3;
+  double(*X)[3] = reinterpret_cast<double(*)[3]>(X0);
+  double(*Jc)[N2][3] = reinterpret_cast<double(*)[N2][3]>(X0 + 24);
+  int* bad = reinterpret_cast<int*>(X0 + 24 + 9 * N2);
+  double* K = X0 + 24 + 9 * N2 + 1;                  // K[c][qp] (geo_once only)
+  double* WS = K + (LAP ? 6 * N3 : 0);               // WS[qp]   (geo_once only)
 
   for (int i = threadIdx.x; i < N3; i += blockDim.x) W3[i] = T.w[i / N2] * T.w[(i / N) % N] * T.w[i % N];
   if (threadIdx.x < N) xq[threadIdx.x] = T.x[threadIdx.x];
@@ -72,62 +109,42 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
   if (member && t == 0) *bad = 0;
   const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
   const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
-  if (STORED) {
-    // stored factors: K = alpha P, WS = beta w S at the thread's points
+  const double* qd = STORED ? a.qd64 + (int64_t)cell * 7 * N3 : nullptr;
+  if (!STORED) {
+    for (int c = member ? t : 8; c < 8; c += N2) {  // a team may have fewer than 8 threads (p = 1)
+      if (active) {
+        const int v = a.vmap[(int64_t)cell * 8 + c];
+        X[c][0] = a.xyz[(int64_t)v * 3 + 0];
+        X[c][1] = a.xyz[(int64_t)v * 3 + 1];
+        X[c][2] = a.xyz[(int64_t)v * 3 + 2];
+      } else {  // idle team: unit cube keeps the arithmetic finite
+        X[c][0] = (c >> 2) & 1; X[c][1] = (c >> 1) & 1; X[c][2] = c & 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (!STORED && member) jacobian_columns<N>(X, xq, Jc, t);
+  __syncthreads();
+  if (geo_once) {
+    // factors at the thread's points qp = k*N2 + t, staged for all RHS
 #pragma unroll 1
     for (int k = 0; k < (member ? N : 0); ++k) {
       const int qp = k * N2 + t;
-      const double* qd = a.qd64 + (int64_t)cell * 7 * N3;
-      if (LAP)
-        for (int j = 0; j < 6; ++j) K[j * N3 + qp] = active ? alpha * qd[j * N3 + qp] : 0.0;
-      if (MAS) WS[qp] = active ? beta * qd[6 * N3 + qp] : 0.0;
+      if (STORED) {
+        if (LAP)
+          for (int j = 0; j < 6; ++j) K[j * N3 + qp] = active ? alpha * qd[j * N3 + qp] : 0.0;
+        if (MAS) WS[qp] = active ? beta * qd[6 * N3 + qp] : 0.0;
+      } else {
+        double kk[6], wsm = 0.0;
+        const double S = point_factors<N, LAP, MAS>(Jc, W3, qp, alpha, beta, kk, &wsm);
+        if (!(S > 0.0)) *bad = 1;
+        if (LAP)
+          for (int j = 0; j < 6; ++j) K[j * N3 + qp] = kk[j];
+        if (MAS) WS[qp] = wsm;
+      }
     }
     __syncthreads();
-  } else {
-  for (int c = member ? t : 8; c < 8; c += N2) {  // a team may have fewer than 8 threads (p = 1)
-    if (active) {
-      const int v = a.vmap[(int64_t)cell * 8 + c];
-      X[c][0] = a.xyz[(int64_t)v * 3 + 0];
-      X[c][1] = a.xyz[(int64_t)v * 3 + 1];
-      X[c][2] = a.xyz[(int64_t)v * 3 + 2];
-    } else {  // idle team: unit cube keeps the arithmetic finite
-      X[c][0] = (c >> 2) & 1; X[c][1] = (c >> 1) & 1; X[c][2] = c & 1;
-    }
   }
-  __syncthreads();
-  if (member) jacobian_columns<N>(X, xq, Jc, t);
-  __syncthreads();
-
-  // geometric factors at the thread's points qp = k*N2 + t, k = q1
-#pragma unroll 1
-  for (int k = 0; k < (member ? N : 0); ++k) {
-    const int qp = k * N2 + t;
-    const int q2 = t / N, q3 = t - (t / N) * N;
-    const double* c0 = Jc[0][t];
-    const double* c1 = Jc[1][k * N + q3];
-    const double* c2 = Jc[2][k * N + q2];
-    double r0[3];
-    cross3(c1, c2, r0);
-    const double S = dot3(c0, r0);
-    if (!(S > 0.0)) *bad = 1;
-    if (LAP) {
-      double r1[3], r2[3];
-      cross3(c2, c0, r1);
-      cross3(c0, c1, r2);
-      const double ws = alpha * W3[qp] / S;  // P = w S G G^T = (w/S) adj(J) adj(J)^T
-      K[0 * N3 + qp] = ws * dot3(r0, r0);
-      K[1 * N3 + qp] = ws * dot3(r1, r1);
-      K[2 * N3 + qp] = ws * dot3(r2, r2);
-      K[3 * N3 + qp] = ws * dot3(r0, r1);
-      K[4 * N3 + qp] = ws * dot3(r0, r2);
-      K[5 * N3 + qp] = ws * dot3(r1, r2);
-    }
-    if (MAS) WS[qp] = beta * W3[qp] * S;
-  }
-  __syncthreads();
-  }
-  const bool ok = active && !*bad;
-  if (active && *bad && t == 0) set_flag(a.status, SFX_DEV_INVERTED);
   const int tl = member ? t : N3;  // first index of this thread's strided loops (none for non-members)
 
   // dof of local l: the space's map, or cell offset + l for p-adaptive DQ
@@ -136,7 +153,7 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
   auto dof = [&](int l) -> int64_t { return mrow ? (int64_t)mrow[l] : doff + l; };
 #pragma unroll 1
   for (int r = a.r0; r < a.r1; ++r) {
-    for (int l = tl; l < N3; l += N2) U[l] = ok ? a.x[dof(l) * a.nrhs + r] : 0.0;
+    for (int l = tl; l < N3; l += N2) U[l] = active ? a.x[dof(l) * a.nrhs + r] : 0.0;
     __syncthreads();
     if (!DQ) {
       if (member) contract<N, N, N, 0, N, false, false, kMaxN>(U, U, T.Bc, t);
@@ -157,15 +174,26 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
 #pragma unroll 1
     for (int k = 0; k < (member ? N : 0); ++k) {
       const int qp = k * N2 + t;
+      double kk[6] = {0, 0, 0, 0, 0, 0}, wsm = 0.0;
+      if (geo_once) {
+        if (LAP)
+          for (int j = 0; j < 6; ++j) kk[j] = K[j * N3 + qp];
+        if (MAS) wsm = WS[qp];
+      } else if (STORED) {
+        if (LAP)
+          for (int j = 0; j < 6; ++j) kk[j] = active ? alpha * qd[j * N3 + qp] : 0.0;
+        if (MAS) wsm = active ? beta * qd[6 * N3 + qp] : 0.0;
+      } else {
+        const double S = point_factors<N, LAP, MAS>(Jc, W3, qp, alpha, beta, kk, &wsm);
+        if (!(S > 0.0)) *bad = 1;
+      }
       if (LAP) {
         const double g0 = G0[qp], g1 = G1[qp], g2 = G2[qp];
-        const double k00 = K[qp], k11 = K[N3 + qp], k22 = K[2 * N3 + qp];
-        const double k01 = K[3 * N3 + qp], k02 = K[4 * N3 + qp], k12 = K[5 * N3 + qp];
-        G0[qp] = k00 * g0 + k01 * g1 + k02 * g2;
-        G1[qp] = k01 * g0 + k11 * g1 + k12 * g2;
-        G2[qp] = k02 * g0 + k12 * g1 + k22 * g2;
+        G0[qp] = kk[0] * g0 + kk[3] * g1 + kk[4] * g2;
+        G1[qp] = kk[3] * g0 + kk[1] * g1 + kk[5] * g2;
+        G2[qp] = kk[4] * g0 + kk[5] * g1 + kk[2] * g2;
       }
-      if (MAS) U[qp] = WS[qp] * U[qp];
+      if (MAS) U[qp] = wsm * U[qp];
     }
     __syncthreads();
     if (LAP) {
@@ -184,7 +212,9 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
       if (member) contract<N, N, N, 2, N, true, false, kMaxN>(U, U, T.Bc, t);
       __syncthreads();
     }
-    if (ok) {  // ok implies member
+    // the inverted-cell flag is final here (set while forming the factors)
+    const bool ok = active && !*bad;
+    if (ok) {
       if (a.cell_vectors) {
         for (int l = t; l < N3; l += N2) a.y[(slot * N3 + l) * a.nrhs + r] = U[l];
       } else {
@@ -193,6 +223,7 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
     } else if (active && a.cell_vectors) {
       for (int l = t; l < N3; l += N2) a.y[(slot * N3 + l) * a.nrhs + r] = 0.0;
     }
+    if (r == a.r0 && active && *bad && t == 0) set_flag(a.status, SFX_DEV_INVERTED);
     __syncthreads();
   }
 }

@@ -173,36 +173,72 @@ struct MixedShape {
   static constexpr int N2 = N * N, N3 = N2 * N;
   static constexpr bool LAP = FORM != SFX_MASS;
   static constexpr bool MAS = FORM != SFX_LAPLACE;
-  // per-cell floats: U, G0..G2 (LAP), K[6] (LAP), WS (MAS)
-  static constexpr int CELLF = N3 + (LAP ? 9 * N3 : 0) + (MAS ? N3 : 0);
-  // per-cell doubles: corners (24) + Jacobian column tables (9 N^2)
-  static constexpr int CELLD = 24 + 9 * N2;
-  static constexpr int BYTES_PER_CELL = CELLF * 4 + CELLD * 8 + 4;
+  // per-cell floats: U, G0..G2 (LAP); plus the staged factors K[6] (LAP) and
+  // WS (MAS) when geo_once
+  static constexpr int cellf(bool geo_once) {
+    return N3 + (LAP ? 3 * N3 : 0) + (geo_once ? (LAP ? 6 * N3 : 0) + (MAS ? N3 : 0) : 0);
+  }
+  // per-cell doubles: corners (24) + Jacobian column tables (9 N^2), on-the-fly geometry only
+  static constexpr int celld(bool stored) { return stored ? 0 : 24 + 9 * N2; }
+  static constexpr size_t fixed_bytes() { return 2 * sizeof(TabF) + (N3 + 16) * 8; }
+  static constexpr size_t bytes(int cb, bool geo_once, bool stored) {
+    return fixed_bytes() + (size_t)cb * celld(stored) * 8 + (size_t)cb * cellf(geo_once) * 4 + (size_t)cb * 8 + 16;
+  }
 };
 
-// STORED: the FP32 geometric factors come from a.qd32 (sfx_qdata) and no
-// FP64 geometry runs in the kernel.
+// Factors at point qp of cell c from the FP64 Jacobian column tables, rounded
+// to FP32 after the FP64 arithmetic.  Returns S.
+template <int N, bool LAP, bool MAS>
+__device__ __forceinline__ double mixed_point_factors(const double* cdc, const double* W3, int qp, double alpha,
+                                                      double beta, float* K, float* wsm) {
+  constexpr int N2 = N * N;
+  const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
+  const double(*Jc)[N2][3] = reinterpret_cast<const double(*)[N2][3]>(cdc + 24);
+  const double* c0 = Jc[0][q2 * N + q3];
+  const double* c1 = Jc[1][q1 * N + q3];
+  const double* c2 = Jc[2][q1 * N + q2];
+  double r0[3];
+  cross3(c1, c2, r0);
+  const double S = dot3(c0, r0);
+  if (LAP) {
+    double r1[3], r2[3];
+    cross3(c2, c0, r1);
+    cross3(c0, c1, r2);
+    const double ws = alpha * W3[qp] / S;
+    K[0] = (float)(ws * dot3(r0, r0));
+    K[1] = (float)(ws * dot3(r1, r1));
+    K[2] = (float)(ws * dot3(r2, r2));
+    K[3] = (float)(ws * dot3(r0, r1));
+    K[4] = (float)(ws * dot3(r0, r2));
+    K[5] = (float)(ws * dot3(r1, r2));
+  }
+  if (MAS) *wsm = (float)(beta * W3[qp] * S);
+  return S;
+}
+
+// STORED: the FP32 factors come from a.qd32 (sfx_qdata) and no FP64 geometry
+// runs in the kernel.  geo_once: stage the factors once per cell for all RHS.
 template <int N, bool DQ, int FORM, int PREC, bool STORED>
 __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs a, const int64_t ncell_total,
-                                                                  const int cb) {
+                                                                  const int cb, const bool geo_once) {
   using Sh = MixedShape<N, FORM>;
   constexpr int N2 = Sh::N2, N3 = Sh::N3;
   constexpr bool LAP = Sh::LAP, MAS = Sh::MAS;
   const Tab1D& T = c_tab[N - 1];
   extern __shared__ double smd[];
-  // layout: [tables: 4 TabF][W3: N3 doubles][xq: 16 doubles][cells: doubles][cells: floats][flags]
+  // layout: [tables: 2 TabF][W3: N3 doubles][xq: 16 doubles][cells: doubles][cells: floats][flags]
   TabF* tabs = reinterpret_cast<TabF*>(smd);  // 0: B, 1: Dq
   double* W3 = smd + (2 * sizeof(TabF)) / 8;
   double* xq = W3 + N3;
-  double* cd = xq + 16;                       // per-cell doubles
-  float* cf = reinterpret_cast<float*>(cd + (size_t)cb * Sh::CELLD);
+  double* cd = xq + 16;                       // per-cell doubles (on-the-fly geometry)
+  float* cf = reinterpret_cast<float*>(cd + (size_t)cb * Sh::celld(STORED));
   float* U = cf;
   float* G0 = U + cb * N3;
   float* G1 = G0 + cb * N3;
   float* G2 = G1 + cb * N3;
-  float* K = LAP ? G2 + cb * N3 : U + cb * N3;  // K[j][cell][qp]
-  float* WS = K + (LAP ? 6 * cb * N3 : 0);
-  int* flags = reinterpret_cast<int*>(WS + (MAS ? cb * N3 : 0));  // per cell: cell id or -1, bad
+  float* K = (LAP ? G2 : U) + cb * N3;        // K[j][cell][qp]   (geo_once only)
+  float* WS = K + (LAP ? 6 * cb * N3 : 0);   // WS[cell][qp]     (geo_once only)
+  int* flags = reinterpret_cast<int*>(cf + (size_t)cb * Sh::cellf(geo_once));  // per cell: id or -1, bad
 
   const int tid = threadIdx.x;
   for (int i = tid; i < 16 * 16; i += kThreads) {
@@ -221,70 +257,50 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
   __syncthreads();
   const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
   const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
-  if (STORED) {
-    const float fa = (float)alpha, fb = (float)beta;
+  const float fa = (float)alpha, fb = (float)beta;
+  if (!STORED) {
+    for (int i = tid; i < cb * 24; i += kThreads) {
+      const int c = i / 24, v = (i % 24) / 3, k = i % 3;
+      const int cell = flags[2 * c];
+      double* X = cd + (size_t)c * Sh::celld(false);
+      X[v * 3 + k] = cell >= 0 ? a.xyz[(int64_t)a.vmap[(int64_t)cell * 8 + v] * 3 + k] : (double)((v >> (2 - k)) & 1);
+    }
+    __syncthreads();
+    for (int i = tid; i < cb * N2; i += kThreads) {
+      const int c = i / N2, t = i - c * N2;
+      double* X = cd + (size_t)c * Sh::celld(false);
+      jacobian_columns<N>(reinterpret_cast<const double(*)[3]>(X), xq, reinterpret_cast<double(*)[N2][3]>(X + 24), t);
+    }
+    __syncthreads();
+  }
+  if (geo_once) {
     for (int i = tid; i < cb * N3; i += kThreads) {
       const int c = i / N3, qp = i - c * N3;
       const int cell = flags[2 * c];
-      const float* qd = a.qd32 + (int64_t)(cell >= 0 ? cell : 0) * 7 * N3;
+      float kk[6], wsm = 0.f;
+      if (STORED) {
+        const float* qd = a.qd32 + (int64_t)(cell >= 0 ? cell : 0) * 7 * N3;
+        if (LAP)
+          for (int j = 0; j < 6; ++j) kk[j] = cell >= 0 ? fa * qd[j * N3 + qp] : 0.f;
+        if (MAS) wsm = cell >= 0 ? fb * qd[6 * N3 + qp] : 0.f;
+      } else {
+        const double S = mixed_point_factors<N, LAP, MAS>(cd + (size_t)c * Sh::celld(false), W3, qp, alpha, beta,
+                                                          kk, &wsm);
+        if (!(S > 0.0)) flags[2 * c + 1] = 1;
+      }
       if (LAP)
-        for (int j = 0; j < 6; ++j) K[(j * cb + c) * N3 + qp] = cell >= 0 ? fa * qd[j * N3 + qp] : 0.f;
-      if (MAS) WS[c * N3 + qp] = cell >= 0 ? fb * qd[6 * N3 + qp] : 0.f;
+        for (int j = 0; j < 6; ++j) K[(j * cb + c) * N3 + qp] = kk[j];
+      if (MAS) WS[c * N3 + qp] = wsm;
     }
     __syncthreads();
-  } else {
-  // corners
-  for (int i = tid; i < cb * 24; i += kThreads) {
-    const int c = i / 24, v = (i % 24) / 3, k = i % 3;
-    const int cell = flags[2 * c];
-    double* X = cd + (size_t)c * Sh::CELLD;
-    X[v * 3 + k] = cell >= 0 ? a.xyz[(int64_t)a.vmap[(int64_t)cell * 8 + v] * 3 + k] : (double)((v >> (2 - k)) & 1);
   }
-  __syncthreads();
-  for (int i = tid; i < cb * N2; i += kThreads) {
-    const int c = i / N2, t = i - c * N2;
-    double* X = cd + (size_t)c * Sh::CELLD;
-    jacobian_columns<N>(reinterpret_cast<const double(*)[3]>(X), xq, reinterpret_cast<double(*)[N2][3]>(X + 24), t);
-  }
-  __syncthreads();
-  // geometric factors in FP64, stored rounded to FP32
-  for (int i = tid; i < cb * N3; i += kThreads) {
-    const int c = i / N3, qp = i - c * N3;
-    const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
-    const double(*Jc)[N2][3] = reinterpret_cast<const double(*)[N2][3]>(cd + (size_t)c * Sh::CELLD + 24);
-    const double* c0 = Jc[0][q2 * N + q3];
-    const double* c1 = Jc[1][q1 * N + q3];
-    const double* c2 = Jc[2][q1 * N + q2];
-    double r0[3];
-    cross3(c1, c2, r0);
-    const double S = dot3(c0, r0);
-    if (!(S > 0.0)) flags[2 * c + 1] = 1;
-    if (LAP) {
-      double r1[3], r2[3];
-      cross3(c2, c0, r1);
-      cross3(c0, c1, r2);
-      const double ws = alpha * W3[qp] / S;
-      K[(0 * cb + c) * N3 + qp] = (float)(ws * dot3(r0, r0));
-      K[(1 * cb + c) * N3 + qp] = (float)(ws * dot3(r1, r1));
-      K[(2 * cb + c) * N3 + qp] = (float)(ws * dot3(r2, r2));
-      K[(3 * cb + c) * N3 + qp] = (float)(ws * dot3(r0, r1));
-      K[(4 * cb + c) * N3 + qp] = (float)(ws * dot3(r0, r2));
-      K[(5 * cb + c) * N3 + qp] = (float)(ws * dot3(r1, r2));
-    }
-    if (MAS) WS[c * N3 + qp] = (float)(beta * W3[qp] * S);
-  }
-  __syncthreads();
-  for (int c = tid; c < cb; c += kThreads)
-    if (flags[2 * c] >= 0 && flags[2 * c + 1]) set_flag(a.status, SFX_DEV_INVERTED);
 
-  }
 #pragma unroll 1
   for (int r = 0; r < a.nrhs; ++r) {
     for (int i = tid; i < cb * N3; i += kThreads) {
       const int c = i / N3, l = i - c * N3;
       const int cell = flags[2 * c];
-      const bool ok = cell >= 0 && !flags[2 * c + 1];
-      U[i] = ok ? (float)a.x[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r] : 0.f;
+      U[i] = cell >= 0 ? (float)a.x[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r] : 0.f;
     }
     __syncthreads();
     if (!DQ) {
@@ -303,16 +319,31 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
     }
     for (int i = tid; i < cb * N3; i += kThreads) {
       const int c = i / N3, qp = i - c * N3;
+      const int cell = flags[2 * c];
+      float kk[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, wsm = 0.f;
+      if (geo_once) {
+        if (LAP)
+          for (int j = 0; j < 6; ++j) kk[j] = K[(j * cb + c) * N3 + qp];
+        if (MAS) wsm = WS[c * N3 + qp];
+      } else if (STORED) {
+        if (cell >= 0) {
+          const float* qd = a.qd32 + (int64_t)cell * 7 * N3;
+          if (LAP)
+            for (int j = 0; j < 6; ++j) kk[j] = fa * qd[j * N3 + qp];
+          if (MAS) wsm = fb * qd[6 * N3 + qp];
+        }
+      } else {
+        const double S = mixed_point_factors<N, LAP, MAS>(cd + (size_t)c * Sh::celld(false), W3, qp, alpha, beta,
+                                                          kk, &wsm);
+        if (!(S > 0.0)) flags[2 * c + 1] = 1;
+      }
       if (LAP) {
         const float g0 = G0[i], g1 = G1[i], g2 = G2[i];
-        const float k00 = K[(0 * cb + c) * N3 + qp], k11 = K[(1 * cb + c) * N3 + qp];
-        const float k22 = K[(2 * cb + c) * N3 + qp], k01 = K[(3 * cb + c) * N3 + qp];
-        const float k02 = K[(4 * cb + c) * N3 + qp], k12 = K[(5 * cb + c) * N3 + qp];
-        G0[i] = k00 * g0 + k01 * g1 + k02 * g2;
-        G1[i] = k01 * g0 + k11 * g1 + k12 * g2;
-        G2[i] = k02 * g0 + k12 * g1 + k22 * g2;
+        G0[i] = kk[0] * g0 + kk[3] * g1 + kk[4] * g2;
+        G1[i] = kk[3] * g0 + kk[1] * g1 + kk[5] * g2;
+        G2[i] = kk[4] * g0 + kk[5] * g1 + kk[2] * g2;
       }
-      if (MAS) U[i] = WS[i] * U[i];
+      if (MAS) U[i] = wsm * U[i];
     }
     __syncthreads();
     if (LAP) {
@@ -343,6 +374,9 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
         a.y[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r] += (double)U[i];
       }
     }
+    if (r == 0)
+      for (int c = tid; c < cb; c += kThreads)
+        if (flags[2 * c] >= 0 && flags[2 * c + 1]) set_flag(a.status, SFX_DEV_INVERTED);
     __syncthreads();
   }
 }

@@ -215,6 +215,30 @@ int upload_all_tables() {
 }
 }  // namespace sfx
 
+// ------------------------------------------------------------------- tuning
+namespace {
+int g_tune[SFX_TUNE_NKERNEL][kMaxDeg + 1] = {{0}};
+}
+namespace sfx {
+int tuned_cells_per_cta(int kernel, int degree, int fallback) {
+  const int v = (kernel >= 0 && kernel < SFX_TUNE_NKERNEL && degree >= 1 && degree <= kMaxDeg) ? g_tune[kernel][degree] : 0;
+  return v > 0 ? v : fallback;
+}
+}  // namespace sfx
+
+extern "C" sfx_status sfx_tune_set_cells_per_cta(int kernel, int degree, int cells) {
+  if (kernel < 0 || kernel >= SFX_TUNE_NKERNEL || degree < 1 || degree > kMaxDeg || cells < 0 || cells > 64)
+    return SFX_ERR_ARG;
+  g_tune[kernel][degree] = cells;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_tune_get_cells_per_cta(int kernel, int degree, int* cells) {
+  if (kernel < 0 || kernel >= SFX_TUNE_NKERNEL || degree < 1 || degree > kMaxDeg || !cells) return SFX_ERR_ARG;
+  *cells = g_tune[kernel][degree];
+  return SFX_OK;
+}
+
 // ------------------------------------------------------------------ context
 extern "C" sfx_status sfx_ctx_create(int device, sfx_ctx** out) {
   if (!out || device < -1) return SFX_ERR_ARG;

@@ -146,6 +146,11 @@ int batched_launch(const BatchArgs& b, int grid, size_t smem, void* stream);
 int batched_tile_sizes(int* cb_per_degree /*[kMaxDeg+1]*/);
 int launch_qdata(const sfx_space* sp, sfx_qdata* q, uint32_t* status, void* stream);
 
+// Cells per CTA of the action kernels: the autotuner's choice per (kernel,
+// degree), 0 = not tuned (the launcher's default).  Host-side table.
+enum { SFX_TUNE_SCALAR_FP64 = 0, SFX_TUNE_SCALAR_MIXED = 1, SFX_TUNE_SCALAR_MIXED_STORED = 2, SFX_TUNE_NKERNEL = 3 };
+int tuned_cells_per_cta(int kernel, int degree, int fallback);
+
 // Each kernel file keeps its own constant-memory copy of the 1D tables.
 int upload_tab_scalar(const Tab1D* t);
 int upload_tab_scalar_mixed_tf32(const Tab1D* t);
