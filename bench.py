@@ -28,6 +28,12 @@ HELM = (1.0, -1.0, 0.0, 0.0)  # alpha * laplace + beta * mass, beta = -k^2, k = 
 FP64_PEAK_GFLOPS = 1250.0     # nominal GB300 FP64 (FMA pipe), see the design doc
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "DoFs/s of the operator action (config-2 sweep)"
+# DRAM bytes (read + write) per cell of one colour launch, from the ncu captures of
+# the 32^3, p = 8 case (dram__bytes.sum.per_second x gpu__time_duration / 4096
+# cells); the full-size launch processes 8x the cells, and the traffic of these
+# kernels grows in proportion (x, map, y and factors are per cell).
+NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_mixed", "Q", 8): 104.5e6 / 4096,
+                           ("k_action_scalar_fp64", "Q", 8): 106.3e6 / 4096}
 
 
 def parse():
@@ -249,7 +255,7 @@ def main():
         kinds = sorted({("fp64" if pr.startswith("fp64") else ("mixed_stored" if pr.endswith(":stored") else "mixed"))
                         for pr in precs} - {"fp64"} | ({"fp64"} if any(pr.startswith("fp64") for pr in precs) else set()))
         degrees = sorted({p for _, p, _ in wl})
-        tuning = autotune.tune(ctx, degrees=degrees, kinds=kinds)
+        tuning = autotune.ensure(ctx, torch.cuda.get_device_name(local), degrees=degrees, kinds=kinds)
     arms = {pr: time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, pr, flush, stream, ws, local)
             for pr in precs}
     prec = precs[0]
@@ -268,19 +274,24 @@ def main():
     if prec == "fp64":
         fl = flops_per_cell(fam, p, form) * mesh_cells
         achieved = fl / (dom["ms"] * 1e-3) / 1e9
+        tpc = NCU_DRAM_BYTES_PER_CELL.get(("k_action_scalar_fp64", fam, p))
         roofline = {"bound": "alu", "kernel": "k_action_scalar_fp64 %s p=%d %s" % (fam, p, form),
                     "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                    "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                    "traffic": round(tpc * mesh_cells / launches_per_action(fam)) if tpc else None,
                     "note": "FP64 flops per action (all colour launches) / event time; peak = nominal FP64 "
                             "(152 SMs x 4 FP64 flop/clk x 2.07 GHz, of nominal)"}
     else:
         fl = geometry_flops_per_cell(fam, p, form) * mesh_cells
         achieved = fl / (dom["ms"] * 1e-3) / 1e9
+        tpc = NCU_DRAM_BYTES_PER_CELL.get(("k_action_scalar_mixed", fam, p)) if ":" not in prec else None
         roofline = {"bound": "alu", "kernel": "k_action_scalar_mixed %s p=%d %s %s" % (fam, p, form, prec),
                     "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": None,
+                    "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                    "traffic": round(tpc * mesh_cells / launches_per_action(fam)) if tpc else None,
                     "note": "binding resource = FP64 pipe (geometry J, det J, adj J, w/S per point and the "
-                            "FP64 scatter); achieved = those FP64 flops / event time, of nominal"}
+                            "FP64 scatter; ncu: FP64 pipe 81% busy); achieved = those FP64 flops / event time, "
+                            "of nominal; traffic = DRAM bytes per colour launch, scaled from the 32^3 capture"}
 
     out = {"metric": METRIC, "value": value, "unit": "DoF/s",
            "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,

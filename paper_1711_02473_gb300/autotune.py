@@ -97,15 +97,22 @@ def load(gpu_name):
         return json.load(f)["table"]
 
 
-def ensure(ctx, gpu_name, **kw):
-    """Load the cached table for this GPU, or tune and cache it; apply it."""
-    table = load(gpu_name)
-    if table is None:
-        table = tune(ctx, **kw)
+def ensure(ctx, gpu_name, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), **kw):
+    """Apply the cached table for this GPU, tuning (and caching) only the
+    (kind, degree) entries it lacks.  Later runs on the same machine then use
+    identical launch shapes without tuning again."""
+    table = load(gpu_name) or {}
+    table = {k: {int(p): v for p, v in per.items()} for k, per in table.items()}
+    apply(table)
+    missing = [(k, p) for k in kinds for p in degrees if p not in table.get(k, {})]
+    if missing:
+        new = tune(ctx, degrees=sorted({p for _, p in missing}), kinds=sorted({k for k, _ in missing}), **kw)
+        for k, per in new.items():
+            for p, rec in per.items():
+                table.setdefault(k, {})[p] = rec
         save(table, gpu_name)
-    else:
         apply(table)
-    return table
+    return {k: {p: v for p, v in per.items() if p in degrees} for k, per in table.items() if k in kinds}
 
 
 __all__ = ["tune", "apply", "save", "load", "ensure", "candidates", "TUNE_KERNEL", "Context"]

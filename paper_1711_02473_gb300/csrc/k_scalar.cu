@@ -9,7 +9,7 @@ SFX_DEFINE_TAB_UPLOAD(upload_tab_scalar)
 namespace {
 
 template <int N, bool DQ, int FORM, bool STORED>
-__global__ void __launch_bounds__(256) k_action_scalar_fp64(const ActArgs a, const int64_t ncell_total,
+__global__ void __launch_bounds__(256, 2) k_action_scalar_fp64(const ActArgs a, const int64_t ncell_total,
                                                            const bool geo_once) {
   extern __shared__ double sm[];
   const int cb = blockDim.x / (N * N);
