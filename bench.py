@@ -333,11 +333,13 @@ def main():
 
 
 def geometry_flops_per_cell(fam, p, form):
-    """FP64 flops per cell left in the mixed kernel: the per-point geometry
-    (Laplace part 73 flops, mass part 17) plus the FP64 scatter (1 per dof)."""
+    """FP64 flops per cell left in the split-precision kernel: per point the
+    adjugate rows (3 cross products, 27), det J (5), w/S (2) and the scaling of
+    the six factors (6) for the Laplace part -- the six row products run in
+    FP32 -- or det J and w S (17) for mass; plus the FP64 scatter (1 per dof)."""
     n = p + 1
     lap = form != "mass"
-    return ((73 if lap else 17) + 1) * n ** 3
+    return ((40 if lap else 17) + 1) * n ** 3
 
 
 def time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, arm, flush, stream, ws, local):

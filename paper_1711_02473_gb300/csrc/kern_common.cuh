@@ -59,6 +59,35 @@ __device__ __forceinline__ void jacobian_columns(const double (*X)[3], const dou
   }
 }
 
+// Conversions between double and float on the integer pipe (GB300's FP64
+// pipe, which also runs the hardware conversions, is the scarce unit).
+// float -> double is exact: re-bias the exponent, widen the mantissa.  Zero
+// and subnormal floats map to a signed zero (values below 1.2e-38 do not
+// matter here), infinities and NaNs take the hardware path.
+__device__ __forceinline__ double f2d_int(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
+  if (e == 0u) return __longlong_as_double((long long)sgn);
+  if (e == 0xffu) return (double)f;
+  const unsigned long long bits =
+      sgn | ((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+// double -> float, round to nearest even on the 52 -> 23 bit mantissa; a
+// carry out of the mantissa increments the exponent field, as it should.
+// Zero, results that would be subnormal or overflow, and non-finite values
+// take the hardware path.
+__device__ __forceinline__ float d2f_int(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+  if (e <= 0 || e >= 255) return (float)d;
+  const unsigned long long m = b & 0xfffffffffffffull;
+  const unsigned long long r = m + 0x0fffffffull + ((m >> 29) & 1ull);
+  const uint32_t out = ((uint32_t)(b >> 63) << 31) | ((uint32_t)e << 23);
+  return __uint_as_float(out + (uint32_t)(r >> 29));
+}
+
 __device__ __forceinline__ void cross3(const double* u, const double* v, double* w) {
   w[0] = u[1] * v[2] - u[2] * v[1];
   w[1] = u[2] * v[0] - u[0] * v[2];

@@ -6,8 +6,9 @@
 //
 // Same algorithm as k_scalar.cu (Sec. 3.3, Eqs. coeff_eval and form_eval with
 // the sum factorisation of Sec. 3.2).  What changes is where the arithmetic runs:
-//   - J, det J, adj J and the factor P = w S G G^T are computed in FP64, once
-//     per cell, then rounded to FP32;
+//   - J, det J, adj J and the weight scaling w/S are computed in FP64; the
+//     six products of adjugate rows that form P = w S G G^T run in FP32 (they
+//     only feed FP32 factors) and are scaled in FP64 before rounding;
 //   - every 1D contraction (B, Dq and their transposes) is one batched matrix
 //     product per CTA: the table (q x n, padded to 16 x 8k) times the fibers of
 //     all cells held by the CTA (n x (cells*n^2)), on mma.sync with FP32
@@ -186,8 +187,11 @@ struct MixedShape {
   }
 };
 
-// Factors at point qp of cell c from the FP64 Jacobian column tables, rounded
-// to FP32 after the FP64 arithmetic.  Returns S.
+// Factors at point qp of cell c.  J (column tables), the adjugate rows
+// r_k = rows of S J^{-1}, S = det J and the weight scaling w/S are computed in
+// FP64; the six products r_k . r_l, which only feed FP32 factors, run on the
+// FP32 pipe from the rows rounded once to FP32, and are scaled by w/S in FP64
+// before the final rounding.  Returns S.
 template <int N, bool LAP, bool MAS>
 __device__ __forceinline__ double mixed_point_factors(const double* cdc, const double* W3, int qp, double alpha,
                                                       double beta, float* K, float* wsm) {
@@ -205,14 +209,22 @@ __device__ __forceinline__ double mixed_point_factors(const double* cdc, const d
     cross3(c2, c0, r1);
     cross3(c0, c1, r2);
     const double ws = alpha * W3[qp] / S;
-    K[0] = (float)(ws * dot3(r0, r0));
-    K[1] = (float)(ws * dot3(r1, r1));
-    K[2] = (float)(ws * dot3(r2, r2));
-    K[3] = (float)(ws * dot3(r0, r1));
-    K[4] = (float)(ws * dot3(r0, r2));
-    K[5] = (float)(ws * dot3(r1, r2));
+    float f0[3], f1[3], f2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      f0[k] = d2f_int(r0[k]);
+      f1[k] = d2f_int(r1[k]);
+      f2[k] = d2f_int(r2[k]);
+    }
+    auto dotf = [](const float* u, const float* v) { return fmaf(u[0], v[0], fmaf(u[1], v[1], u[2] * v[2])); };
+    K[0] = d2f_int(ws * f2d_int(dotf(f0, f0)));
+    K[1] = d2f_int(ws * f2d_int(dotf(f1, f1)));
+    K[2] = d2f_int(ws * f2d_int(dotf(f2, f2)));
+    K[3] = d2f_int(ws * f2d_int(dotf(f0, f1)));
+    K[4] = d2f_int(ws * f2d_int(dotf(f0, f2)));
+    K[5] = d2f_int(ws * f2d_int(dotf(f1, f2)));
   }
-  if (MAS) *wsm = (float)(beta * W3[qp] * S);
+  if (MAS) *wsm = d2f_int(beta * W3[qp] * S);
   return S;
 }
 
@@ -300,7 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
     for (int i = tid; i < cb * N3; i += kThreads) {
       const int c = i / N3, l = i - c * N3;
       const int cell = flags[2 * c];
-      U[i] = cell >= 0 ? (float)a.x[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r] : 0.f;
+      U[i] = cell >= 0 ? d2f_int(a.x[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r]) : 0.f;
     }
     __syncthreads();
     if (!DQ) {
@@ -369,9 +381,9 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
       const int64_t slot = (int64_t)blockIdx.x * cb + c;
       const bool ok = !flags[2 * c + 1];
       if (a.cell_vectors) {
-        a.y[(slot * N3 + l) * a.nrhs + r] = ok ? (double)U[i] : 0.0;
+        a.y[(slot * N3 + l) * a.nrhs + r] = ok ? f2d_int(U[i]) : 0.0;
       } else if (ok) {
-        a.y[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r] += (double)U[i];
+        a.y[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r] += f2d_int(U[i]);
       }
     }
     if (r == 0)
