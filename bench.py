@@ -482,6 +482,10 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
     ex["structured_fp64"] = rows
     if ctx.sync_status() != 0:
         ex["structured_status"] = "device status flagged"
+    # --- precision: Laplace (Q_p) and neo-Hookean residual (vector Q_p) on 64^3, p=3..8,
+    #     FP64 vs TF32x3 vs BF16x3 split contractions; error against the FP64 GPU action
+    ex["precision_64cube"] = precision_block(sfx, torch, ctx, inputs, flush, stream)
+    torch.cuda.empty_cache()
     # --- p-adaptive batching: 200,000 cells (40x50x100), p in 1..8 with P(p) ~ 1/p,
     #     DQ_p per cell, Laplace + mass on 16 RHS (seeds 0..15)
     dims = (40, 50, 100)
@@ -552,6 +556,42 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
                   "flushed); DoFs/s follows the paper's N/t; dofs_per_s_paper for matrices scales N by the "
                   "fraction of cells assembled")
     return ex
+
+
+def precision_block(sfx, torch, ctx, inputs, flush, stream, dims=(64, 64, 64), degrees=range(3, 9),
+                    precs=("fp64", "tf32x3", "bf16x3")):
+    """Per (form, p): event time of each precision, DoF/s, speedup over FP64
+    and the normwise (inf) relative error against the FP64 GPU action (which
+    the GPU tests hold at 1e-12 of the oracle).  The displacement for degree p
+    is the first ndof draws of stream 1 scaled by 0.05 h / p, exactly what
+    inputs.displacement returns; it is generated once at the largest size and
+    sliced, since the stream is counter-based."""
+    mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    rows = []
+    for fam, form in [("Q", "laplace"), ("VQ", "neohooke")]:
+        spaces = {p: sfx.Space(mesh, fam, p) for p in degrees}
+        base = torch.from_numpy(inputs.random_vector(max(sp.ndof for sp in spaces.values()), 1, seed=1)).cuda()
+        for p in degrees:
+            sp = spaces[p]
+            xd = base[:sp.ndof] * (0.05 / (dims[0] * p)) if fam == "VQ" else base[:sp.ndof]
+            ys = {pr: torch.empty_like(xd) for pr in precs}
+            row = {"family": fam, "form": form, "p": p, "ndof": sp.ndof}
+            for pr in precs:
+                t = _time(torch, stream, flush,
+                          lambda: sfx.sfx_assemble_action(ctx, form, sp, xd, ys[pr], precision=pr, stream=stream))
+                row[pr + "_ms"] = round(t, 4)
+                row[pr + "_dofs_per_s"] = sp.ndof / (t * 1e-3)
+            for pr in precs[1:]:
+                row[pr + "_speedup_vs_fp64"] = row["fp64_ms"] / row[pr + "_ms"]
+                row[pr + "_rel_err_vs_fp64"] = float((ys[pr] - ys["fp64"]).abs().max() / ys["fp64"].abs().max())
+            rows.append(row)
+            del xd, ys
+        del base, spaces
+        torch.cuda.empty_cache()
+    status = ctx.sync_status()
+    return {"rows": rows, "mesh": "%dx%dx%d" % dims, "device_status": status,
+            "note": "TF32x3/BF16x3: 1D contractions on the tensor cores (mma.sync, three split products, FP32 "
+                    "accumulation); geometry, neo-Hookean stress and scatter in FP64"}
 
 
 def e2e(args, sfx, torch, ctx, spaces, wl, prec, stream):

@@ -83,9 +83,12 @@ typedef enum { SFX_NODES_GLL = 0, SFX_NODES_GL = 1 } sfx_nodes;
 
 /* Arithmetic of the contractions.  FP64: all in double.  TF32X3 / BF16X3:
  * the 1D contractions run on the tensor cores as three split products
- * (hi*hi + hi*lo + lo*hi, FP32 accumulation); the geometry (J, det J, J^{-1}),
- * the quadrature-weight scaling, the pointwise physics and the scatter stay in
- * double. */
+ * (hi*hi + hi*lo + lo*hi, FP32 accumulation); the geometry (J, det J, adj J)
+ * and the quadrature-weight scaling are computed in double, and the scatter
+ * adds in double.  Scalar forms round the scaled geometric factors once to
+ * FP32 and apply them in FP32; the hyperelastic stress P(F) is evaluated in
+ * double.  Available for Q_p / DQ_p (mass, Laplace, Helmholtz) and vector
+ * Q_p (neo-Hookean, SVK); NCF/NCE accept FP64 only. */
 typedef enum { SFX_PREC_FP64 = 0, SFX_PREC_TF32X3 = 1, SFX_PREC_BF16X3 = 2 } sfx_precision;
 
 /* SUMFACT: sum-factorised kernels.  NAIVE: dense 3D tabulation, O(n^6) per
@@ -225,10 +228,11 @@ sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_for
 
 /* ------------------------------------------------------------------ tuning */
 
-/* Cells per CTA of the scalar action kernels, per kernel kind and degree
+/* Cells per CTA of the split-precision and FP64 action kernels, per kernel kind and degree
  * (1..8): 0 restores the built-in choice.  Kinds: 0 = FP64 (capped at the
  * 256-thread team limit, 256 / (p+1)^2), 1 = split precision with on-the-fly
- * geometry, 2 = split precision with stored factors.  Every kernel reduces
+ * geometry, 2 = split precision with stored factors, 3 = split-precision
+ * hyperelastic residual (vector Q_p).  Every kernel reduces
  * the value further if its shared memory would not fit.  Values are chosen by
  * measurement (paper_1711_02473_gb300/autotune.py) and are process-wide.
  * Errors: SFX_ERR_ARG. */

@@ -104,62 +104,16 @@ __global__ void __launch_bounds__(256) k_residual_elastic_fp64(const ActArgs a, 
       cross3(c2, c0, R[1]);
       cross3(c0, c1, R[2]);
       const double S = dot3(c0, R[0]);
-      const double iS = 1.0 / S;
-      double F[3][3];
+      double Hq[3][3], flux[3][3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          // (H G)_ij = sum_k H_ik R_kj / S
-          double s = H[(i * 3 + 0) * N3 + qp] * R[0][j] + H[(i * 3 + 1) * N3 + qp] * R[1][j] +
-                     H[(i * 3 + 2) * N3 + qp] * R[2][j];
-          F[i][j] = s * iS + (i == j ? 1.0 : 0.0);
-        }
-      double Pk[3][3];
-      if (NEO) {
-        double Cf[3][3];  // cofactor matrix of F: F^{-T} = Cf / det F
-        cross3(F[1], F[2], Cf[0]);
-        cross3(F[2], F[0], Cf[1]);
-        cross3(F[0], F[1], Cf[2]);
-        const double JF = dot3(F[0], Cf[0]);
-        if (JF > 0.0) {
-          const double iJ = 1.0 / JF, lnJ = log(JF);
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              const double FiT = Cf[i][j] * iJ;
-              Pk[i][j] = mu * (F[i][j] - FiT) + lam * lnJ * FiT;
-            }
-        } else {
-          if (ok) set_flag(a.status, SFX_DEV_DETF);
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) Pk[i][j] = 0.0;
-        }
-      } else {
-        double E[3][3], S2[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j)
-            E[i][j] = 0.5 * (F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j] - (i == j ? 1.0 : 0.0));
-        const double trE = E[0][0] + E[1][1] + E[2][2];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) S2[i][j] = (i == j ? lam * trE : 0.0) + 2.0 * mu * E[i][j];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) Pk[i][j] = F[i][0] * S2[0][j] + F[i][1] * S2[1][j] + F[i][2] * S2[2][j];
-      }
-      const double w = W3[qp];
+        for (int k = 0; k < 3; ++k) Hq[i][k] = H[(i * 3 + k) * N3 + qp];
+      if (!hyperelastic_flux<NEO>(Hq, R, S, W3[qp], mu, lam, flux) && ok) set_flag(a.status, SFX_DEV_DETF);
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) H[(i * 3 + k) * N3 + qp] = w * dot3(Pk[i], R[k]);
+        for (int k = 0; k < 3; ++k) H[(i * 3 + k) * N3 + qp] = flux[i][k];
     }
     __syncthreads();
     for (int comp = 0; comp < 3; ++comp) {
@@ -224,7 +178,8 @@ int dispatch_p(int p, const ActArgs& a, int64_t nc, int64_t nds, cudaStream_t s)
 
 int launch_action_elastic(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
                           void* stream) {
-  if (prec != SFX_PREC_FP64 || sp->family != SFX_VQ) return -1;
+  if (sp->family != SFX_VQ) return -1;
+  if (prec != SFX_PREC_FP64) return launch_action_elastic_mixed(sp, form, prec, a, stream);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t nds = sp->ndof / 3;
   if (form == SFX_NEOHOOKE) return dispatch_p<true>(sp->p, a, sp->mesh->ncell, nds, s);

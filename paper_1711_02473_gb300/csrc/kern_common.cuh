@@ -95,6 +95,65 @@ __device__ __forceinline__ void cross3(const double* u, const double* v, double*
 }
 __device__ __forceinline__ double dot3(const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; }
 
+// Hyperelastic test flux at one point (Sec. 4.1 and the neo-Hookean variant).
+// H = grad^ u (reference gradient, H[i][k] = d u_i / d xi_k), R = rows of
+// adj(J) = S J^{-1}, S = det J, w the quadrature weight.  F = I + H R / S;
+//   neo-Hookean  P = mu (F - F^{-T}) + lambda ln(det F) F^{-T}
+//   SVK          P = F (lambda tr(E) I + 2 mu E),  E = (F^T F - I)/2
+// and the flux w S P G^T = w P R^T is written to out[i][k].  Returns false
+// (and a zero flux) if det F <= 0 for the neo-Hookean law.
+template <bool NEO>
+__device__ __forceinline__ bool hyperelastic_flux(const double (*H)[3], const double (*R)[3], double S, double w,
+                                                  double mu, double lam, double (*out)[3]) {
+  const double iS = 1.0 / S;
+  double F[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      F[i][j] = (H[i][0] * R[0][j] + H[i][1] * R[1][j] + H[i][2] * R[2][j]) * iS + (i == j ? 1.0 : 0.0);
+  double Pk[3][3];
+  bool good = true;
+  if (NEO) {
+    double Cf[3][3];  // cofactor matrix of F: F^{-T} = Cf / det F
+    cross3(F[1], F[2], Cf[0]);
+    cross3(F[2], F[0], Cf[1]);
+    cross3(F[0], F[1], Cf[2]);
+    const double JF = dot3(F[0], Cf[0]);
+    good = JF > 0.0;
+    const double iJ = good ? 1.0 / JF : 0.0, lnJ = good ? log(JF) : 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double FiT = Cf[i][j] * iJ;
+        Pk[i][j] = good ? mu * (F[i][j] - FiT) + lam * lnJ * FiT : 0.0;
+      }
+  } else {
+    double E[3][3], S2[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        E[i][j] = 0.5 * (F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j] - (i == j ? 1.0 : 0.0));
+    const double trE = E[0][0] + E[1][1] + E[2][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) S2[i][j] = (i == j ? lam * trE : 0.0) + 2.0 * mu * E[i][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Pk[i][j] = F[i][0] * S2[0][j] + F[i][1] * S2[1][j] + F[i][2] * S2[2][j];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[i][k] = w * dot3(Pk[i], R[k]);
+  return good;
+}
+
+
 // One 1D contraction of an N0 x N1 x N2 array held in shared memory, along
 // axis AX, for the fiber owned by thread `t` (fibers are indexed by the two
 // other axes; t < product of their extents):

@@ -196,6 +196,7 @@ static int upload_tables(const Tab1D* t) {
   if (!e) e = upload_tab_qdata(t);
   if (!e) e = upload_tab_hdivcurl(t);
   if (!e) e = upload_tab_elastic(t);
+  if (!e) e = upload_tab_elastic_mixed(t);
   if (!e) e = upload_tab_matrix(t);
   if (!e) e = upload_tab_naive(t);
   if (!e) e = upload_tab_batched(t);

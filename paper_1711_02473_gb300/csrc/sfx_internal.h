@@ -107,6 +107,8 @@ int launch_action_hdivcurl(const sfx_space* sp, sfx_form form, sfx_precision pre
                            void* stream);
 int launch_action_elastic(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
                           void* stream);
+int launch_action_elastic_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
+                                void* stream);
 int launch_action_scalar_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
                                void* stream);
 int launch_action_scalar_naive(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
@@ -148,7 +150,13 @@ int launch_qdata(const sfx_space* sp, sfx_qdata* q, uint32_t* status, void* stre
 
 // Cells per CTA of the action kernels: the autotuner's choice per (kernel,
 // degree), 0 = not tuned (the launcher's default).  Host-side table.
-enum { SFX_TUNE_SCALAR_FP64 = 0, SFX_TUNE_SCALAR_MIXED = 1, SFX_TUNE_SCALAR_MIXED_STORED = 2, SFX_TUNE_NKERNEL = 3 };
+enum {
+  SFX_TUNE_SCALAR_FP64 = 0,
+  SFX_TUNE_SCALAR_MIXED = 1,
+  SFX_TUNE_SCALAR_MIXED_STORED = 2,
+  SFX_TUNE_ELASTIC_MIXED = 3,
+  SFX_TUNE_NKERNEL = 4
+};
 int tuned_cells_per_cta(int kernel, int degree, int fallback);
 
 // Each kernel file keeps its own constant-memory copy of the 1D tables.
@@ -157,6 +165,7 @@ int upload_tab_scalar_mixed_tf32(const Tab1D* t);
 int upload_tab_scalar_mixed_bf16(const Tab1D* t);
 int upload_tab_hdivcurl(const Tab1D* t);
 int upload_tab_elastic(const Tab1D* t);
+int upload_tab_elastic_mixed(const Tab1D* t);
 int upload_tab_matrix(const Tab1D* t);
 int upload_tab_naive(const Tab1D* t);
 int upload_tab_batched(const Tab1D* t);

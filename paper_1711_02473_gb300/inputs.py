@@ -55,9 +55,14 @@ def box_coords(nx: int, ny: int, nz: int, perturb: float = 0.1, seed: int = 0) -
 
 
 def random_vector(ndof: int, nrhs: int = 1, seed: int = 1, lo: float = -1.0, hi: float = 1.0):
-    """uniform[lo, hi) entries, (ndof,) for nrhs == 1 else (ndof, nrhs), rhs fastest."""
-    u = uniform01(seed, ndof * nrhs)
-    v = lo + (hi - lo) * u
+    """uniform[lo, hi) entries, (ndof,) for nrhs == 1 else (ndof, nrhs), rhs fastest.
+    Generated in chunks so that large vectors need no full-size temporaries."""
+    n = ndof * nrhs
+    v = np.empty(n, dtype=np.float64)
+    chunk = 1 << 24
+    for s in range(0, n, chunk):
+        c = min(chunk, n - s)
+        v[s:s + c] = lo + (hi - lo) * uniform01(seed, c, start=s)
     return v if nrhs == 1 else v.reshape(ndof, nrhs)
 
 
