@@ -25,7 +25,9 @@ sys.path.insert(0, ROOT)
 DIMS = (64, 64, 64)
 FORMS = ("mass", "laplace", "helmholtz")
 HELM = (1.0, -1.0, 0.0, 0.0)  # alpha * laplace + beta * mass, beta = -k^2, k = 1
-FP64_PEAK_GFLOPS = 1250.0     # nominal GB300 FP64 (FMA pipe), see the design doc
+# nominal GB300 FP64 pipe: 152 SMs x 2 FP64 operations (add, multiply or FMA) per
+# clock x 2.07 GHz; as flops (FMA = 2) this is the 1.26 TFLOP/s nominal figure
+FP64_PEAK_GOPS = 152 * 2 * 2.07
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "DoFs/s of the operator action (config-2 sweep)"
 # DRAM bytes (read + write) per cell of one colour launch, from the ncu captures of
@@ -66,19 +68,22 @@ def cases(args):
     return [(f, p, form) for p in ps for f in fams for form in FORMS]
 
 
-def flops_per_cell(fam, p, form):
-    """Algorithmic FP64 flops of the implemented sum-factorised action per cell
-    (q = n = p+1): 1D contractions 2*n^4 flops each -- B (3 forward, 3 back;
-    absent for DQ) and the collocation derivative Dq (3 forward, 3 back; Laplace
-    part only) -- plus the pointwise work per point: Laplace geometry 73 flops
-    (3 cross products, det, w/S, 6 dot products of the adjugate rows, scaling)
-    and 15 for the flux; mass 17 (det, w S, scaling)."""
+def fp64_ops_per_cell(fam, p, form):
+    """Algorithmic FP64 operations (an add, multiply or FMA each counts one: the
+    FP64 pipe issues any of them at the same rate) of the FP64 sum-factorised
+    action per cell, one RHS, q = n = p+1, as the kernel computes it:
+    1D contractions n^4 FMAs each -- B (3 forward, 3 back; none for DQ) and the
+    collocation derivative Dq (3 + 3, Laplace part); the Jacobian column tables
+    (78 per (a, b) entry); per point for the Laplace part the adjugate rows (3
+    cross products, 18), det J (3), the weight (1, +1 for Helmholtz), a two-step
+    Newton reciprocal (4), the flux t R (R^T g) (21), and for the mass part
+    w S u (3; 12 with det J when alone); the scatter adds one per dof."""
     n = p + 1
     lap = form != "mass"
     mas = form != "laplace"
     ncontr = (0 if fam == "DQ" else 6) + (6 if lap else 0)
-    pw = (73 + 15 if lap else 0) + (17 if mas and not lap else (4 if mas else 0))
-    return ncontr * 2 * n ** 4 + pw * n ** 3
+    pt = (47 + (1 if form == "helmholtz" else 0) if lap else 0) + ((3 if lap else 12) if mas else 0)
+    return ncontr * n ** 4 + 78 * n ** 2 + (pt + 1) * n ** 3
 
 
 def launches_per_action(fam):
@@ -272,26 +277,28 @@ def main():
     dom = max(head["per_case"], key=lambda c: c["ms"])
     fam, p, form = dom["family"], dom["p"], dom["form"]
     if prec == "fp64":
-        fl = flops_per_cell(fam, p, form) * mesh_cells
-        achieved = fl / (dom["ms"] * 1e-3) / 1e9
+        ops = fp64_ops_per_cell(fam, p, form) * mesh_cells
+        achieved = ops / (dom["ms"] * 1e-3) / 1e9
         tpc = NCU_DRAM_BYTES_PER_CELL.get(("k_action_scalar_fp64", fam, p))
         roofline = {"bound": "alu", "kernel": "k_action_scalar_fp64 %s p=%d %s" % (fam, p, form),
-                    "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                    "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GOPS, 1), "unit": "G FP64 op/s",
+                    "frac": round(achieved / FP64_PEAK_GOPS, 4),
                     "traffic": round(tpc * mesh_cells / launches_per_action(fam)) if tpc else None,
-                    "note": "FP64 flops per action (all colour launches) / event time; peak = nominal FP64 "
-                            "(152 SMs x 4 FP64 flop/clk x 2.07 GHz, of nominal)"}
+                    "note": "algorithmic FP64 operations per action (all colour launches; add, multiply or FMA "
+                            "= 1) / event time; peak = 152 SMs x 2 FP64 op/clk x 2.07 GHz, of nominal"}
     else:
-        fl = geometry_flops_per_cell(fam, p, form) * mesh_cells
-        achieved = fl / (dom["ms"] * 1e-3) / 1e9
+        ops = mixed_fp64_ops_per_cell(fam, p, form) * mesh_cells
+        achieved = ops / (dom["ms"] * 1e-3) / 1e9
         tpc = NCU_DRAM_BYTES_PER_CELL.get(("k_action_scalar_mixed", fam, p)) if ":" not in prec else None
         roofline = {"bound": "alu", "kernel": "k_action_scalar_mixed %s p=%d %s %s" % (fam, p, form, prec),
-                    "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                    "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GOPS, 1), "unit": "G FP64 op/s",
+                    "frac": round(achieved / FP64_PEAK_GOPS, 4),
                     "traffic": round(tpc * mesh_cells / launches_per_action(fam)) if tpc else None,
-                    "note": "binding resource = FP64 pipe (geometry J, det J, adj J, w/S per point and the "
-                            "FP64 scatter; ncu: FP64 pipe 81% busy); achieved = those FP64 flops / event time, "
-                            "of nominal; traffic = DRAM bytes per colour launch, scaled from the 32^3 capture"}
+                    "note": "binding resource = FP64 pipe (adjugate rows, det J, w/S and the factor scaling per "
+                            "point, the FP64 scatter; the contractions run on the tensor cores); achieved = "
+                            "those algorithmic FP64 operations / event time, peak = 152 SMs x 2 FP64 op/clk x "
+                            "2.07 GHz, of nominal; traffic = DRAM bytes per colour launch, scaled from a 32^3 "
+                            "capture"}
 
     out = {"metric": METRIC, "value": value, "unit": "DoF/s",
            "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
@@ -332,14 +339,27 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def geometry_flops_per_cell(fam, p, form):
-    """FP64 flops per cell left in the split-precision kernel: per point the
-    adjugate rows (3 cross products, 27), det J (5), w/S (2) and the scaling of
-    the six factors (6) for the Laplace part -- the six row products run in
-    FP32 -- or det J and w S (17) for mass; plus the FP64 scatter (1 per dof)."""
+def mixed_fp64_ops_per_cell(fam, p, form):
+    """FP64 operations per cell left in the split-precision action (the
+    contractions run on the tensor cores, the flux in FP32).  n >= 4: staged
+    adjugate-row tables per cell -- edge vectors (126), 1D vectors (108 per
+    point, 42 for mass alone), 2D tables (22 per (a, b) entry, 10 for mass) --
+    then per point the rows (9), det J (3), the weight (1), a one-step Newton
+    reciprocal (2), w/S (1, +1 for Helmholtz) and the scaling of the six
+    factors (6); mass adds w S (2), or 9 with det J when alone.  n <= 3: the
+    Jacobian column tables (78 per entry) and cross products at the point
+    (32 / 13).  The scatter adds one per dof."""
     n = p + 1
     lap = form != "mass"
-    return ((40 if lap else 17) + 1) * n ** 3
+    mas = form != "laplace"
+    helm = 1 if form == "helmholtz" else 0
+    if n >= 4:
+        tables = 126 + (108 if lap else 42) * n + (22 if lap else 10) * n ** 2
+        pt = (22 + helm if lap else 0) + ((2 if lap else 9) if mas else 0)
+    else:
+        tables = 78 * n ** 2
+        pt = (32 + helm if lap else 0) + ((2 if lap else 13) if mas else 0)
+    return tables + (pt + 1) * n ** 3
 
 
 def time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, arm, flush, stream, ws, local):
@@ -403,8 +423,9 @@ def time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, arm, flush, stream, ws, 
         t = float(np.median([a.elapsed_time(b) for a, b in ev[c]]))
         fam, p, form = c
         nd = spaces[(fam, p)].ndof
+        ops = (fp64_ops_per_cell if prec == "fp64" else mixed_fp64_ops_per_cell)(fam, p, form)
         per_case.append({"family": fam, "p": p, "form": form, "ms": round(t, 4), "dofs_per_s": nd / (t * 1e-3),
-                         "gflops_fp64_alg": flops_per_cell(fam, p, form) * ncell / (t * 1e-3) / 1e9})
+                         "gops_fp64_alg": ops * ncell / (t * 1e-3) / 1e9 if not stored else None})
     for q in qd.values():
         q.close()
     out = {"ms_step": ms_total / args.steps, "per_case": per_case, "clocks": clocks}
@@ -441,15 +462,19 @@ def _time(torch, stream, flush, fn, reps=3, warm=2):
     return float(np.median(ts))
 
 
-def dq_multi_flops(p, form, nrhs):
-    """FP64 flops of the DQ action for one cell and nrhs right-hand sides
-    (geometry once, contractions and flux per RHS)."""
+def dq_multi_ops(p, form, nrhs):
+    """FP64 operations (add, multiply or FMA = 1) of the DQ action for one
+    cell and nrhs right-hand sides in the persistent kernel: the Jacobian
+    column tables (78 per entry) and the staged factors once per cell (Laplace:
+    rows 18, det J 3, weight and w/S 2, reciprocal 4, six dot products 18 and
+    their scaling 6; mass: w S 2, or 11 with det J when alone), then per RHS
+    the Dq contractions (6 n^4, Laplace), the flux (9 per point, Laplace;
+    1 for mass) and the scatter (1 per dof)."""
     n = p + 1
     lap = form != "mass"
-    contr = (6 if lap else 0) * 2 * n ** 4
-    geo = (73 if lap else 0) + (17 if not lap else 4)
-    flux = 15 if lap else 1
-    return (contr + flux * n ** 3) * nrhs + geo * n ** 3
+    geo = 78 * n ** 2 + ((51 + 2) if lap else 11) * n ** 3
+    per_rhs = (6 * n ** 4 if lap else 0) + ((9 if lap else 1) + 1) * n ** 3
+    return geo + per_rhs * nrhs
 
 
 def matrix_flops(p, fam):
@@ -501,14 +526,14 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
     tl = _time(torch, stream, flush, lambda: plan.execute(xd, ys, mode="per_launch", stream=stream), reps=2, warm=1)
     work = plan.ndof * R * len(forms)
     ndeg = len(np.unique(deg))
-    fl = sum(dq_multi_flops(int(p), f, R) * int((deg == p).sum()) for p in np.unique(deg) for f in forms)
+    fl = sum(dq_multi_ops(int(p), f, R) * int((deg == p).sum()) for p in np.unique(deg) for f in forms)
     ex["padaptive_batched_fp64"] = {
         "cells": int(np.prod(dims)), "ndof": int(plan.ndof), "nrhs": R, "forms": forms, "tiles": int(plan.ntiles),
         "graph_ms": round(tg, 3), "per_launch_ms": round(tl, 3),
         "graph_dofs_per_s": work / (tg * 1e-3), "per_launch_dofs_per_s": work / (tl * 1e-3),
         "speedup_graph_vs_per_launch": tl / tg, "launches_graph": 1, "launches_per_launch": ndeg * R * len(forms),
-        "roofline": {"bound": "alu", "achieved": round(fl / (tg * 1e-3) / 1e9, 2), "peak": FP64_PEAK_GFLOPS,
-                     "unit": "GFLOP/s", "frac": round(fl / (tg * 1e-3) / 1e9 / FP64_PEAK_GFLOPS, 4)}}
+        "roofline": {"bound": "alu", "achieved": round(fl / (tg * 1e-3) / 1e9, 2), "peak": round(FP64_PEAK_GOPS, 1),
+                     "unit": "G FP64 op/s", "frac": round(fl / (tg * 1e-3) / 1e9 / FP64_PEAK_GOPS, 4)}}
     del xd, ys, plan, mesh
     torch.cuda.empty_cache()
     # --- naive (un-factorised) vs sum-factorised action, Q_p Laplace, 32^3

@@ -20,7 +20,7 @@ template <int N, bool DQ, int FORM>
 int launch_fp64(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   using Sh = ScalarShape<N, FORM>;
   // several RHS: stage the factors once per cell; one RHS: form them at the point
-  const bool geo_once = a.r1 - a.r0 > 1;
+  const bool geo_once = a.r1 - a.r0 > 1 || a.stage_factors;
   const size_t per_team = (size_t)Sh::team_doubles(geo_once) * sizeof(double);
   const size_t fixed = (Sh::N3 + 16) * sizeof(double);
   const size_t budget = 200 * 1024;

@@ -60,7 +60,13 @@ __device__ __forceinline__ void jacobian_columns(const double (*X)[3], const dou
 }
 
 // Conversions between double and float on the integer pipe (GB300's FP64
-// pipe, which also runs the hardware conversions, is the scarce unit).
+// pipe, which also runs the hardware conversions, is the scarce unit).  The
+// rare cases take the hardware conversion in an out-of-line call, so that it
+// is a branch and not an FP64-pipe instruction issued under a predicate.
+static __device__ __noinline__ float d2f_hw(double d) { return (float)d; }
+static __device__ __noinline__ double f2d_hw(float f) { return (double)f; }
+static __device__ __noinline__ double recip_div(double s) { return 1.0 / s; }
+
 // float -> double is exact: re-bias the exponent, widen the mantissa.  Zero
 // and subnormal floats map to a signed zero (values below 1.2e-38 do not
 // matter here), infinities and NaNs take the hardware path.
@@ -69,7 +75,7 @@ __device__ __forceinline__ double f2d_int(float f) {
   const uint32_t e = (b >> 23) & 0xffu;
   const unsigned long long sgn = (unsigned long long)(b >> 31) << 63;
   if (e == 0u) return __longlong_as_double((long long)sgn);
-  if (e == 0xffu) return (double)f;
+  if (e == 0xffu) return f2d_hw(f);
   const unsigned long long bits =
       sgn | ((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
   return __longlong_as_double((long long)bits);
@@ -81,7 +87,7 @@ __device__ __forceinline__ double f2d_int(float f) {
 __device__ __forceinline__ float d2f_int(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
-  if (e <= 0 || e >= 255) return (float)d;
+  if (e <= 0 || e >= 255) return d2f_hw(d);
   const unsigned long long m = b & 0xfffffffffffffull;
   const unsigned long long r = m + 0x0fffffffull + ((m >> 29) & 1ull);
   const uint32_t out = ((uint32_t)(b >> 63) << 31) | ((uint32_t)e << 23);
@@ -94,6 +100,192 @@ __device__ __forceinline__ void cross3(const double* u, const double* v, double*
   w[2] = u[0] * v[1] - u[1] * v[0];
 }
 __device__ __forceinline__ double dot3(const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; }
+
+// Rows r_k of adj J = S J^{-1} at point qp from the Jacobian column tables
+// (r0 = c1 x c2, r1 = c2 x c0, r2 = c0 x c1); r1, r2 only when ROWS.  Returns
+// S = det J = c0 . r0.
+template <int N, bool ROWS>
+__device__ __forceinline__ double point_rows(const double (*Jc)[N * N][3], int qp, double* r0, double* r1,
+                                             double* r2) {
+  constexpr int N2 = N * N;
+  const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
+  const double* c0 = Jc[0][q2 * N + q3];
+  const double* c1 = Jc[1][q1 * N + q3];
+  const double* c2 = Jc[2][q1 * N + q2];
+  cross3(c1, c2, r0);
+  if (ROWS) {
+    cross3(c2, c0, r1);
+    cross3(c0, c1, r2);
+  }
+  return dot3(c0, r0);
+}
+
+// 1/s in FP64 by the Newton-Raphson iteration r <- r + r (1 - s r), seeded
+// with the FP32 approximate reciprocal (PTX rcp.approx, relative error below
+// 2^-22 including the rounding of s to FP32).  Each step squares the relative
+// error: one step leaves < 2^-44, two steps reach FP64 rounding.  Two FMAs per
+// step on the FP64 pipe instead of a full IEEE division; the conversions run
+// on the integer pipe.  Outside the normal FP32 range of s the plain division
+// is used.
+template <int STEPS>
+__device__ __forceinline__ double recip_nr(double s) {
+  const float sf = d2f_int(s);
+  const float af = fabsf(sf);
+  if (!(af >= 1.0e-37f && af <= 1.0e37f)) return recip_div(s);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(sf));
+  double r = f2d_int(rf);
+#pragma unroll
+  for (int k = 0; k < STEPS; ++k) r = fma(r, fma(-s, r, 1.0), r);
+  return r;
+}
+
+// Adjugate rows of the trilinear Jacobian from per-cell tables.
+//
+// J = [c0 c1 c2] with c_d = dx/dxi_d; the rows of adj(J) = S J^{-1} are
+// r0 = c1 x c2, r1 = c2 x c0, r2 = c0 x c1 (S = c0 . r0).  For the trilinear
+// (vector-Q1) coordinate field (Sec. 3.1) each c_d is bilinear in the two
+// other coordinates:
+//   c0(xi2,xi3) = Pb + xi2 P2 + xi3 P3 + xi2 xi3 Pt
+//   c1(xi1,xi3) = Qb + xi1 Q1 + xi3 Q3 + xi1 xi3 Qt
+//   c2(xi1,xi2) = Rb + xi1 R1 + xi2 R2 + xi1 xi2 Rt
+// with edge vectors from the 8 corners.  Expanding the cross products, each
+// row is a bilinear combination, in the two coordinates it does not single
+// out, of four vectors that depend on the third:
+//   r0 = U0a(xi1) + xi2 U0b(xi1) + xi3 [U0c(xi1) + xi2 U0d(xi1)]
+//   r1 = U1a(xi2) + xi3 U1b(xi2) + xi1 [U1c(xi2) + xi3 U1d(xi2)]
+//   r2 = U2a(xi3) + xi2 U2b(xi3) + xi1 [U2c(xi3) + xi2 U2d(xi3)]
+// (U0* = products of c1 = e0 + xi3 e1 and c2 = k0 + xi2 k1 at fixed xi1, and
+// so on), the same sum factorisation as the basis functions get (Sec. 3.2).
+// The tables are built in three stages per cell -- edge vectors (36 values),
+// the 1D vectors U (one cross product per vector and point), then the 2D
+// coefficient tables below with one FMA per component -- so that a point
+// costs three FMAs per row instead of a cross product:
+//   r0 = A0(q1,q2) + xi3 B0(q1,q2),  r1 = A1(q2,q3) + xi1 B1(q2,q3),
+//   r2 = A2(q2,q3) + xi1 B2(q2,q3),  c0 = c0(q2,q3).
+// The same sums as the direct cross products, in another rounding order.
+//
+// Layouts (per cell, doubles):
+//   E[v*3 + k]        edge vectors, v = Pb P2 P3 Pt Qb Q1 Q3 Qt Rb R1 R2 Rt
+//   T[q*42 + .]       1D vectors at point q: U0a..U0d (0..11), U1a..U1d, g0, g1
+//                     (12..29; c0 = g0(xi2) + xi3 g1(xi2)), U2a..U2d (30..41)
+//   R23[j*N^2 + (q2*N+q3)]  j = c0[0..2], then (REC23 = 16) A1[3], B1[3], A2[3],
+//                     B2[3], and w2*w3 last; (REC23 = 4) c0[3], w2*w3
+//   R12[j*N^2 + (q1*N+q2)]  j = A0[0..2], B0[0..2]
+// Component-major 2D tables: threads at neighbouring points read neighbouring words.
+constexpr int kAdjEdge = 36, kAdjT1D = 42;
+
+// Stage 1: edge value j (< 36) from the corners X (corner (a,b,c) at 4a+2b+c).
+__device__ __forceinline__ void adj_edges(const double (*X)[3], double* E, int j) {
+  const int v = j / 3, k = j - (j / 3) * 3;
+  const double x0 = X[0][k], x1 = X[1][k], x2 = X[2][k], x3 = X[3][k];
+  const double x4 = X[4][k], x5 = X[5][k], x6 = X[6][k], x7 = X[7][k];
+  const double tw = ((x7 - x6) - (x5 - x4)) - ((x3 - x2) - (x1 - x0));
+  double e;
+  switch (v) {
+    case 0: e = x4 - x0; break;                  // Pb
+    case 1: e = (x6 - x2) - (x4 - x0); break;    // P2
+    case 2: e = (x5 - x1) - (x4 - x0); break;    // P3
+    case 4: e = x2 - x0; break;                  // Qb
+    case 5: e = (x6 - x4) - (x2 - x0); break;    // Q1
+    case 6: e = (x3 - x1) - (x2 - x0); break;    // Q3
+    case 8: e = x1 - x0; break;                  // Rb
+    case 9: e = (x5 - x4) - (x1 - x0); break;    // R1
+    case 10: e = (x3 - x2) - (x1 - x0); break;   // R2
+    default: e = tw; break;                      // Pt = Qt = Rt
+  }
+  E[j] = e;
+}
+
+// Stage 2: the 1D vectors of axis `ax` at point q (one thread per (ax, q)).
+// ROWS: all three rows (Laplace part); otherwise only r0 and c0 (det J).
+template <bool ROWS>
+__device__ __forceinline__ void adj_1d(const double* E, const double* xq, double* T, int ax, int q) {
+  const double x = xq[q];
+  const double* Pb = E + 0; const double* P2 = E + 3; const double* P3 = E + 6; const double* Pt = E + 9;
+  const double* Qb = E + 12; const double* Q1 = E + 15; const double* Q3 = E + 18; const double* Qt = E + 21;
+  const double* Rb = E + 24; const double* R1 = E + 27; const double* R2 = E + 30; const double* Rt = E + 33;
+  double* o = T + q * kAdjT1D;
+  double u[3], v[3], s[3], t[3];
+  if (ax == 0) {  // r0 = (e0 + xi3 e1) x (k0 + xi2 k1) at xi1 = x
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      u[k] = fma(x, Q1[k], Qb[k]); v[k] = fma(x, Qt[k], Q3[k]);
+      s[k] = fma(x, R1[k], Rb[k]); t[k] = fma(x, Rt[k], R2[k]);
+    }
+    cross3(u, s, o + 0); cross3(u, t, o + 3); cross3(v, s, o + 6); cross3(v, t, o + 9);
+  } else if (ax == 1) {  // r1 = (f0 + xi1 f1) x (g0 + xi3 g1) at xi2 = x
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      u[k] = fma(x, R2[k], Rb[k]); v[k] = fma(x, Rt[k], R1[k]);
+      s[k] = fma(x, P2[k], Pb[k]); t[k] = fma(x, Pt[k], P3[k]);
+      o[24 + k] = s[k]; o[27 + k] = t[k];
+    }
+    if (ROWS) { cross3(u, s, o + 12); cross3(u, t, o + 15); cross3(v, s, o + 18); cross3(v, t, o + 21); }
+  } else if (ROWS) {  // r2 = (h0 + xi2 h1) x (d0 + xi1 d1) at xi3 = x
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      u[k] = fma(x, P3[k], Pb[k]); v[k] = fma(x, Pt[k], P2[k]);
+      s[k] = fma(x, Q3[k], Qb[k]); t[k] = fma(x, Qt[k], Q1[k]);
+    }
+    cross3(u, s, o + 30); cross3(v, s, o + 33); cross3(u, t, o + 36); cross3(v, t, o + 39);
+  }
+}
+
+// Stage 3: entry t (< N^2) of both 2D tables.
+template <int N, int REC23>
+__device__ __forceinline__ void adj_2d(const double* T, const double* xq, const double* wq, double* R23, double* R12,
+                                       int t) {
+  constexpr int N2 = N * N;
+  const int a = t / N, b = t - (t / N) * N;
+  const double xa = xq[a], xb = xq[b];
+  {  // (q2, q3) = (a, b)
+    const double* ta = T + a * kAdjT1D;
+    const double* tb = T + b * kAdjT1D;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) R23[k * N2 + t] = fma(xb, ta[27 + k], ta[24 + k]);
+    if (REC23 == 16) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        R23[(3 + k) * N2 + t] = fma(xb, ta[15 + k], ta[12 + k]);   // A1 = U1a + xi3 U1b
+        R23[(6 + k) * N2 + t] = fma(xb, ta[21 + k], ta[18 + k]);   // B1 = U1c + xi3 U1d
+        R23[(9 + k) * N2 + t] = fma(xa, tb[33 + k], tb[30 + k]);   // A2 = U2a + xi2 U2b
+        R23[(12 + k) * N2 + t] = fma(xa, tb[39 + k], tb[36 + k]);  // B2 = U2c + xi2 U2d
+      }
+    }
+    R23[(REC23 - 1) * N2 + t] = wq[a] * wq[b];
+  }
+  {  // (q1, q2) = (a, b)
+    const double* ta = T + a * kAdjT1D;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      R12[k * N2 + t] = fma(xb, ta[3 + k], ta[0 + k]);        // A0 = U0a + xi2 U0b
+      R12[(3 + k) * N2 + t] = fma(xb, ta[9 + k], ta[6 + k]);  // B0 = U0c + xi2 U0d
+    }
+  }
+}
+
+// Rows at point (q1,q2,q3) from the 2D tables of adj_2d: r0 always (with S),
+// r1 and r2 when ROWS.  Returns S = det J; *w = w1 w2 w3.
+template <int N, int REC23, bool ROWS>
+__device__ __forceinline__ double adj_rows(const double* R23, const double* R12, const double* xq, const double* wq,
+                                           int q1, int q2, int q3, double* r0, double* r1, double* r2, double* w) {
+  constexpr int N2 = N * N;
+  const double* o = R23 + (q2 * N + q3);
+  const double* e = R12 + (q1 * N + q2);
+  const double x1 = xq[q1], x3 = xq[q3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r0[k] = fma(x3, e[(3 + k) * N2], e[k * N2]);
+  if (ROWS) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      r1[k] = fma(x1, o[(6 + k) * N2], o[(3 + k) * N2]);
+      r2[k] = fma(x1, o[(12 + k) * N2], o[(9 + k) * N2]);
+    }
+  }
+  *w = wq[q1] * o[(REC23 - 1) * N2];
+  return o[0] * r0[0] + o[N2] * r0[1] + o[2 * N2] * r0[2];
+}
 
 // Hyperelastic test flux at one point (Sec. 4.1 and the neo-Hookean variant).
 // H = grad^ u (reference gradient, H[i][k] = d u_i / d xi_k), R = rows of

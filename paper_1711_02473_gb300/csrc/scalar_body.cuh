@@ -43,22 +43,14 @@ struct ScalarShape {
 
 // The factors at point qp of a cell: P (6 symmetric entries, scaled by alpha)
 // and w S (scaled by beta), from the Jacobian column tables.  Returns S.
+// 1/S is a two-step Newton reciprocal (FP64 rounding level).
 template <int N, bool LAP, bool MAS>
 __device__ __forceinline__ double point_factors(const double (*Jc)[N * N][3], const double* W3, int qp,
                                                 double alpha, double beta, double* K, double* ws_mass) {
-  constexpr int N2 = N * N;
-  const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
-  const double* c0 = Jc[0][q2 * N + q3];
-  const double* c1 = Jc[1][q1 * N + q3];
-  const double* c2 = Jc[2][q1 * N + q2];
-  double r0[3];
-  cross3(c1, c2, r0);
-  const double S = dot3(c0, r0);
+  double r0[3], r1[3], r2[3];
+  const double S = point_rows<N, LAP>(Jc, qp, r0, r1, r2);
   if (LAP) {
-    double r1[3], r2[3];
-    cross3(c2, c0, r1);
-    cross3(c0, c1, r2);
-    const double ws = alpha * W3[qp] / S;  // P = w S G G^T = (w/S) adj(J) adj(J)^T
+    const double ws = alpha * W3[qp] * recip_nr<2>(S);  // P = w S G G^T = (w/S) adj(J) adj(J)^T
     K[0] = ws * dot3(r0, r0);
     K[1] = ws * dot3(r1, r1);
     K[2] = ws * dot3(r2, r2);
@@ -184,8 +176,23 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
           for (int j = 0; j < 6; ++j) kk[j] = active ? alpha * qd[j * N3 + qp] : 0.0;
         if (MAS) wsm = active ? beta * qd[6 * N3 + qp] : 0.0;
       } else {
-        const double S = point_factors<N, LAP, MAS>(Jc, W3, qp, alpha, beta, kk, &wsm);
+        // at the point: the flux P g = (w/S) R R^T g with R the adjugate rows,
+        // applied as R (t R^T g) without forming the six entries of P
+        double r0[3], r1[3], r2[3];
+        const double S = point_rows<N, LAP>(Jc, qp, r0, r1, r2);
         if (!(S > 0.0)) *bad = 1;
+        if (LAP) {
+          const double tw = alpha * W3[qp] * recip_nr<2>(S);
+          const double g0 = G0[qp], g1 = G1[qp], g2 = G2[qp];
+          double v[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) v[d] = tw * (r0[d] * g0 + r1[d] * g1 + r2[d] * g2);
+          G0[qp] = dot3(r0, v);
+          G1[qp] = dot3(r1, v);
+          G2[qp] = dot3(r2, v);
+        }
+        if (MAS) U[qp] = (beta * W3[qp] * S) * U[qp];
+        continue;
       }
       if (LAP) {
         const double g0 = G0[qp], g1 = G1[qp], g2 = G2[qp];

@@ -29,41 +29,54 @@ struct MixedShape {
   static constexpr int N2 = N * N, N3 = N2 * N;
   static constexpr bool LAP = FORM != SFX_MASS;
   static constexpr bool MAS = FORM != SFX_LAPLACE;
+  // Geometry tables: for N >= 4 the staged adjugate-row tables (see adj_rows;
+  // 2D record per (q2,q3): all three rows for the Laplace part, only c0 for
+  // mass); for N <= 3, where a cell has at most 27 points and the staged build
+  // does not pay, the Jacobian column tables with cross products at the point.
+  static constexpr bool HIER = N >= 4;
+  static constexpr int REC23 = LAP ? 16 : 4;
   // per-cell floats: U, G0..G2 (LAP); plus the staged factors K[6] (LAP) and
   // WS (MAS) when geo_once
   static constexpr int cellf(bool geo_once) {
     return N3 + (LAP ? 3 * N3 : 0) + (geo_once ? (LAP ? 6 * N3 : 0) + (MAS ? N3 : 0) : 0);
   }
-  // per-cell doubles: corners (24) + Jacobian column tables (9 N^2), on-the-fly geometry only
-  static constexpr int celld(bool stored) { return stored ? 0 : 24 + 9 * N2; }
-  static constexpr size_t fixed_bytes() { return 2 * sizeof(TabF) + (N3 + 16) * 8; }
+  // per-cell temporaries of the table build: corners, edge vectors, 1D vectors
+  static constexpr int TMPD = HIER ? 24 + kAdjEdge + kAdjT1D * N : 24;
+  // they live in the float area (free until the gather) when it is large enough
+  static constexpr bool TMP_IN_F = HIER && 2 * TMPD <= N3 + (LAP ? 3 * N3 : 0);
+  // per-cell doubles: [temporaries] + 2D tables R23, R12 (or the column
+  // tables Jc[3][N^2][3]); on-the-fly geometry only
+  static constexpr int TABD = HIER ? N2 * (REC23 + 6) : 9 * N2;
+  static constexpr int celld(bool stored) { return stored ? 0 : (TMP_IN_F ? 0 : TMPD) + TABD; }
+  // two FP32 tables, 1D points and weights (16 doubles each)
+  static constexpr size_t fixed_bytes() { return 2 * sizeof(TabF) + 32 * 8; }
   static constexpr size_t bytes(int cb, bool geo_once, bool stored) {
     return fixed_bytes() + (size_t)cb * celld(stored) * 8 + (size_t)cb * cellf(geo_once) * 4 + (size_t)cb * 8 + 16;
   }
 };
 
-// Factors at point qp of cell c.  J (column tables), the adjugate rows
-// r_k = rows of S J^{-1}, S = det J and the weight scaling w/S are computed in
-// FP64; the six products r_k . r_l, which only feed FP32 factors, run on the
-// FP32 pipe from the rows rounded once to FP32, and are scaled by w/S in FP64
-// before the final rounding.  Returns S.
+// Factors at point qp of a cell, from the cell's 2D adjugate-row tables (tab
+// = R23 followed by R12).  The rows r_k of adj J = S J^{-1}, S = det J and the
+// weight scaling w/S (Newton reciprocal, one step: < 2^-44 relative, far below
+// the FP32 rounding of the factors) are computed in FP64; the six products
+// r_k . r_l, which only feed FP32 factors, run on the FP32 pipe from the rows
+// rounded once to FP32, and are scaled by w/S in FP64 before the final
+// rounding.  Returns S.
 template <int N, bool LAP, bool MAS>
-__device__ __forceinline__ double mixed_point_factors(const double* cdc, const double* W3, int qp, double alpha,
-                                                      double beta, float* K, float* wsm) {
+__device__ __forceinline__ double mixed_point_factors(const double* tab, const double* xq, const double* wq, int qp,
+                                                      double alpha, double beta, float* K, float* wsm) {
   constexpr int N2 = N * N;
+  constexpr int REC23 = LAP ? 16 : 4;
   const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
-  const double(*Jc)[N2][3] = reinterpret_cast<const double(*)[N2][3]>(cdc + 24);
-  const double* c0 = Jc[0][q2 * N + q3];
-  const double* c1 = Jc[1][q1 * N + q3];
-  const double* c2 = Jc[2][q1 * N + q2];
-  double r0[3];
-  cross3(c1, c2, r0);
-  const double S = dot3(c0, r0);
+  double r0[3], r1[3], r2[3], w, S;
+  if (N >= 4) {
+    S = adj_rows<N, REC23, LAP>(tab, tab + N2 * REC23, xq, wq, q1, q2, q3, r0, r1, r2, &w);
+  } else {
+    S = point_rows<N, LAP>(reinterpret_cast<const double(*)[N2][3]>(tab), qp, r0, r1, r2);
+    w = wq[q1] * wq[q2] * wq[q3];
+  }
   if (LAP) {
-    double r1[3], r2[3];
-    cross3(c2, c0, r1);
-    cross3(c0, c1, r2);
-    const double ws = alpha * W3[qp] / S;
+    const double ws = (alpha * w) * recip_nr<1>(S);
     float f0[3], f1[3], f2[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -79,7 +92,7 @@ __device__ __forceinline__ double mixed_point_factors(const double* cdc, const d
     K[4] = d2f_int(ws * f2d_int(dotf(f0, f2)));
     K[5] = d2f_int(ws * f2d_int(dotf(f1, f2)));
   }
-  if (MAS) *wsm = d2f_int(beta * W3[qp] * S);
+  if (MAS) *wsm = d2f_int((beta * w) * S);
   return S;
 }
 
@@ -93,11 +106,11 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
   constexpr bool LAP = Sh::LAP, MAS = Sh::MAS;
   const Tab1D& T = c_tab[N - 1];
   extern __shared__ double smd[];
-  // layout: [tables: 2 TabF][W3: N3 doubles][xq: 16 doubles][cells: doubles][cells: floats][flags]
+  // layout: [tables: 2 TabF][xq: 16 doubles][wq: 16 doubles][cells: doubles][cells: floats][flags]
   TabF* tabs = reinterpret_cast<TabF*>(smd);  // 0: B, 1: Dq
-  double* W3 = smd + (2 * sizeof(TabF)) / 8;
-  double* xq = W3 + N3;
-  double* cd = xq + 16;                       // per-cell doubles (on-the-fly geometry)
+  double* xq = smd + (2 * sizeof(TabF)) / 8;
+  double* wq = xq + 16;
+  double* cd = wq + 16;                       // per-cell doubles (on-the-fly geometry)
   float* cf = reinterpret_cast<float*>(cd + (size_t)cb * Sh::celld(STORED));
   float* U = cf;
   float* G0 = U + cb * N3;
@@ -113,8 +126,10 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
     tabs[0].v[r][k] = (r < N && k < N) ? (float)T.Bc[r][k] : 0.f;
     tabs[1].v[r][k] = (r < N && k < N) ? (float)T.Dq[r][k] : 0.f;
   }
-  for (int i = tid; i < N3; i += kThreads) W3[i] = T.w[i / N2] * T.w[(i / N) % N] * T.w[i % N];
-  if (tid < N) xq[tid] = T.x[tid];
+  if (tid < N) {
+    xq[tid] = T.x[tid];
+    wq[tid] = T.w[tid];
+  }
   for (int c = tid; c < cb; c += kThreads) {
     int cell = -1;
     if (!slot_cell(a, (int64_t)blockIdx.x * cb + c, ncell_total, &cell)) cell = -1;
@@ -125,20 +140,48 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
   const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
   const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
   const float fa = (float)alpha, fb = (float)beta;
+  // per-cell build temporaries and 2D tables (see adj_rows)
+  auto tmp_of = [&](int c) -> double* {
+    return Sh::TMP_IN_F ? reinterpret_cast<double*>(cf) + (size_t)c * Sh::TMPD : cd + (size_t)c * Sh::celld(false);
+  };
+  auto tab_of = [&](int c) -> const double* {
+    return cd + (size_t)c * Sh::celld(false) + (Sh::TMP_IN_F ? 0 : Sh::TMPD);
+  };
   if (!STORED) {
     for (int i = tid; i < cb * 24; i += kThreads) {
       const int c = i / 24, v = (i % 24) / 3, k = i % 3;
       const int cell = flags[2 * c];
-      double* X = cd + (size_t)c * Sh::celld(false);
-      X[v * 3 + k] = cell >= 0 ? a.xyz[(int64_t)a.vmap[(int64_t)cell * 8 + v] * 3 + k] : (double)((v >> (2 - k)) & 1);
+      tmp_of(c)[v * 3 + k] =
+          cell >= 0 ? a.xyz[(int64_t)a.vmap[(int64_t)cell * 8 + v] * 3 + k] : (double)((v >> (2 - k)) & 1);
     }
     __syncthreads();
-    for (int i = tid; i < cb * N2; i += kThreads) {
-      const int c = i / N2, t = i - c * N2;
-      double* X = cd + (size_t)c * Sh::celld(false);
-      jacobian_columns<N>(reinterpret_cast<const double(*)[3]>(X), xq, reinterpret_cast<double(*)[N2][3]>(X + 24), t);
+    if (!Sh::HIER) {
+      for (int i = tid; i < cb * N2; i += kThreads) {
+        const int c = i / N2, t = i - c * N2;
+        jacobian_columns<N>(reinterpret_cast<const double(*)[3]>(tmp_of(c)), xq,
+                            reinterpret_cast<double(*)[N2][3]>(const_cast<double*>(tab_of(c))), t);
+      }
+      __syncthreads();
+    } else {
+      for (int i = tid; i < cb * kAdjEdge; i += kThreads) {
+        const int c = i / kAdjEdge;
+        double* X = tmp_of(c);
+        adj_edges(reinterpret_cast<const double(*)[3]>(X), X + 24, i - c * kAdjEdge);
+      }
+      __syncthreads();
+      for (int i = tid; i < cb * 3 * N; i += kThreads) {
+        const int c = i / (3 * N), r = i - c * (3 * N);
+        double* X = tmp_of(c);
+        adj_1d<LAP>(X + 24, xq, X + 24 + kAdjEdge, r / N, r % N);
+      }
+      __syncthreads();
+      for (int i = tid; i < cb * N2; i += kThreads) {
+        const int c = i / N2, t = i - c * N2;
+        double* R23 = const_cast<double*>(tab_of(c));
+        adj_2d<N, Sh::REC23>(tmp_of(c) + 24 + kAdjEdge, xq, wq, R23, R23 + N2 * Sh::REC23, t);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   if (geo_once) {
     for (int i = tid; i < cb * N3; i += kThreads) {
@@ -151,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
           for (int j = 0; j < 6; ++j) kk[j] = cell >= 0 ? fa * qd[j * N3 + qp] : 0.f;
         if (MAS) wsm = cell >= 0 ? fb * qd[6 * N3 + qp] : 0.f;
       } else {
-        const double S = mixed_point_factors<N, LAP, MAS>(cd + (size_t)c * Sh::celld(false), W3, qp, alpha, beta,
+        const double S = mixed_point_factors<N, LAP, MAS>(tab_of(c), xq, wq, qp, alpha, beta,
                                                           kk, &wsm);
         if (!(S > 0.0)) flags[2 * c + 1] = 1;
       }
@@ -200,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
           if (MAS) wsm = fb * qd[6 * N3 + qp];
         }
       } else {
-        const double S = mixed_point_factors<N, LAP, MAS>(cd + (size_t)c * Sh::celld(false), W3, qp, alpha, beta,
+        const double S = mixed_point_factors<N, LAP, MAS>(tab_of(c), xq, wq, qp, alpha, beta,
                                                           kk, &wsm);
         if (!(S > 0.0)) flags[2 * c + 1] = 1;
       }

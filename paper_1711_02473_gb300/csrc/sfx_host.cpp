@@ -789,6 +789,7 @@ extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* co
           a.y = y[f];
           a.r0 = r;
           a.r1 = r + 1;
+          a.stage_factors = 1;  // same per-point arithmetic as the persistent kernel
           a.alpha = pl->params[f].alpha;
           a.beta = pl->params[f].beta;
           if (launch_scalar_fp64_degree(p, true, pl->forms[f], a, pl->mesh->ncell, stream) != 0) return SFX_ERR_CUDA;
