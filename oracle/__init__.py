@@ -17,6 +17,8 @@ import numpy as np
 from . import build as _build
 
 FAMILIES = {"Q": 0, "DQ": 1, "NCF": 2, "NCE": 3, "VQ": 4}
+# quadrature rules: Gauss-Legendre (default) and Gauss-Lobatto-Legendre
+QRULES = {"GL": 1, "GLL": 0}
 FORMS = {"mass": 0, "laplace": 1, "helmholtz": 2, "ncf_mass_divdiv": 3,
          "nce_curlcurl": 4, "neohooke": 5, "svk": 6}
 
@@ -56,6 +58,9 @@ def lib():
         L.orc_action.argtypes = [i, i, i, i, P, i, i, i, P, P, P, i, i]
         L.orc_cell_matrices.argtypes = [i, i, i, i, P, i, i, i, P, i64, i64, P, i]
         L.orc_energy.argtypes = [i, i, i, P, i, i, i, P, P, P]
+        L.orc_cell_vectors_rule.argtypes = [i, i, i, i, i, P, i, i, i, P, P, i, P, i64, P, i]
+        L.orc_action_rule.argtypes = [i, i, i, i, i, P, i, i, i, P, P, P, i, i]
+        L.orc_cell_matrices_rule.argtypes = [i, i, i, i, i, P, i, i, i, P, i64, i64, P, i]
         L.orc_q_node_coords.argtypes = [i, i, i, i, P, P]
         L.orc_interp_grad_q_to_nce.argtypes = [i, i, i, i, P, P]
         L.orc_interp_curl_nce_to_ncf.argtypes = [i, i, i, i, P, P]
@@ -113,8 +118,9 @@ def _params(form, params):
     return _f64(DEFAULT_PARAMS[form] if params is None else params)
 
 
-def action(family, form, p, dims, coords, x, nq=None, params=None, nthreads=0):
-    """y = sum_K P_K^T b^K.  x: (ndof,) or (ndof, nrhs)."""
+def action(family, form, p, dims, coords, x, nq=None, params=None, nthreads=0, qrule="GL"):
+    """y = sum_K P_K^T b^K.  x: (ndof,) or (ndof, nrhs).  qrule "GLL" with the
+    default nq = p + 1 is the collocated (underintegrated) rule."""
     ndof, nloc = space_size(family, p, dims)
     x = _f64(x)
     nrhs = 1 if x.ndim == 1 else x.shape[1]
@@ -122,12 +128,12 @@ def action(family, form, p, dims, coords, x, nq=None, params=None, nthreads=0):
     y = np.zeros_like(x)
     pr = _params(form, params)
     coords = _f64(coords)
-    _check(lib().orc_action(FAMILIES[family], FORMS[form], p, nq or p + 1, _p(pr), *dims,
-                            _p(coords), _p(x), _p(y), nrhs, nthreads), "action")
+    _check(lib().orc_action_rule(FAMILIES[family], FORMS[form], p, nq or p + 1, QRULES[qrule], _p(pr), *dims,
+                                 _p(coords), _p(x), _p(y), nrhs, nthreads), "action")
     return y
 
 
-def cell_vectors(family, form, p, dims, coords, x, cells, nq=None, params=None, nthreads=0):
+def cell_vectors(family, form, p, dims, coords, x, cells, nq=None, params=None, nthreads=0, qrule="GL"):
     """Per-cell local vectors b^K for the listed cells: (ncells, nloc[, nrhs])."""
     ndof, nloc = space_size(family, p, dims)
     x = _f64(x)
@@ -136,14 +142,14 @@ def cell_vectors(family, form, p, dims, coords, x, cells, nq=None, params=None, 
     b = np.zeros((len(cells), nloc, nrhs))
     pr = _params(form, params)
     coords = _f64(coords)
-    _check(lib().orc_cell_vectors(FAMILIES[family], FORMS[form], p, nq or p + 1, _p(pr), *dims,
-                                  _p(coords), _p(x), nrhs, _p(cells), len(cells), _p(b), nthreads),
+    _check(lib().orc_cell_vectors_rule(FAMILIES[family], FORMS[form], p, nq or p + 1, QRULES[qrule], _p(pr),
+                                       *dims, _p(coords), _p(x), nrhs, _p(cells), len(cells), _p(b), nthreads),
            "cell_vectors")
     return b[:, :, 0] if x.ndim == 1 else b
 
 
 def cell_matrices(family, form, p, dims, coords, cell_begin=0, cell_end=None, nq=None,
-                  params=None, nthreads=0):
+                  params=None, nthreads=0, qrule="GL"):
     """A[c, j, i], row = test j, column = trial i."""
     ndof, nloc = space_size(family, p, dims)
     ncell = dims[0] * dims[1] * dims[2]
@@ -151,8 +157,8 @@ def cell_matrices(family, form, p, dims, coords, cell_begin=0, cell_end=None, nq
     A = np.zeros((cell_end - cell_begin, nloc, nloc))
     pr = _params(form, params)
     coords = _f64(coords)
-    _check(lib().orc_cell_matrices(FAMILIES[family], FORMS[form], p, nq or p + 1, _p(pr), *dims,
-                                   _p(coords), cell_begin, cell_end, _p(A), nthreads), "cell_matrices")
+    _check(lib().orc_cell_matrices_rule(FAMILIES[family], FORMS[form], p, nq or p + 1, QRULES[qrule], _p(pr),
+                                        *dims, _p(coords), cell_begin, cell_end, _p(A), nthreads), "cell_matrices")
     return A
 
 

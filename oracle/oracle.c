@@ -292,15 +292,20 @@ static void tab_free(tab_t* T) {
   free(T->xq); free(T->wq); free(T->val); free(T->grad); free(T->comp);
 }
 
-static int tabulate(const elem_t* E, int nq, tab_t* T) {
+/* qrule: ORC_GL (Gauss-Legendre, the default of every form) or ORC_GLL
+ * (Gauss-Lobatto-Legendre; with nq = p + 1 on a Q_p element the points are
+ * the element's own nodes: the collocated rule of Sec. 2.5 that the
+ * "underintegration" experiment of Sec. 4.1 uses). */
+static int tabulate(const elem_t* E, int nq, int qrule, tab_t* T) {
   memset(T, 0, sizeof(*T));
-  if (nq < 1 || nq > 32) return -1;
+  if (nq < 1 || nq > 32 || (qrule != ORC_GL && qrule != ORC_GLL) || (qrule == ORC_GLL && nq < 2)) return -1;
   T->nq = nq;
   T->nq3 = nq * nq * nq;
   T->nloc = E->nloc;
   T->xq = (double*)malloc(sizeof(double) * nq);
   T->wq = (double*)malloc(sizeof(double) * nq);
-  orc_gauss_legendre(nq, T->xq, T->wq);
+  if (qrule == ORC_GLL) orc_gauss_lobatto(nq, T->xq, T->wq);
+  else orc_gauss_legendre(nq, T->xq, T->wq);
   T->val = (double*)malloc(sizeof(double) * T->nq3 * E->nloc);
   T->grad = (double*)malloc(sizeof(double) * T->nq3 * E->nloc * 3);
   T->comp = (int*)malloc(sizeof(int) * E->nloc);
@@ -647,10 +652,18 @@ int orc_cell_vectors(int family, int form, int p, int nq, const double* params,
                      int nx, int ny, int nz, const double* coords,
                      const double* x, int nrhs, const int64_t* cells, int64_t ncells,
                      double* b, int nthreads) {
+  return orc_cell_vectors_rule(family, form, p, nq, ORC_GL, params, nx, ny, nz, coords, x, nrhs, cells, ncells, b,
+                               nthreads);
+}
+
+int orc_cell_vectors_rule(int family, int form, int p, int nq, int qrule, const double* params,
+                          int nx, int ny, int nz, const double* coords,
+                          const double* x, int nrhs, const int64_t* cells, int64_t ncells,
+                          double* b, int nthreads) {
   elem_t E;
   if (make_elem(family, p, nx, ny, nz, &E) || !form_ok(family, form) || nrhs < 1) return -1;
   tab_t T;
-  if (tabulate(&E, nq, &T)) return -1;
+  if (tabulate(&E, nq, qrule, &T)) return -1;
   int64_t ncell = (int64_t)nx * ny * nz;
   int err = 0;
   int nt = nthreads_of(nthreads);
@@ -680,6 +693,12 @@ int orc_cell_vectors(int family, int form, int p, int nq, const double* params,
 int orc_action(int family, int form, int p, int nq, const double* params,
                int nx, int ny, int nz, const double* coords,
                const double* x, double* y, int nrhs, int nthreads) {
+  return orc_action_rule(family, form, p, nq, ORC_GL, params, nx, ny, nz, coords, x, y, nrhs, nthreads);
+}
+
+int orc_action_rule(int family, int form, int p, int nq, int qrule, const double* params,
+                    int nx, int ny, int nz, const double* coords,
+                    const double* x, double* y, int nrhs, int nthreads) {
   elem_t E;
   if (make_elem(family, p, nx, ny, nz, &E) || !form_ok(family, form) || nrhs < 1) return -1;
   memset(y, 0, sizeof(double) * E.ndof * nrhs);
@@ -692,7 +711,8 @@ int orc_action(int family, int form, int p, int nq, const double* params,
   for (int64_t c0 = 0; c0 < ncell && !err; c0 += CH) {
     int64_t m = (ncell - c0 < CH) ? ncell - c0 : CH;
     for (int64_t k = 0; k < m; ++k) cells[k] = c0 + k;
-    err = orc_cell_vectors(family, form, p, nq, params, nx, ny, nz, coords, x, nrhs, cells, m, b, nthreads);
+    err = orc_cell_vectors_rule(family, form, p, nq, qrule, params, nx, ny, nz, coords, x, nrhs, cells, m, b,
+                                nthreads);
     /* global assembly y += P_K^T b^K, cells in order */
     for (int64_t k = 0; k < m && !err; ++k) {
       elem_cell_dofs(&E, ny, nz, c0 + k, dofs);
@@ -709,13 +729,20 @@ int orc_action(int family, int form, int p, int nq, const double* params,
 int orc_cell_matrices(int family, int form, int p, int nq, const double* params,
                       int nx, int ny, int nz, const double* coords,
                       int64_t cell_begin, int64_t cell_end, double* A, int nthreads) {
+  return orc_cell_matrices_rule(family, form, p, nq, ORC_GL, params, nx, ny, nz, coords, cell_begin, cell_end, A,
+                                nthreads);
+}
+
+int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const double* params,
+                           int nx, int ny, int nz, const double* coords,
+                           int64_t cell_begin, int64_t cell_end, double* A, int nthreads) {
   elem_t E;
   if (make_elem(family, p, nx, ny, nz, &E) || !form_ok(family, form)) return -1;
   if (form == ORC_NEOHOOKE || form == ORC_SVK) return -1;
   int64_t ncell = (int64_t)nx * ny * nz;
   if (cell_begin < 0 || cell_end > ncell || cell_begin > cell_end) return -1;
   tab_t T;
-  if (tabulate(&E, nq, &T)) return -1;
+  if (tabulate(&E, nq, qrule, &T)) return -1;
   int nloc = E.nloc;
   int err = 0;
   int nt = nthreads_of(nthreads);
@@ -797,7 +824,7 @@ int orc_energy(int form, int p, int nq, const double* params,
   elem_t E;
   if (make_elem(ORC_VQ, p, nx, ny, nz, &E) || !(form == ORC_NEOHOOKE || form == ORC_SVK)) return -1;
   tab_t T;
-  if (tabulate(&E, nq, &T)) return -1;
+  if (tabulate(&E, nq, ORC_GL, &T)) return -1;
   int64_t ncell = (int64_t)nx * ny * nz;
   int64_t* dofs = (int64_t*)malloc(sizeof(int64_t) * E.nloc);
   double total = 0.0;

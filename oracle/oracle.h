@@ -72,6 +72,21 @@ int orc_action(int family, int form, int p, int nq, const double* params,
 int orc_cell_matrices(int family, int form, int p, int nq, const double* params,
                       int nx, int ny, int nz, const double* coords,
                       int64_t cell_begin, int64_t cell_end, double* A, int nthreads);
+/* The same three routines with the quadrature rule chosen: qrule = ORC_GL
+ * (Gauss-Legendre, what the routines above use) or ORC_GLL (Gauss-Lobatto-
+ * Legendre, nq >= 2).  With nq = p + 1 on Q_p the GLL points are the element's
+ * nodes (collocated quadrature, Sec. 2.5, Eq. colocated; the "underintegration"
+ * case of Sec. 4.1). */
+int orc_cell_vectors_rule(int family, int form, int p, int nq, int qrule, const double* params,
+                          int nx, int ny, int nz, const double* coords,
+                          const double* x, int nrhs, const int64_t* cells, int64_t ncells,
+                          double* b, int nthreads);
+int orc_action_rule(int family, int form, int p, int nq, int qrule, const double* params,
+                    int nx, int ny, int nz, const double* coords,
+                    const double* x, double* y, int nrhs, int nthreads);
+int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const double* params,
+                           int nx, int ny, int nz, const double* coords,
+                           int64_t cell_begin, int64_t cell_end, double* A, int nthreads);
 /* Hyperelastic stored energy W(u) (NEOHOOKE or SVK), summed over cells. */
 int orc_energy(int form, int p, int nq, const double* params,
                int nx, int ny, int nz, const double* coords,
