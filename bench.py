@@ -29,6 +29,7 @@ HELM = (1.0, -1.0, 0.0, 0.0)  # alpha * laplace + beta * mass, beta = -k^2, k = 
 # clock x 2.07 GHz; as flops (FMA = 2) this is the 1.26 TFLOP/s nominal figure
 FP64_PEAK_GOPS = 152 * 2 * 2.07
 L2_FLUSH_BYTES = 256 << 20
+HBM_GBS = 6788.3             # GB300 HBM bandwidth, measured by a STREAM-style copy (GB/s)
 METRIC = "DoFs/s of the operator action (config-2 sweep)"
 # DRAM bytes (read + write) per cell of one colour launch, from the ncu captures of
 # the 32^3, p = 8 case (dram__bytes.sum.per_second x gpu__time_duration / 4096
@@ -550,6 +551,11 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
                      "sumfact_dofs_per_s": sp.ndof / (ts * 1e-3), "naive_dofs_per_s": sp.ndof / (tn * 1e-3)})
         del xd, yd, sp
     ex["naive_vs_sumfact_Q_laplace_32cube"] = rows
+    # --- underintegration (Sec. 4.1): Q_p Laplace on the collocated Gauss-Lobatto rule (B = I) vs the
+    #     (p+1)-point Gauss rule; actions on 64^3 (FP64, TF32x3), element matrices on a 32^3 chunk
+    #     (delta-cancelled O(n^5) kernel vs the sum-factorised O(n^7) kernel)
+    ex["underintegration"] = underint_block(sfx, torch, ctx, inputs, flush, stream)
+    torch.cuda.empty_cache()
     # --- element matrices (FP64): Q_p Laplace p=1..8 and NCF/NCE p=1..5 on 32^3,
     #     on a chunk of cells sized to ~1 GB of output; sum-factorised and, p <= 4, naive
     rows = []
@@ -581,6 +587,52 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
                   "flushed); DoFs/s follows the paper's N/t; dofs_per_s_paper for matrices scales N by the "
                   "fraction of cells assembled")
     return ex
+
+
+def underint_block(sfx, torch, ctx, inputs, flush, stream):
+    """Collocated (GLL) vs Gauss rule: Laplace action DoF/s on 64^3, p = 1..8,
+    FP64 and TF32x3; Laplace element matrices on the first cells of a 32^3
+    mesh (about 1 GB of output), delta-cancelled vs sum-factorised, with the
+    bytes written per second (the collocated kernel's dense n^6 output)."""
+    mesh = sfx.Mesh.box(ctx, 64, 64, 64, perturb=0.1, seed=0)
+    acts = []
+    for p in range(1, 9):
+        sp = sfx.Space(mesh, "Q", p)
+        xd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
+        yd = torch.empty_like(xd)
+        row = {"p": p, "ndof": sp.ndof}
+        for prec in ("fp64", "tf32x3"):
+            for algo in ("collocated", "sumfact"):
+                t = _time(torch, stream, flush, lambda: sfx.sfx_assemble_action(ctx, "laplace", sp, xd, yd,
+                                                                                precision=prec, algo=algo,
+                                                                                stream=stream))
+                row["%s_%s_ms" % (algo, prec)] = round(t, 4)
+                row["%s_%s_dofs_per_s" % (algo, prec)] = sp.ndof / (t * 1e-3)
+            row["speedup_collocated_vs_gauss_" + prec] = row["sumfact_%s_ms" % prec] / row["collocated_%s_ms" % prec]
+        acts.append(row)
+        del xd, yd, sp
+    del mesh
+    torch.cuda.empty_cache()
+    mesh = sfx.Mesh.box(ctx, 32, 32, 32, perturb=0.1, seed=0)
+    mats = []
+    for p in range(1, 9):
+        sp = sfx.Space(mesh, "Q", p)
+        nc = int(min(sp.ncell, max(8, (1 << 30) // (sp.nloc * sp.nloc * 8))))
+        A = torch.empty(nc * sp.nloc * sp.nloc, dtype=torch.float64, device="cuda")
+        tc = _time(torch, stream, flush, lambda: sfx.sfx_assemble_cell_matrices(ctx, "laplace", sp, 0, nc, A,
+                                                                                algo="collocated", stream=stream))
+        ts = _time(torch, stream, flush, lambda: sfx.sfx_assemble_cell_matrices(ctx, "laplace", sp, 0, nc, A,
+                                                                                stream=stream), reps=2, warm=1)
+        gbs = nc * sp.nloc ** 2 * 8 / (tc * 1e-3) / 1e9
+        mats.append({"p": p, "cells": nc, "nloc": sp.nloc, "collocated_ms": round(tc, 4), "sumfact_ms": round(ts, 4),
+                     "speedup": ts / tc, "collocated_cells_per_s": nc / (tc * 1e-3),
+                     "collocated_gb_per_s_written": gbs, "collocated_write_frac_of_hbm": gbs / HBM_GBS})
+        del A, sp
+        torch.cuda.empty_cache()
+    status = ctx.sync_status()
+    return {"action_64cube": acts, "matrices_32cube": mats, "device_status": status,
+            "note": "collocated = (p+1)-point Gauss-Lobatto rule on the GLL nodes (B = I): fewer contractions "
+                    "and a different (under-integrated) operator; matrices: dense n^3 x n^3 output per cell"}
 
 
 def precision_block(sfx, torch, ctx, inputs, flush, stream, dims=(64, 64, 64), degrees=range(3, 9),

@@ -91,9 +91,16 @@ typedef enum { SFX_NODES_GLL = 0, SFX_NODES_GL = 1 } sfx_nodes;
  * Q_p (neo-Hookean, SVK); NCF/NCE accept FP64 only. */
 typedef enum { SFX_PREC_FP64 = 0, SFX_PREC_TF32X3 = 1, SFX_PREC_BF16X3 = 2 } sfx_precision;
 
-/* SUMFACT: sum-factorised kernels.  NAIVE: dense 3D tabulation, O(n^6) per
- * cell for the action (the un-factorised form of Sec. 3.2, for comparison). */
-typedef enum { SFX_ALGO_SUMFACT = 0, SFX_ALGO_NAIVE = 1 } sfx_algo;
+/* SUMFACT: sum-factorised kernels on the (p+1)-point Gauss rule.  NAIVE:
+ * dense 3D tabulation, O(n^6) per cell for the action (the un-factorised form
+ * of Sec. 3.2, for comparison).  COLLOCATED: Q_p mass / Laplace / Helmholtz
+ * on the (p+1)-point Gauss-Lobatto rule, whose points are the GLL nodes of
+ * Q_p (Sec. 2.5, Eq. colocated): the value tabulation is the identity, so
+ * the action needs only the derivative contractions and the element matrix
+ * is delta-cancelled to O(n^5) work (the "underintegration" case of Sec. 4.1;
+ * the rule does not integrate these forms exactly, by design).  The action
+ * accepts FP64 and TF32X3, the element matrices FP64. */
+typedef enum { SFX_ALGO_SUMFACT = 0, SFX_ALGO_NAIVE = 1, SFX_ALGO_COLLOCATED = 2 } sfx_algo;
 
 typedef struct sfx_ctx sfx_ctx;
 typedef struct sfx_mesh sfx_mesh;

@@ -21,7 +21,7 @@ FORM = {"mass": 0, "laplace": 1, "helmholtz": 2, "ncf_mass_divdiv": 3, "nce_curl
         "neohooke": 5, "svk": 6}
 NODES = {"GLL": 0, "GL": 1}
 PRECISION = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
-ALGO = {"sumfact": 0, "naive": 1}
+ALGO = {"sumfact": 0, "naive": 1, "collocated": 2}
 DEV_INVERTED, DEV_DETF, DEV_BADCELL = 1, 2, 4
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported combination", -3: "CUDA runtime error",
           -4: "allocation failed", -5: "size exceeds 32-bit indexing"}

@@ -234,6 +234,100 @@ __global__ void __launch_bounds__(kMatThreads) k_cell_matrices(const MatArgs a, 
     }
 }
 
+// Element matrices of the scalar forms on Q_p with the collocated Gauss-
+// Lobatto rule (Sec. 4.1, "underintegration"): the points are the nodes, so a
+// reference derivative of a basis function at a point is one 1D derivative
+// table times two deltas,
+//   d psi_r / d xi_1 (q) = D[q1][r1] delta(q2, r2) delta(q3, r3)   (cyclic),
+// with D[a][b] = l_b'(x_a) the GLL collocation derivative.  Substituting this
+// into A_rs = sum_q sum_kl C_kl(q) d_k psi_r(q) d_l psi_s(q) + M(q) psi_r psi_s
+// cancels every sum but one (delta cancellation, Sec. 3.1 / 3.4):
+//   k = l = 1:  [r2 = s2, r3 = s3]  sum_q1 C_11(q1,r2,r3) D[q1][r1] D[q1][s1]
+//   k=1, l=2:   [r3 = s3]           C_12(s1,r2,r3) D[s1][r1] D[r2][s2]
+//   k=2, l=1:   [r3 = s3]           C_12(r1,s2,r3) D[s2][r2] D[r1][s1]
+//   (and cyclically), mass:  [r = s]  M(r)
+// with C = w S G G^T = (w/S) adj(J) adj(J)^T and M = w S at the GLL points:
+// O(n^5) arithmetic per cell instead of the O(n^7) of the sum-factorised
+// kernel above; the dense n^3 x n^3 output (zeros included) is written with
+// consecutive columns on consecutive threads.
+template <int N>
+__global__ void __launch_bounds__(kMatThreads) k_cell_matrices_coll(const MatArgs a) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const Tab1D& T = c_tab[N - 1];
+  extern __shared__ double sm[];
+  double* D = sm;              // [a][b] = l_b'(x_a)
+  double* xq = D + N2;         // 16
+  double* wq = xq + 16;        // 16
+  double* X = wq + 16;         // 24
+  double* Jc = X + 24;         // [3][N2][3]
+  double* C = Jc + 9 * N2;     // [7][N3]: C_00, C_11, C_22, C_01, C_02, C_12, M
+  int* bad = reinterpret_cast<int*>(C + 7 * N3);
+  const int tid = threadIdx.x;
+  const int64_t cell = a.cell_begin + blockIdx.x;
+  for (int i = tid; i < N2; i += kMatThreads) D[i] = T.Dg[i / N][i % N];
+  if (tid < N) {
+    xq[tid] = T.xg[tid];
+    wq[tid] = T.wg[tid];
+  }
+  if (tid < 24) X[tid] = a.xyz[(int64_t)a.vmap[cell * 8 + tid / 3] * 3 + tid % 3];
+  if (tid == 0) *bad = 0;
+  __syncthreads();
+  for (int i = tid; i < N2; i += kMatThreads)
+    jacobian_columns<N>(reinterpret_cast<const double(*)[3]>(X), xq, reinterpret_cast<double(*)[N2][3]>(Jc), i);
+  __syncthreads();
+  for (int qp = tid; qp < N3; qp += kMatThreads) {
+    const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
+    double r0[3], r1[3], r2[3];
+    const double S = point_rows<N, true>(reinterpret_cast<const double(*)[N2][3]>(Jc), qp, r0, r1, r2);
+    if (!(S > 0.0)) *bad = 1;
+    const double w = wq[q1] * wq[q2] * wq[q3];
+    const double ws = a.alpha * w * recip_nr<2>(S);
+    C[0 * N3 + qp] = ws * dot3(r0, r0);
+    C[1 * N3 + qp] = ws * dot3(r1, r1);
+    C[2 * N3 + qp] = ws * dot3(r2, r2);
+    C[3 * N3 + qp] = ws * dot3(r0, r1);
+    C[4 * N3 + qp] = ws * dot3(r0, r2);
+    C[5 * N3 + qp] = ws * dot3(r1, r2);
+    C[6 * N3 + qp] = a.beta * w * S;
+  }
+  __syncthreads();
+  double* Ac = a.A + (int64_t)blockIdx.x * N3 * N3;
+  if (*bad) {
+    if (tid == 0) set_flag(a.status, SFX_DEV_INVERTED);
+    for (int i = tid; i < N3 * N3; i += kMatThreads) Ac[i] = 0.0;
+    return;
+  }
+  auto at = [&](int k, int q1, int q2, int q3) { return C[k * N3 + (q1 * N + q2) * N + q3]; };
+  auto d = [&](int q, int i) { return D[q * N + i]; };
+  for (int e = tid; e < N3 * N3; e += kMatThreads) {
+    const int row = e / N3, col = e - (e / N3) * N3;
+    const int r1 = row / N2, r2 = (row / N) % N, r3 = row % N;
+    const int s1 = col / N2, s2 = (col / N) % N, s3 = col % N;
+    const bool e1 = r1 == s1, e2 = r2 == s2, e3 = r3 == s3;
+    double acc = 0.0;
+    if (e2 && e3)
+      for (int q = 0; q < N; ++q) acc = fma(at(0, q, r2, r3), d(q, r1) * d(q, s1), acc);
+    if (e1 && e3)
+      for (int q = 0; q < N; ++q) acc = fma(at(1, r1, q, r3), d(q, r2) * d(q, s2), acc);
+    if (e1 && e2)
+      for (int q = 0; q < N; ++q) acc = fma(at(2, r1, r2, q), d(q, r3) * d(q, s3), acc);
+    if (e3) {  // (k, l) = (1, 2) and (2, 1)
+      acc = fma(at(3, s1, r2, r3), d(s1, r1) * d(r2, s2), acc);
+      acc = fma(at(3, r1, s2, r3), d(s2, r2) * d(r1, s1), acc);
+    }
+    if (e2) {  // (1, 3) and (3, 1)
+      acc = fma(at(4, s1, r2, r3), d(s1, r1) * d(r3, s3), acc);
+      acc = fma(at(4, r1, r2, s3), d(s3, r3) * d(r1, s1), acc);
+    }
+    if (e1) {  // (2, 3) and (3, 2)
+      acc = fma(at(5, r1, s2, r3), d(s2, r2) * d(r3, s3), acc);
+      acc = fma(at(5, r1, r2, s3), d(s3, r3) * d(r2, s2), acc);
+    }
+    if (row == col) acc += at(6, r1, r2, r3);
+    Ac[e] = acc;
+  }
+}
+
 // ---------------------------------------------------------------- host side
 void add_term(MatDesc& d, int bt, int bs, int cid, double sign, const int* tt, const int* ts) {
   MatTerm& m = d.term[d.nterm++];
@@ -380,6 +474,36 @@ int launch_cell_matrices(const sfx_space* sp, sfx_form form, sfx_algo algo, cons
     k_cell_matrices<false><<<(unsigned)a.ncells, kMatThreads, smem, s>>>(a, d, sp->p);
   }
   return (int)cudaGetLastError();
+}
+
+template <int N>
+int launch_coll(const MatArgs& a, cudaStream_t s) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const size_t smem = sizeof(double) * (N2 + 32 + 24 + 9 * N2 + 7 * N3) + 16;
+  cudaError_t e = cudaFuncSetAttribute(k_cell_matrices_coll<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  k_cell_matrices_coll<N><<<(unsigned)a.ncells, kMatThreads, smem, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int launch_cell_matrices_coll(const sfx_space* sp, sfx_form form, const MatArgs& a0, void* stream) {
+  if (sp->family != SFX_Q) return -1;
+  if (form != SFX_MASS && form != SFX_LAPLACE && form != SFX_HELMHOLTZ) return -1;
+  MatArgs a = a0;
+  if (form == SFX_MASS) { a.alpha = 0.0; a.beta = 1.0; }
+  if (form == SFX_LAPLACE) { a.alpha = 1.0; a.beta = 0.0; }
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (sp->p) {
+    case 1: return launch_coll<2>(a, s);
+    case 2: return launch_coll<3>(a, s);
+    case 3: return launch_coll<4>(a, s);
+    case 4: return launch_coll<5>(a, s);
+    case 5: return launch_coll<6>(a, s);
+    case 6: return launch_coll<7>(a, s);
+    case 7: return launch_coll<8>(a, s);
+    case 8: return launch_coll<9>(a, s);
+  }
+  return -1;
 }
 
 }  // namespace sfx

@@ -64,7 +64,11 @@ __device__ __forceinline__ double point_factors(const double (*Jc)[N * N][3], co
 
 // One tile: the cb cells of slots slot0 .. slot0+cb-1, one team of N^2 threads
 // per cell (threads of teams >= cb idle but take part in the barriers).
-template <int N, bool DQ, int FORM, bool STORED = false>
+// COLL: the collocated Gauss-Lobatto rule on the GLL nodes of Q_p (Sec. 2.5,
+// "underintegration" in Sec. 4.1): the points are the nodes, so B = I as for
+// DQ_p, the derivative table is the GLL collocation matrix and the geometry is
+// evaluated at the GLL points with the GLL weights.
+template <int N, bool DQ, int FORM, bool STORED = false, bool COLL = false>
 __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t ncell_total, const int64_t slot0,
                                                  const int cb, double* sm, const bool geo_once) {
   using Sh = ScalarShape<N, FORM>;
@@ -92,8 +96,10 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
   double* K = X0 + 24 + 9 * N2 + 1;                  // K[c][qp] (geo_once only)
   double* WS = K + (LAP ? 6 * N3 : 0);               // WS[qp]   (geo_once only)
 
-  for (int i = threadIdx.x; i < N3; i += blockDim.x) W3[i] = T.w[i / N2] * T.w[(i / N) % N] * T.w[i % N];
-  if (threadIdx.x < N) xq[threadIdx.x] = T.x[threadIdx.x];
+  const double* tw = COLL ? T.wg : T.w;
+  const double(*TD)[kMaxQ] = COLL ? T.Dg : T.Dq;  // derivative at the points
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) W3[i] = tw[i / N2] * tw[(i / N) % N] * tw[i % N];
+  if (threadIdx.x < N) xq[threadIdx.x] = COLL ? T.xg[threadIdx.x] : T.x[threadIdx.x];
 
   int cell = 0;
   const int64_t slot = slot0 + team;
@@ -147,7 +153,7 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
   for (int r = a.r0; r < a.r1; ++r) {
     for (int l = tl; l < N3; l += N2) U[l] = active ? a.x[dof(l) * a.nrhs + r] : 0.0;
     __syncthreads();
-    if (!DQ) {
+    if (!DQ && !COLL) {
       if (member) contract<N, N, N, 0, N, false, false, kMaxN>(U, U, T.Bc, t);
       __syncthreads();
       if (member) contract<N, N, N, 1, N, false, false, kMaxN>(U, U, T.Bc, t);
@@ -157,9 +163,9 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
     }
     if (LAP) {
       if (member) {
-        contract<N, N, N, 0, N, false, false, kMaxQ>(U, G0, T.Dq, t);
-        contract<N, N, N, 1, N, false, false, kMaxQ>(U, G1, T.Dq, t);
-        contract<N, N, N, 2, N, false, false, kMaxQ>(U, G2, T.Dq, t);
+        contract<N, N, N, 0, N, false, false, kMaxQ>(U, G0, TD, t);
+        contract<N, N, N, 1, N, false, false, kMaxQ>(U, G1, TD, t);
+        contract<N, N, N, 2, N, false, false, kMaxQ>(U, G2, TD, t);
       }
       __syncthreads();
     }
@@ -204,14 +210,14 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
     }
     __syncthreads();
     if (LAP) {
-      if (member) contract<N, N, N, 0, N, true, MAS, kMaxQ>(G0, U, T.Dq, t);
+      if (member) contract<N, N, N, 0, N, true, MAS, kMaxQ>(G0, U, TD, t);
       __syncthreads();
-      if (member) contract<N, N, N, 1, N, true, true, kMaxQ>(G1, U, T.Dq, t);
+      if (member) contract<N, N, N, 1, N, true, true, kMaxQ>(G1, U, TD, t);
       __syncthreads();
-      if (member) contract<N, N, N, 2, N, true, true, kMaxQ>(G2, U, T.Dq, t);
+      if (member) contract<N, N, N, 2, N, true, true, kMaxQ>(G2, U, TD, t);
       __syncthreads();
     }
-    if (!DQ) {
+    if (!DQ && !COLL) {
       if (member) contract<N, N, N, 0, N, true, false, kMaxN>(U, U, T.Bc, t);
       __syncthreads();
       if (member) contract<N, N, N, 1, N, true, false, kMaxN>(U, U, T.Bc, t);

@@ -98,7 +98,10 @@ __device__ __forceinline__ double mixed_point_factors(const double* tab, const d
 
 // STORED: the FP32 factors come from a.qd32 (sfx_qdata) and no FP64 geometry
 // runs in the kernel.  geo_once: stage the factors once per cell for all RHS.
-template <int N, bool DQ, int FORM, int PREC, bool STORED>
+// COLL: the collocated Gauss-Lobatto rule on the GLL nodes of Q_p (the points
+// are the nodes: B = I, derivative table = GLL collocation matrix, geometry at
+// the GLL points with the GLL weights; Sec. 2.5 and "underintegration" in 4.1).
+template <int N, bool DQ, int FORM, int PREC, bool STORED, bool COLL = false>
 __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs a, const int64_t ncell_total,
                                                                   const int cb, const bool geo_once) {
   using Sh = MixedShape<N, FORM>;
@@ -124,11 +127,11 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
   for (int i = tid; i < 16 * 16; i += kThreads) {
     const int r = i / 16, k = i % 16;
     tabs[0].v[r][k] = (r < N && k < N) ? (float)T.Bc[r][k] : 0.f;
-    tabs[1].v[r][k] = (r < N && k < N) ? (float)T.Dq[r][k] : 0.f;
+    tabs[1].v[r][k] = (r < N && k < N) ? (float)(COLL ? T.Dg[r][k] : T.Dq[r][k]) : 0.f;
   }
   if (tid < N) {
-    xq[tid] = T.x[tid];
-    wq[tid] = T.w[tid];
+    xq[tid] = COLL ? T.xg[tid] : T.x[tid];
+    wq[tid] = COLL ? T.wg[tid] : T.w[tid];
   }
   for (int c = tid; c < cb; c += kThreads) {
     int cell = -1;
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
       U[i] = cell >= 0 ? d2f_int(a.x[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r]) : 0.f;
     }
     __syncthreads();
-    if (!DQ) {
+    if (!DQ && !COLL) {
       tc_contract<N, 0, false, false, PREC>(U, U, tabs[0], cb);
       __syncthreads();
       tc_contract<N, 1, false, false, PREC>(U, U, tabs[0], cb);
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
       tc_contract<N, 2, true, true, PREC>(G2, U, tabs[1], cb);
       __syncthreads();
     }
-    if (!DQ) {
+    if (!DQ && !COLL) {
       tc_contract<N, 0, true, false, PREC>(U, U, tabs[0], cb);
       __syncthreads();
       tc_contract<N, 1, true, false, PREC>(U, U, tabs[0], cb);

@@ -184,6 +184,10 @@ void make_tab1d(int p, Tab1D* t) {
   for (int a = 0; a < q; ++a) for (int j = 0; j < p; ++j) t->Dd[a][j] = tmp[a * p + j];
   lagrange_table(t->x, q, t->x, q, 1, tmp);
   for (int a = 0; a < q; ++a) for (int j = 0; j < q; ++j) t->Dq[a][j] = tmp[a * q + j];
+  // collocated Gauss-Lobatto rule on the GLL nodes
+  for (int a = 0; a < n; ++a) { t->xg[a] = xc[a]; t->wg[a] = wc[a]; }
+  lagrange_table(xc, n, xc, n, 1, tmp);
+  for (int a = 0; a < n; ++a) for (int j = 0; j < n; ++j) t->Dg[a][j] = tmp[a * n + j];
 }
 
 }  // namespace sfx
@@ -200,6 +204,8 @@ static int upload_tables(const Tab1D* t) {
   if (!e) e = upload_tab_matrix(t);
   if (!e) e = upload_tab_naive(t);
   if (!e) e = upload_tab_batched(t);
+  if (!e) e = upload_tab_scalar_coll(t);
+  if (!e) e = upload_tab_scalar_mixed_coll(t);
   return e;
 }
 
@@ -550,8 +556,12 @@ extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx
   if (!ctx || !sp || !x || !y || nrhs < 1 || nrhs > 64 || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
   if (!form_ok(sp->family, form)) return SFX_ERR_ARG;
   if (x == y) return SFX_ERR_ARG;
-  if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3 || (algo != SFX_ALGO_SUMFACT && algo != SFX_ALGO_NAIVE))
+  if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3 ||
+      (algo != SFX_ALGO_SUMFACT && algo != SFX_ALGO_NAIVE && algo != SFX_ALGO_COLLOCATED))
     return SFX_ERR_ARG;
+  if (algo == SFX_ALGO_COLLOCATED &&
+      (sp->family != SFX_Q || (prec != SFX_PREC_FP64 && prec != SFX_PREC_TF32X3)))
+    return SFX_ERR_UNSUPPORTED;
   sfx_form_params pr = params ? *params : default_params(form);
   cudaStream_t s = (cudaStream_t)stream;
   if (!accumulate) {
@@ -574,7 +584,10 @@ extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx
     a.ncells = sp->colour_off[col + 1] - sp->colour_off[col];
     if (a.ncells == 0) continue;
     int e;
-    if (sp->family == SFX_Q || sp->family == SFX_DQ) e = launch_action_scalar(sp, form, prec, algo, a, stream);
+    if (algo == SFX_ALGO_COLLOCATED)
+      e = prec == SFX_PREC_FP64 ? launch_action_scalar_coll(sp, form, a, stream)
+                                : launch_action_scalar_mixed_coll(sp, form, a, stream);
+    else if (sp->family == SFX_Q || sp->family == SFX_DQ) e = launch_action_scalar(sp, form, prec, algo, a, stream);
     else if (algo != SFX_ALGO_SUMFACT) return SFX_ERR_UNSUPPORTED;
     else if (sp->family == SFX_VQ) e = launch_action_elastic(sp, form, prec, a, stream);
     else e = launch_action_hdivcurl(sp, form, prec, a, stream);
@@ -625,7 +638,8 @@ extern "C" sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, co
   if (!form_ok(sp->family, form) || form == SFX_NEOHOOKE || form == SFX_SVK) return SFX_ERR_ARG;
   if (cell_begin < 0 || cell_end > sp->mesh->ncell || cell_begin > cell_end) return SFX_ERR_ARG;
   if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
-  if (algo != SFX_ALGO_SUMFACT && algo != SFX_ALGO_NAIVE) return SFX_ERR_ARG;
+  if (algo != SFX_ALGO_SUMFACT && algo != SFX_ALGO_NAIVE && algo != SFX_ALGO_COLLOCATED) return SFX_ERR_ARG;
+  if (algo == SFX_ALGO_COLLOCATED && sp->family != SFX_Q) return SFX_ERR_UNSUPPORTED;
   if (cell_end == cell_begin) return SFX_OK;
   sfx_form_params pr = params ? *params : default_params(form);
   MatArgs a{};
@@ -637,7 +651,8 @@ extern "C" sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, co
   a.alpha = pr.alpha;
   a.beta = pr.beta;
   a.status = ctx->d_status;
-  int e = launch_cell_matrices(sp, form, algo, a, stream);
+  int e = algo == SFX_ALGO_COLLOCATED ? launch_cell_matrices_coll(sp, form, a, stream)
+                                      : launch_cell_matrices(sp, form, algo, a, stream);
   if (e == -1) return SFX_ERR_UNSUPPORTED;
   return e ? SFX_ERR_CUDA : SFX_OK;
 }

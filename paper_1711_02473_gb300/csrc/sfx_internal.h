@@ -19,13 +19,17 @@ constexpr int kMaxQ = kMaxDeg + 1;  // 1D quadrature points per axis (q = p + 1)
 //   Bd, Dd   Gauss-node Lagrange basis with p nodes (the dP_{p-1} factor)       [q][p]
 //   Dq       collocation derivative on the Gauss points themselves              [q][q]
 //            (Dq[a][b] = l_b'(x_a), l_b the Lagrange basis on the q points)
-//   vq       (1 - x, x): the trilinear coordinate element's 1D factors at the points
+//   xg, wg   Gauss-Lobatto rule with p+1 points: the GLL nodes themselves
+//            (the collocated rule of Sec. 2.5, "underintegration" in Sec. 4.1)
+//   Dg       collocation derivative on the GLL nodes, Dg[a][b] = l_b'(xg_a)
 struct Tab1D {
   int p, q;
   double w[kMaxQ], x[kMaxQ];
   double Bc[kMaxQ][kMaxN], Dc[kMaxQ][kMaxN];
   double Bd[kMaxQ][kMaxN], Dd[kMaxQ][kMaxN];
   double Dq[kMaxQ][kMaxQ];
+  double wg[kMaxN], xg[kMaxN];
+  double Dg[kMaxN][kMaxN];
 };
 
 // 1D rules and Lagrange tables (host, double).  Newton iteration on the
@@ -114,6 +118,9 @@ int launch_action_elastic_mixed(const sfx_space* sp, sfx_form form, sfx_precisio
 int launch_action_scalar_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
                                void* stream);
 int launch_action_scalar_naive(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+// Q_p actions with the collocated GLL rule (B = I): FP64 and TF32x3.
+int launch_action_scalar_coll(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+int launch_action_scalar_mixed_coll(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
 
 struct MatArgs {
   const int32_t* vmap;
@@ -124,6 +131,8 @@ struct MatArgs {
   uint32_t* status;
 };
 int launch_cell_matrices(const sfx_space* sp, sfx_form form, sfx_algo algo, const MatArgs& a, void* stream);
+// Q_p element matrices with the collocated GLL rule, delta-cancelled (k_matrix.cu).
+int launch_cell_matrices_coll(const sfx_space* sp, sfx_form form, const MatArgs& a, void* stream);
 
 // FP64 scalar action over an explicit cell list for one degree (DQ, p-adaptive
 // plans); also used by the per-launch comparison mode.
@@ -172,5 +181,7 @@ int upload_tab_matrix(const Tab1D* t);
 int upload_tab_naive(const Tab1D* t);
 int upload_tab_batched(const Tab1D* t);
 int upload_tab_qdata(const Tab1D* t);
+int upload_tab_scalar_coll(const Tab1D* t);
+int upload_tab_scalar_mixed_coll(const Tab1D* t);
 
 }  // namespace sfx
