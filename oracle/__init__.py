@@ -61,6 +61,8 @@ def lib():
         L.orc_cell_vectors_rule.argtypes = [i, i, i, i, i, P, i, i, i, P, P, i, P, i64, P, i]
         L.orc_action_rule.argtypes = [i, i, i, i, i, P, i, i, i, P, P, P, i, i]
         L.orc_cell_matrices_rule.argtypes = [i, i, i, i, i, P, i, i, i, P, i64, i64, P, i]
+        L.orc_linearised_cell_vectors.argtypes = [i, i, i, P, i, i, i, P, P, P, i, P, i64, P, i]
+        L.orc_linearised_action.argtypes = [i, i, i, P, i, i, i, P, P, P, P, i, i]
         L.orc_q_node_coords.argtypes = [i, i, i, i, P, P]
         L.orc_interp_grad_q_to_nce.argtypes = [i, i, i, i, P, P]
         L.orc_interp_curl_nce_to_ncf.argtypes = [i, i, i, i, P, P]
@@ -160,6 +162,33 @@ def cell_matrices(family, form, p, dims, coords, cell_begin=0, cell_end=None, nq
     _check(lib().orc_cell_matrices_rule(FAMILIES[family], FORMS[form], p, nq or p + 1, QRULES[qrule], _p(pr),
                                         *dims, _p(coords), cell_begin, cell_end, _p(A), nthreads), "cell_matrices")
     return A
+
+
+def linearised_action(form, p, dims, coords, u, du, nq=None, params=None, nthreads=0):
+    """Action of the linearised hyperelastic operator at the state u on the
+    direction(s) du: (ndof,) or (ndof, nrhs)."""
+    ndof, _ = space_size("VQ", p, dims)
+    u, du = _f64(u), _f64(du)
+    nrhs = 1 if du.ndim == 1 else du.shape[1]
+    assert u.shape == (ndof,) and du.shape[0] == ndof
+    y = np.zeros_like(du)
+    pr = _params(form, params)
+    _check(lib().orc_linearised_action(FORMS[form], p, nq or p + 1, _p(pr), *dims, _p(_f64(coords)), _p(u), _p(du),
+                                       _p(y), nrhs, nthreads), "linearised_action")
+    return y
+
+
+def linearised_cell_vectors(form, p, dims, coords, u, du, cells, nq=None, params=None, nthreads=0):
+    ndof, nloc = space_size("VQ", p, dims)
+    u, du = _f64(u), _f64(du)
+    nrhs = 1 if du.ndim == 1 else du.shape[1]
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    b = np.zeros((len(cells), nloc, nrhs))
+    pr = _params(form, params)
+    _check(lib().orc_linearised_cell_vectors(FORMS[form], p, nq or p + 1, _p(pr), *dims, _p(_f64(coords)), _p(u),
+                                             _p(du), nrhs, _p(cells), len(cells), _p(b), nthreads),
+           "linearised_cell_vectors")
+    return b[:, :, 0] if du.ndim == 1 else b
 
 
 def energy(form, p, dims, coords, x, nq=None, params=None):

@@ -535,6 +535,64 @@ static int piola(int form, const double* params, double Hu[3][3], double P[3][3]
   return 0;
 }
 
+/* Directional derivative dP = (d/dt) P(I + Hu + t dH) at t = 0 of the two
+ * stress laws (the linearisation of Sec. 4.1's residual, whose action the
+ * paper benchmarks):
+ *   neo-Hookean  dP = mu dF + (mu - lambda ln J) F^{-T} dF^T F^{-T}
+ *                     + lambda tr(F^{-1} dF) F^{-T}
+ *     (from d F^{-T} = -F^{-T} dF^T F^{-T} and d ln J = tr(F^{-1} dF));
+ *   SVK          dE = (dF^T F + F^T dF)/2,  dS = lambda tr(dE) I + 2 mu dE,
+ *                dP = dF S + F dS.
+ * Returns -1 if det F <= 0 (neo-Hookean). */
+static int dpiola(int form, const double* params, double Hu[3][3], double dF[3][3], double dP[3][3]) {
+  double mu = params[2], lam = params[3];
+  double F[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) F[a][b] = Hu[a][b] + (a == b ? 1.0 : 0.0);
+  if (form == ORC_NEOHOOKE) {
+    double JF = det3(F);
+    if (!(JF > 0.0)) return -1;
+    double Fi[3][3];
+    if (inv3(F, Fi)) return -1;
+    double lnJ = log(JF);
+    double tr = 0.0; /* tr(F^{-1} dF) */
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) tr += Fi[a][b] * dF[b][a];
+    double c = (g_plant == 8) ? mu : mu - lam * lnJ;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double t = 0.0; /* (F^{-T} dF^T F^{-T})_ij = sum_kl Fi[k][i] dF[l][k] Fi[j][l] */
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) t += Fi[k][i] * dF[l][k] * Fi[j][l];
+        dP[i][j] = mu * dF[i][j] + c * t + lam * tr * Fi[j][i];
+      }
+    return 0;
+  }
+  double E[3][3], S2[3][3], dE[3][3], dS[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double C = 0.0, dC = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        C += F[k][a] * F[k][b];
+        dC += dF[k][a] * F[k][b] + F[k][a] * dF[k][b];
+      }
+      E[a][b] = 0.5 * (C - (a == b ? 1.0 : 0.0));
+      dE[a][b] = 0.5 * dC;
+    }
+  double trE = E[0][0] + E[1][1] + E[2][2], trdE = dE[0][0] + dE[1][1] + dE[2][2];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      S2[a][b] = lam * trE * (a == b ? 1.0 : 0.0) + 2.0 * mu * E[a][b];
+      dS[a][b] = lam * trdE * (a == b ? 1.0 : 0.0) + 2.0 * mu * dE[a][b];
+    }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      dP[a][b] = 0.0;
+      for (int k = 0; k < 3; ++k) dP[a][b] += dF[a][k] * S2[k][b] + F[a][k] * dS[k][b];
+    }
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One cell: local vector b (nloc x nrhs) for coefficient xl (nloc x nrhs)    */
 /* ------------------------------------------------------------------------ */
@@ -815,6 +873,118 @@ int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const
     free(pm);
   }
   tab_free(&T);
+  return err;
+}
+
+/* Linearised hyperelastic operator: b^K_(a,j) = sum_q w_q |J| dP(u_K; du_K) :
+ * grad(psi_j e_a), with the state u (ndof, one vector) and the directions du
+ * (ndof x nrhs); grad u = (grad^ u) G as in the residual. */
+int orc_linearised_cell_vectors(int form, int p, int nq, const double* params,
+                                int nx, int ny, int nz, const double* coords,
+                                const double* u, const double* du, int nrhs,
+                                const int64_t* cells, int64_t ncells, double* b, int nthreads) {
+  elem_t E;
+  if (make_elem(ORC_VQ, p, nx, ny, nz, &E) || !(form == ORC_NEOHOOKE || form == ORC_SVK) || nrhs < 1) return -1;
+  tab_t T;
+  if (tabulate(&E, nq, ORC_GL, &T)) return -1;
+  int64_t ncell = (int64_t)nx * ny * nz;
+  int nloc = E.nloc;
+  int err = 0;
+  int nt = nthreads_of(nthreads);
+#pragma omp parallel num_threads(nt)
+  {
+    int64_t* dofs = (int64_t*)malloc(sizeof(int64_t) * nloc);
+    double* ul = (double*)malloc(sizeof(double) * nloc);
+    double* dl = (double*)malloc(sizeof(double) * nloc * nrhs);
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t kc = 0; kc < ncells; ++kc) {
+      int64_t c = cells[kc];
+      if (c < 0 || c >= ncell) { err = -1; continue; }
+      double X[8][3];
+      cell_vertices(nx, ny, nz, coords, c, X);
+      elem_cell_dofs(&E, ny, nz, c, dofs);
+      for (int l = 0; l < nloc; ++l) {
+        ul[l] = u[dofs[l]];
+        for (int r = 0; r < nrhs; ++r) dl[l * nrhs + r] = du[dofs[l] * nrhs + r];
+      }
+      double* bc = &b[(size_t)kc * nloc * nrhs];
+      memset(bc, 0, sizeof(double) * nloc * nrhs);
+      for (int q = 0; q < T.nq3; ++q) {
+        double xi[3];
+        qpoint(&T, q, xi);
+        geo_t g;
+        if (geometry(X, xi, &g)) { err = -2; break; }
+        double w = qweight(&T, q);
+        const double* grd = &T.grad[(size_t)q * nloc * 3];
+        double Hr[3][3] = {{0}}, Hu[3][3];
+        for (int l = 0; l < nloc; ++l) {
+          int a = T.comp[l];
+          for (int k = 0; k < 3; ++k) Hr[a][k] += ul[l] * grd[l * 3 + k];
+        }
+        for (int a = 0; a < 3; ++a)
+          for (int bb = 0; bb < 3; ++bb) {
+            Hu[a][bb] = 0.0;
+            for (int k = 0; k < 3; ++k) Hu[a][bb] += Hr[a][k] * g.G[k][bb];
+          }
+        for (int r = 0; r < nrhs; ++r) {
+          double Dr[3][3] = {{0}}, dF[3][3], dP[3][3], PGt[3][3];
+          for (int l = 0; l < nloc; ++l) {
+            int a = T.comp[l];
+            for (int k = 0; k < 3; ++k) Dr[a][k] += dl[l * nrhs + r] * grd[l * 3 + k];
+          }
+          for (int a = 0; a < 3; ++a)
+            for (int bb = 0; bb < 3; ++bb) {
+              dF[a][bb] = 0.0;
+              for (int k = 0; k < 3; ++k) dF[a][bb] += Dr[a][k] * g.G[k][bb];
+            }
+          if (dpiola(form, params, Hu, dF, dP)) { err = -3; break; }
+          for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k) {
+              PGt[a][k] = 0.0;
+              for (int bb = 0; bb < 3; ++bb) PGt[a][k] += dP[a][bb] * g.G[k][bb];
+            }
+          for (int l = 0; l < nloc; ++l) {
+            int a = T.comp[l];
+            double sacc = 0.0;
+            for (int k = 0; k < 3; ++k) sacc += PGt[a][k] * grd[l * 3 + k];
+            bc[l * nrhs + r] += w * g.S * sacc;
+          }
+        }
+      }
+    }
+    free(dofs);
+    free(ul);
+    free(dl);
+  }
+  tab_free(&T);
+  return err;
+}
+
+int orc_linearised_action(int form, int p, int nq, const double* params,
+                          int nx, int ny, int nz, const double* coords,
+                          const double* u, const double* du, double* y, int nrhs, int nthreads) {
+  elem_t E;
+  if (make_elem(ORC_VQ, p, nx, ny, nz, &E) || nrhs < 1) return -1;
+  memset(y, 0, sizeof(double) * E.ndof * nrhs);
+  int64_t ncell = (int64_t)nx * ny * nz;
+  const int64_t CH = 2048;
+  int64_t* cells = (int64_t*)malloc(sizeof(int64_t) * CH);
+  double* b = (double*)malloc(sizeof(double) * CH * E.nloc * nrhs);
+  int64_t* dofs = (int64_t*)malloc(sizeof(int64_t) * E.nloc);
+  int err = 0;
+  for (int64_t c0 = 0; c0 < ncell && !err; c0 += CH) {
+    int64_t m = (ncell - c0 < CH) ? ncell - c0 : CH;
+    for (int64_t k = 0; k < m; ++k) cells[k] = c0 + k;
+    err = orc_linearised_cell_vectors(form, p, nq, params, nx, ny, nz, coords, u, du, nrhs, cells, m, b, nthreads);
+    for (int64_t k = 0; k < m && !err; ++k) {
+      elem_cell_dofs(&E, ny, nz, c0 + k, dofs);
+      for (int l = 0; l < E.nloc; ++l)
+        for (int r = 0; r < nrhs; ++r) y[dofs[l] * nrhs + r] += b[((size_t)k * E.nloc + l) * nrhs + r];
+    }
+  }
+  free(cells);
+  free(b);
+  free(dofs);
   return err;
 }
 

@@ -87,6 +87,16 @@ int orc_action_rule(int family, int form, int p, int nq, int qrule, const double
 int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const double* params,
                            int nx, int ny, int nz, const double* coords,
                            int64_t cell_begin, int64_t cell_end, double* A, int nthreads);
+/* Linearised hyperelastic operator (NEOHOOKE or SVK) at the state u (ndof):
+ * per-cell vectors and the assembled action on the directions du (ndof x
+ * nrhs), b^K_(a,j) = sum_q w_q |J| dP(F(u); grad du) : grad(psi_j e_a). */
+int orc_linearised_cell_vectors(int form, int p, int nq, const double* params,
+                                int nx, int ny, int nz, const double* coords,
+                                const double* u, const double* du, int nrhs,
+                                const int64_t* cells, int64_t ncells, double* b, int nthreads);
+int orc_linearised_action(int form, int p, int nq, const double* params,
+                          int nx, int ny, int nz, const double* coords,
+                          const double* u, const double* du, double* y, int nrhs, int nthreads);
 /* Hyperelastic stored energy W(u) (NEOHOOKE or SVK), summed over cells. */
 int orc_energy(int form, int p, int nq, const double* params,
                int nx, int ny, int nz, const double* coords,

@@ -74,6 +74,21 @@ def piola_scale_ok(orc):
     return np.abs(A - A1 / h).max() < 1e-13
 
 
+def linearisation_ok(orc):
+    """The neo-Hookean linearisation matches central differences of the
+    residual at a state with volume change (ln J != 0)."""
+    p, d = 1, (2, 1, 2)
+    X = inputs.box_coords(*d, perturb=0.1, seed=4)
+    ndof, _ = orc.space_size("VQ", p, d)
+    u = orc.q_node_coords(p, d, X) @ np.diag([0.08, 0.05, -0.03])
+    u = np.concatenate([u[:, 0], u[:, 1], u[:, 2]]) + 0.01 * inputs.random_vector(ndof, 1, seed=9)
+    du = inputs.random_vector(ndof, 1, seed=13)
+    k = orc.linearised_action("neohooke", p, d, X, u, du)
+    e = 1e-5
+    fd = (orc.action("VQ", "neohooke", p, d, X, u + e * du) - orc.action("VQ", "neohooke", p, d, X, u - e * du)) / (2 * e)
+    return np.abs(k - fd).max() <= 1e-7 * np.abs(k).max()
+
+
 PLANTS = {
     1: ("G used where G^T belongs", patch_ok),
     2: ("|J| dropped from the scalar forms", moments_ok),
@@ -82,6 +97,7 @@ PLANTS = {
     5: ("F^{-1} used for F^{-T}", rotation_ok),
     6: ("a term dropped from the Lagrange derivative", lagrange_ok),
     7: ("1/|J| dropped from the contravariant Piola map", piola_scale_ok),
+    8: ("lambda ln J dropped from the neo-Hookean linearisation", linearisation_ok),
 }
 
 
