@@ -508,6 +508,26 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
     ex["structured_fp64"] = rows
     if ctx.sync_status() != 0:
         ex["structured_status"] = "device status flagged"
+    # --- linearised hyperelastic operator K(u) du (the Jacobian of the residual; the operator whose
+    #     action Sec. 4.1 times), vector Q_p on 48^3, p = 2..6, state = the residual's displacement
+    rows = []
+    dims = (48, 48, 48)
+    mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    for form in ("svk", "neohooke"):
+        for p in range(2, 7):
+            sp = sfx.Space(mesh, "VQ", p)
+            ud = torch.from_numpy(inputs.displacement(sp.ndof, p, dims[0], seed=1)).cuda()
+            dd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2)).cuda()
+            yd = torch.empty_like(dd)
+            t = _time(torch, stream, flush,
+                      lambda: sfx.sfx_assemble_linearised_action(ctx, form, sp, ud, dd, yd, stream=stream))
+            rows.append({"family": "VQ", "form": form + "_linearised", "p": p, "mesh": "%dx%dx%d" % dims,
+                         "ndof": sp.ndof, "ms": round(t, 4), "dofs_per_s": sp.ndof / (t * 1e-3)})
+            del ud, dd, yd, sp
+    del mesh
+    ex["linearised_hyperelastic_fp64"] = rows
+    if ctx.sync_status() != 0:
+        ex["linearised_status"] = "device status flagged"
     # --- precision: Laplace (Q_p) and neo-Hookean residual (vector Q_p) on 64^3, p=3..8,
     #     FP64 vs TF32x3 vs BF16x3 split contractions; error against the FP64 GPU action
     ex["precision_64cube"] = precision_block(sfx, torch, ctx, inputs, flush, stream)

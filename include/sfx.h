@@ -195,6 +195,33 @@ sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, const sfx_form
                                      const int64_t* cells, int64_t ncells, double* b,
                                      sfx_precision prec, void* stream);
 
+/* Action of the linearised hyperelastic operator (the Jacobian of the
+ * SFX_NEOHOOKE / SFX_SVK residual; Sec. 4.1 times the action of this
+ * operator for the Saint Venant-Kirchhoff law) on vector Q_p:
+ *   y_(a,j) = sum_K sum_q w_q S dP(F; dF) : (grad^ phi_j G) e_a,
+ *   F = I + grad^u G (the state), dF = grad^du G (the direction),
+ *   neo-Hookean dP = mu dF + (mu - lambda ln det F) F^{-T} dF^T F^{-T}
+ *                    + lambda tr(F^{-1} dF) F^{-T};
+ *   SVK dP = dF S + F (lambda tr(dE) I + 2 mu dE), dE = (dF^T F + F^T dF)/2.
+ *   u    device, ndof doubles (one state, read-only)
+ *   du   device, ndof x nrhs directions (read-only); y device, ndof x nrhs
+ *        (must alias neither); accumulate as in sfx_assemble_action.
+ * Deterministic colour-pass scatter.  A point with det F <= 0 (neo-Hookean)
+ * contributes zero and sets SFX_DEV_DETF.  FP64 only.
+ * Errors: SFX_ERR_ARG (null, aliasing, nrhs, family/form), SFX_ERR_UNSUPPORTED
+ * (precision), SFX_ERR_CUDA. */
+sfx_status sfx_assemble_linearised_action(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                          const sfx_space* space, const double* u, const double* du, double* y,
+                                          int nrhs, int accumulate, sfx_precision prec, void* stream);
+
+/* Per-cell vectors of the same operator (no scatter) for the listed cells
+ * (device int64, each in [0, ncell)), written to b (device, ncells x nloc x
+ * nrhs).  Same arithmetic; errors as above. */
+sfx_status sfx_assemble_linearised_cell_vectors(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                                const sfx_space* space, const double* u, const double* du,
+                                                int nrhs, const int64_t* cells, int64_t ncells, double* b,
+                                                sfx_precision prec, void* stream);
+
 /* Local element matrices A[c][j][i] (row = test j, column = trial i) of the
  * bilinear forms for cells [cell_begin, cell_end) (Sec. 3.2: argument
  * factorisation into P^(k,l) factors and sum factorisation, O(n^7) per cell;

@@ -33,7 +33,8 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices",
            "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy",
            "sfx_padaptive_action_noalloc", "sfx_qdata_create", "sfx_qdata_destroy",
-           "sfx_assemble_action_stored", "sfx_tune_set_cells_per_cta", "sfx_tune_get_cells_per_cta"]
+           "sfx_assemble_action_stored", "sfx_tune_set_cells_per_cta", "sfx_tune_get_cells_per_cta",
+           "sfx_assemble_linearised_action", "sfx_assemble_linearised_cell_vectors"]
 TUNE_KERNEL = {"fp64": 0, "mixed": 1, "mixed_stored": 2, "elastic_mixed": 3}
 QDATA = {"fp64": 1, "fp32": 2, "both": 3}
 EXEC = {"graph": 0, "per_launch": 1}
@@ -82,6 +83,8 @@ def lib():
         L.sfx_space_destroy.restype = None
         L.sfx_tabulate_1d.argtypes = [i, i, i, i, i, P, P, P]
         L.sfx_assemble_action.argtypes = [P, i, C.POINTER(_Params), P, P, P, i, i, i, i, P]
+        L.sfx_assemble_linearised_action.argtypes = [P, i, C.POINTER(_Params), P, P, P, P, i, i, i, P]
+        L.sfx_assemble_linearised_cell_vectors.argtypes = [P, i, C.POINTER(_Params), P, P, P, i, P, i64, P, i, P]
         L.sfx_assemble_cell_vectors.argtypes = [P, i, C.POINTER(_Params), P, P, i, P, i64, P, i, P]
         L.sfx_assemble_cell_matrices.argtypes = [P, i, C.POINTER(_Params), P, i64, i64, P, i, i, P]
         L.sfx_plan_create_padaptive.argtypes = [P, P, P, i, P, P, i, C.POINTER(P)]
@@ -237,6 +240,31 @@ def sfx_assemble_action(ctx, form, space, x, y, nrhs=None, accumulate=False, pre
                                      _dptr(y, "float64"), nrhs, int(bool(accumulate)), PRECISION[precision],
                                      ALGO[algo], _stream(stream)), "sfx_assemble_action")
     return y
+
+
+def sfx_assemble_linearised_action(ctx, form, space, u, du, y, nrhs=None, accumulate=False, precision="fp64",
+                                   params=None, stream=None):
+    nrhs = nrhs if nrhs is not None else (1 if du.dim() == 1 else du.shape[1])
+    if u.numel() != space.ndof or du.numel() != space.ndof * nrhs or y.numel() != space.ndof * nrhs:
+        raise ValueError("u must hold ndof doubles; du and y ndof * nrhs")
+    _check(lib().sfx_assemble_linearised_action(ctx.h, FORM[form], _params(params), space.h, _dptr(u, "float64"),
+                                                _dptr(du, "float64"), _dptr(y, "float64"), nrhs,
+                                                int(bool(accumulate)), PRECISION[precision], _stream(stream)),
+           "sfx_assemble_linearised_action")
+    return y
+
+
+def sfx_assemble_linearised_cell_vectors(ctx, form, space, u, du, cells, b, nrhs=None, precision="fp64",
+                                         params=None, stream=None):
+    nrhs = nrhs if nrhs is not None else (1 if du.dim() == 1 else du.shape[1])
+    if b.numel() != cells.numel() * space.nloc * nrhs:
+        raise ValueError("b must hold ncells * nloc * nrhs doubles")
+    _check(lib().sfx_assemble_linearised_cell_vectors(ctx.h, FORM[form], _params(params), space.h,
+                                                      _dptr(u, "float64"), _dptr(du, "float64"), nrhs,
+                                                      _dptr(cells, "int64"), cells.numel(), _dptr(b, "float64"),
+                                                      PRECISION[precision], _stream(stream)),
+           "sfx_assemble_linearised_cell_vectors")
+    return b
 
 
 def sfx_assemble_cell_vectors(ctx, form, space, x, cells, b, nrhs=None, precision="fp64", params=None,

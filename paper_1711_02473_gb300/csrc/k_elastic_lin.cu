@@ -1,0 +1,272 @@
+// k_elastic_lin.cu -- action of the linearised hyperelastic operator on
+// vector Q_p (GLL), FP64, sum-factorised:
+//   y_(a,j) = sum_K int dP(F(u); dF) : grad(phi_j e_a),  F = I + grad u, dF = grad du,
+// the Jacobian of the residual of k_elastic.cu (the operator whose action the
+// paper's hyperelastic experiments time, Sec. 4.1, for the Saint Venant-
+// Kirchhoff law; the neo-Hookean law is the same skeleton).
+//
+// Per cell: the state's reference gradient grad^ u (9 fields at the points) is
+// formed once by the same per-component contractions as the residual (B along
+// x, y, z, then the collocation derivative Dq), then for every direction du
+// its gradient grad^ du, the pointwise linearised stress and the test flux
+// w S dP G^T = w dP adj(J)^T, contracted back with Dq^T and B^T and added
+// through the map (conflict-free per colour).  Pointwise, with G = adj(J)/S:
+//   neo-Hookean  dP = mu dF + (mu - lambda ln J) F^{-T} dF^T F^{-T} + lambda tr(F^{-1} dF) F^{-T}
+//   SVK          dP = dF S + F (lambda tr(dE) I + 2 mu dE),  dE = sym(F^T dF)
+// A point with det F <= 0 (neo-Hookean) contributes zero and sets SFX_DEV_DETF.
+#include "kern_common.cuh"
+
+namespace sfx {
+
+SFX_DEFINE_TAB_UPLOAD(upload_tab_elastic_lin)
+
+namespace {
+
+template <int N>
+struct LShape {
+  static constexpr int N2 = N * N, N3 = N2 * N;
+  // per team: U (N3 scratch), Hs (9 N3, state), Hd (9 N3, direction / flux),
+  // corners, Jacobian columns, flag
+  static constexpr int TEAM = N3 + 18 * N3 + 24 + 9 * N2 + 1;
+  static constexpr int MAXCB = 256 / N2 > 0 ? 256 / N2 : 1;
+};
+
+// Linearised test flux at one point: Hs = grad^ u, Hd = grad^ du (reference
+// gradients, [i][k] = d u_i / d xi_k), R = rows of adj J, S = det J, w the
+// weight; out[i][k] = w sum_j dP[i][j] R[k][j].  False (zero flux) if
+// det F <= 0 for the neo-Hookean law.
+template <bool NEO>
+__device__ __forceinline__ bool linearised_flux(const double (*Hs)[3], const double (*Hd)[3], const double (*R)[3],
+                                                double S, double w, double mu, double lam, double (*out)[3]) {
+  const double iS = recip_nr<2>(S);
+  double F[3][3], dF[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      F[i][j] = (Hs[i][0] * R[0][j] + Hs[i][1] * R[1][j] + Hs[i][2] * R[2][j]) * iS + (i == j ? 1.0 : 0.0);
+      dF[i][j] = (Hd[i][0] * R[0][j] + Hd[i][1] * R[1][j] + Hd[i][2] * R[2][j]) * iS;
+    }
+  double dP[3][3];
+  bool good = true;
+  if (NEO) {
+    double Cf[3][3];  // cofactor matrix of F: F^{-T} = Cf / det F
+    cross3(F[1], F[2], Cf[0]);
+    cross3(F[2], F[0], Cf[1]);
+    cross3(F[0], F[1], Cf[2]);
+    const double JF = dot3(F[0], Cf[0]);
+    good = JF > 0.0;
+    const double iJ = good ? recip_nr<2>(JF) : 0.0, lnJ = good ? log(JF) : 0.0;
+    double FiT[3][3], T1[3][3];
+    double tr = 0.0;  // tr(F^{-1} dF) = sum_ij F^{-T}_ij dF_ij
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        FiT[i][j] = Cf[i][j] * iJ;
+        tr = fma(FiT[i][j], dF[i][j], tr);
+      }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)  // T1 = dF^T F^{-T}
+#pragma unroll
+      for (int j = 0; j < 3; ++j) T1[k][j] = dF[0][k] * FiT[0][j] + dF[1][k] * FiT[1][j] + dF[2][k] * FiT[2][j];
+    const double c = mu - lam * lnJ, lt = lam * tr;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double m = FiT[i][0] * T1[0][j] + FiT[i][1] * T1[1][j] + FiT[i][2] * T1[2][j];
+        dP[i][j] = good ? mu * dF[i][j] + c * m + lt * FiT[i][j] : 0.0;
+      }
+  } else {
+    double E[3][3], dE[3][3], S2[3][3], dS[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        E[a][b] = 0.5 * (F[0][a] * F[0][b] + F[1][a] * F[1][b] + F[2][a] * F[2][b] - (a == b ? 1.0 : 0.0));
+        dE[a][b] = 0.5 * (dF[0][a] * F[0][b] + dF[1][a] * F[1][b] + dF[2][a] * F[2][b] + F[0][a] * dF[0][b] +
+                          F[1][a] * dF[1][b] + F[2][a] * dF[2][b]);
+      }
+    const double trE = E[0][0] + E[1][1] + E[2][2], trdE = dE[0][0] + dE[1][1] + dE[2][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        S2[a][b] = (a == b ? lam * trE : 0.0) + 2.0 * mu * E[a][b];
+        dS[a][b] = (a == b ? lam * trdE : 0.0) + 2.0 * mu * dE[a][b];
+      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        dP[i][j] = dF[i][0] * S2[0][j] + dF[i][1] * S2[1][j] + dF[i][2] * S2[2][j] + F[i][0] * dS[0][j] +
+                   F[i][1] * dS[1][j] + F[i][2] * dS[2][j];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[i][k] = w * dot3(dP[i], R[k]);
+  return good;
+}
+
+// Reference gradient of component `comp` of the field v (component-major
+// vector map mrow) into H[(comp*3 + k)*N3 + qp], via U.
+template <int N>
+__device__ __forceinline__ void component_gradient(const Tab1D& T, const double* v, int nrhs, int r,
+                                                   const int32_t* mrow, bool ok, int comp, double* U, double* H,
+                                                   int t) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  for (int l = t; l < N3; l += N2) U[l] = ok ? v[(int64_t)mrow[comp * N3 + l] * nrhs + r] : 0.0;
+  __syncthreads();
+  contract<N, N, N, 0, N, false, false, kMaxN>(U, U, T.Bc, t);
+  __syncthreads();
+  contract<N, N, N, 1, N, false, false, kMaxN>(U, U, T.Bc, t);
+  __syncthreads();
+  contract<N, N, N, 2, N, false, false, kMaxN>(U, U, T.Bc, t);
+  __syncthreads();
+  contract<N, N, N, 0, N, false, false, kMaxQ>(U, H + (comp * 3 + 0) * N3, T.Dq, t);
+  contract<N, N, N, 1, N, false, false, kMaxQ>(U, H + (comp * 3 + 1) * N3, T.Dq, t);
+  contract<N, N, N, 2, N, false, false, kMaxQ>(U, H + (comp * 3 + 2) * N3, T.Dq, t);
+  __syncthreads();
+}
+
+template <int N, bool NEO>
+__global__ void __launch_bounds__(256) k_linearised_elastic_fp64(const ActArgs a, const int64_t ncell_total) {
+  using Sh = LShape<N>;
+  constexpr int N2 = Sh::N2, N3 = Sh::N3;
+  const Tab1D& T = c_tab[N - 1];
+  extern __shared__ double sm[];
+  const int cb = blockDim.x / N2;
+  const int team = threadIdx.x / N2, t = threadIdx.x - team * N2;
+  double* W3 = sm;
+  double* xq = sm + N3;
+  double* base = sm + N3 + 16 + team * Sh::TEAM;
+  double* U = base;
+  double* Hs = U + N3;       // state gradient
+  double* Hd = Hs + 9 * N3;  // direction gradient, then the flux
+  double(*X)[3] = reinterpret_cast<double(*)[3]>(Hd + 9 * N3);
+  double(*Jc)[N2][3] = reinterpret_cast<double(*)[N2][3]>(&X[8][0]);
+  int* bad = reinterpret_cast<int*>(&Jc[3][0][0]);
+
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) W3[i] = T.w[i / N2] * T.w[(i / N) % N] * T.w[i % N];
+  if (threadIdx.x < N) xq[threadIdx.x] = T.x[threadIdx.x];
+  int cell = 0;
+  const int64_t slot = (int64_t)blockIdx.x * cb + team;
+  const bool active = slot_cell(a, slot, ncell_total, &cell);
+  if (t == 0) *bad = 0;
+  for (int c = t; c < 8; c += N2) {
+    if (active) {
+      const int v = a.vmap[(int64_t)cell * 8 + c];
+      X[c][0] = a.xyz[(int64_t)v * 3 + 0];
+      X[c][1] = a.xyz[(int64_t)v * 3 + 1];
+      X[c][2] = a.xyz[(int64_t)v * 3 + 2];
+    } else {
+      X[c][0] = (c >> 2) & 1; X[c][1] = (c >> 1) & 1; X[c][2] = c & 1;
+    }
+  }
+  __syncthreads();
+  jacobian_columns<N>(X, xq, Jc, t);
+  __syncthreads();
+  for (int qp = t; qp < N3; qp += N2) {
+    double r0[3], r1[3], r2[3];
+    if (!(point_rows<N, false>(Jc, qp, r0, r1, r2) > 0.0)) *bad = 1;
+  }
+  __syncthreads();
+  const bool ok = active && !*bad;
+  if (active && *bad && t == 0) set_flag(a.status, SFX_DEV_INVERTED);
+  const int32_t* mrow = a.map + (int64_t)cell * 3 * N3;
+  const double mu = a.mu, lam = a.lambda;
+
+  // the state's reference gradient, once per cell
+  for (int comp = 0; comp < 3; ++comp) component_gradient<N>(T, a.xs, 1, 0, mrow, ok, comp, U, Hs, t);
+
+#pragma unroll 1
+  for (int r = 0; r < a.nrhs; ++r) {
+    for (int comp = 0; comp < 3; ++comp) component_gradient<N>(T, a.x, a.nrhs, r, mrow, ok, comp, U, Hd, t);
+    for (int qp = t; qp < N3; qp += N2) {
+      double R[3][3];
+      const double S = point_rows<N, true>(Jc, qp, R[0], R[1], R[2]);
+      double hs[3][3], hd[3][3], flux[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          hs[i][k] = Hs[(i * 3 + k) * N3 + qp];
+          hd[i][k] = Hd[(i * 3 + k) * N3 + qp];
+        }
+      if (!linearised_flux<NEO>(hs, hd, R, S, W3[qp], mu, lam, flux) && ok) set_flag(a.status, SFX_DEV_DETF);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Hd[(i * 3 + k) * N3 + qp] = flux[i][k];
+    }
+    __syncthreads();
+    for (int comp = 0; comp < 3; ++comp) {
+      contract<N, N, N, 0, N, true, false, kMaxQ>(Hd + (comp * 3 + 0) * N3, U, T.Dq, t);
+      __syncthreads();
+      contract<N, N, N, 1, N, true, true, kMaxQ>(Hd + (comp * 3 + 1) * N3, U, T.Dq, t);
+      __syncthreads();
+      contract<N, N, N, 2, N, true, true, kMaxQ>(Hd + (comp * 3 + 2) * N3, U, T.Dq, t);
+      __syncthreads();
+      contract<N, N, N, 0, N, true, false, kMaxN>(U, U, T.Bc, t);
+      __syncthreads();
+      contract<N, N, N, 1, N, true, false, kMaxN>(U, U, T.Bc, t);
+      __syncthreads();
+      contract<N, N, N, 2, N, true, false, kMaxN>(U, U, T.Bc, t);
+      __syncthreads();
+      if (ok) {
+        if (a.cell_vectors) {
+          for (int l = t; l < N3; l += N2) a.y[(slot * 3 * N3 + comp * N3 + l) * a.nrhs + r] = U[l];
+        } else {
+          for (int l = t; l < N3; l += N2) a.y[(int64_t)mrow[comp * N3 + l] * a.nrhs + r] += U[l];
+        }
+      } else if (active && a.cell_vectors) {
+        for (int l = t; l < N3; l += N2) a.y[(slot * 3 * N3 + comp * N3 + l) * a.nrhs + r] = 0.0;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int N, bool NEO>
+int launch_l(const ActArgs& a, int64_t nc, cudaStream_t s) {
+  using Sh = LShape<N>;
+  const size_t per_team = Sh::TEAM * sizeof(double);
+  const size_t fixed = (Sh::N3 + 16) * sizeof(double);
+  int cb = Sh::MAXCB;
+  while (cb > 1 && fixed + cb * per_team > 200 * 1024) --cb;
+  const size_t smem = fixed + cb * per_team;
+  auto kern = k_linearised_elastic_fp64<N, NEO>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  kern<<<(unsigned)((a.ncells + cb - 1) / cb), cb * Sh::N2, smem, s>>>(a, nc);
+  return (int)cudaGetLastError();
+}
+
+template <bool NEO>
+int dispatch_p(int p, const ActArgs& a, int64_t nc, cudaStream_t s) {
+  switch (p) {
+    case 1: return launch_l<2, NEO>(a, nc, s);
+    case 2: return launch_l<3, NEO>(a, nc, s);
+    case 3: return launch_l<4, NEO>(a, nc, s);
+    case 4: return launch_l<5, NEO>(a, nc, s);
+    case 5: return launch_l<6, NEO>(a, nc, s);
+    case 6: return launch_l<7, NEO>(a, nc, s);
+    case 7: return launch_l<8, NEO>(a, nc, s);
+    case 8: return launch_l<9, NEO>(a, nc, s);
+  }
+  return -1;
+}
+
+}  // namespace
+
+int launch_linearised_elastic(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream) {
+  if (sp->family != SFX_VQ) return -1;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (form == SFX_NEOHOOKE) return dispatch_p<true>(sp->p, a, sp->mesh->ncell, s);
+  if (form == SFX_SVK) return dispatch_p<false>(sp->p, a, sp->mesh->ncell, s);
+  return -1;
+}
+
+}  // namespace sfx

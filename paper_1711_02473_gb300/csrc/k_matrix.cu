@@ -243,13 +243,70 @@ __global__ void __launch_bounds__(kMatThreads) k_cell_matrices(const MatArgs a, 
 // into A_rs = sum_q sum_kl C_kl(q) d_k psi_r(q) d_l psi_s(q) + M(q) psi_r psi_s
 // cancels every sum but one (delta cancellation, Sec. 3.1 / 3.4):
 //   k = l = 1:  [r2 = s2, r3 = s3]  sum_q1 C_11(q1,r2,r3) D[q1][r1] D[q1][s1]
+//   k = l = 2:  [r1 = s1, r3 = s3]  sum_q2 C_22(r1,q2,r3) D[q2][r2] D[q2][s2]
+//   k = l = 3:  [r1 = s1, r2 = s2]  sum_q3 C_33(r1,r2,q3) D[q3][r3] D[q3][s3]
 //   k=1, l=2:   [r3 = s3]           C_12(s1,r2,r3) D[s1][r1] D[r2][s2]
 //   k=2, l=1:   [r3 = s3]           C_12(r1,s2,r3) D[s2][r2] D[r1][s1]
-//   (and cyclically), mass:  [r = s]  M(r)
+//   (and the other off-diagonal pairs cyclically), mass:  [r = s]  M(r)
 // with C = w S G G^T = (w/S) adj(J) adj(J)^T and M = w S at the GLL points:
 // O(n^5) arithmetic per cell instead of the O(n^7) of the sum-factorised
-// kernel above; the dense n^3 x n^3 output (zeros included) is written with
-// consecutive columns on consecutive threads.
+// kernel above.  One CTA per (cell, r1).  It tabulates, for its r1, the three
+// k = l sums (n^3 values each) and the six off-diagonal coefficients with one
+// derivative factor folded in (n^3 each); each entry is then a sum of at most
+// nine table terms.  The entries of its n^2 rows are enumerated class by class
+// -- by which of r1 = s1, r2 = s2, r3 = s3 hold -- so that every warp applies
+// one formula (the FP64 pipe issues per warp, so divergent branches would pay
+// for all lanes); the all-unequal class, 70% of a dense Q_8 matrix, is zeros.
+struct CollTabs {
+  const double *T0, *T1, *T2;          // k = l sums: [s1][r2][r3], [r2][s2][r3], [r2][r3][s3]
+  const double *a3, *b3, *a2, *b2, *a1, *b1;
+  const double *D, *M;
+};
+
+// One entry of class (E1, E2, E3) = (r1 = s1, r2 = s2, r3 = s3).
+template <int N, bool E1, bool E2, bool E3>
+__device__ __forceinline__ double coll_entry(const CollTabs& t, int r1, int r2, int r3, int s1, int s2, int s3) {
+  constexpr int N2 = N * N;
+  auto d = [&](int q, int i) { return t.D[q * N + i]; };
+  double acc = 0.0;
+  if (E2 && E3) acc += t.T0[s1 * N2 + r2 * N + r3];
+  if (E1 && E3) acc += t.T1[r2 * N2 + s2 * N + r3];
+  if (E1 && E2) acc += t.T2[r2 * N2 + r3 * N + s3];
+  if (E3) {  // (k, l) = (1, 2), (2, 1)
+    acc = fma(t.a3[s1 * N2 + r2 * N + r3], d(r2, s2), acc);
+    acc = fma(t.b3[r2 * N2 + s2 * N + r3], d(r1, s1), acc);
+  }
+  if (E2) {  // (1, 3), (3, 1)
+    acc = fma(t.a2[s1 * N2 + r2 * N + r3], d(r3, s3), acc);
+    acc = fma(t.b2[r2 * N2 + r3 * N + s3], d(r1, s1), acc);
+  }
+  if (E1) {  // (2, 3), (3, 2)
+    acc = fma(t.a1[r2 * N2 + s2 * N + r3], d(r3, s3), acc);
+    acc = fma(t.b1[r2 * N2 + r3 * N + s3], d(r2, s2), acc);
+  }
+  if (E1 && E2 && E3) acc += t.M[r2 * N + r3];
+  return acc;
+}
+
+// All entries of class (E1, E2, E3) in the CTA's rows (r1, r2, r3): the
+// unequal coordinates run over the N-1 values that skip the row's own.
+template <int N, bool E1, bool E2, bool E3>
+__device__ __forceinline__ void coll_class(const CollTabs& t, int r1, double* Ac, int tid, int nt) {
+  constexpr int N2 = N * N, N3 = N2 * N, M1 = N - 1;
+  constexpr int F1 = E1 ? 1 : M1, F2 = E2 ? 1 : M1, F3 = E3 ? 1 : M1;
+  constexpr int SZ = F1 * F2 * F3;
+  for (int k = tid; k < N2 * SZ; k += nt) {
+    const int row = k / SZ, j = k - (k / SZ) * SZ;
+    const int r2 = row / N, r3 = row - (row / N) * N;
+    const int j1 = j / (F2 * F3), j2 = (j / F3) % F2, j3 = j % F3;
+    const int s1 = E1 ? r1 : j1 + (j1 >= r1);
+    const int s2 = E2 ? r2 : j2 + (j2 >= r2);
+    const int s3 = E3 ? r3 : j3 + (j3 >= r3);
+    const double v = (E1 || E2 || E3) ? coll_entry<N, E1, E2, E3>(t, r1, r2, r3, s1, s2, s3) : 0.0;
+    Ac[(int64_t)row * N3 + (s1 * N + s2) * N + s3] = v;
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(kMatThreads) k_cell_matrices_coll(const MatArgs a) {
   constexpr int N2 = N * N, N3 = N2 * N;
@@ -260,11 +317,14 @@ __global__ void __launch_bounds__(kMatThreads) k_cell_matrices_coll(const MatArg
   double* wq = xq + 16;        // 16
   double* X = wq + 16;         // 24
   double* Jc = X + 24;         // [3][N2][3]
-  double* C = Jc + 9 * N2;     // [7][N3]: C_00, C_11, C_22, C_01, C_02, C_12, M
-  int* bad = reinterpret_cast<int*>(C + 7 * N3);
-  const int tid = threadIdx.x;
-  const int64_t cell = a.cell_begin + blockIdx.x;
-  for (int i = tid; i < N2; i += kMatThreads) D[i] = T.Dg[i / N][i % N];
+  double* C = Jc + 9 * N2;     // [6][N3]: C_00, C_11, C_22, C_01, C_02, C_12
+  double* M = C + 6 * N3;      // [N2]: mass w S at (r1, r2, r3)
+  double* Tt = M + N2;         // 9 tables of N3: T0, T1, T2, a3, b3, a2, b2, a1, b1
+  int* bad = reinterpret_cast<int*>(Tt + 9 * N3);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t cell = a.cell_begin + blockIdx.x / N;
+  const int r1 = blockIdx.x % N;
+  for (int i = tid; i < N2; i += nt) D[i] = T.Dg[i / N][i % N];
   if (tid < N) {
     xq[tid] = T.xg[tid];
     wq[tid] = T.wg[tid];
@@ -272,60 +332,64 @@ __global__ void __launch_bounds__(kMatThreads) k_cell_matrices_coll(const MatArg
   if (tid < 24) X[tid] = a.xyz[(int64_t)a.vmap[cell * 8 + tid / 3] * 3 + tid % 3];
   if (tid == 0) *bad = 0;
   __syncthreads();
-  for (int i = tid; i < N2; i += kMatThreads)
+  for (int i = tid; i < N2; i += nt)
     jacobian_columns<N>(reinterpret_cast<const double(*)[3]>(X), xq, reinterpret_cast<double(*)[N2][3]>(Jc), i);
   __syncthreads();
-  for (int qp = tid; qp < N3; qp += kMatThreads) {
+  for (int qp = tid; qp < N3; qp += nt) {
     const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
-    double r0[3], r1[3], r2[3];
-    const double S = point_rows<N, true>(reinterpret_cast<const double(*)[N2][3]>(Jc), qp, r0, r1, r2);
+    double r0[3], rr1[3], rr2[3];
+    const double S = point_rows<N, true>(reinterpret_cast<const double(*)[N2][3]>(Jc), qp, r0, rr1, rr2);
     if (!(S > 0.0)) *bad = 1;
     const double w = wq[q1] * wq[q2] * wq[q3];
     const double ws = a.alpha * w * recip_nr<2>(S);
     C[0 * N3 + qp] = ws * dot3(r0, r0);
-    C[1 * N3 + qp] = ws * dot3(r1, r1);
-    C[2 * N3 + qp] = ws * dot3(r2, r2);
-    C[3 * N3 + qp] = ws * dot3(r0, r1);
-    C[4 * N3 + qp] = ws * dot3(r0, r2);
-    C[5 * N3 + qp] = ws * dot3(r1, r2);
-    C[6 * N3 + qp] = a.beta * w * S;
+    C[1 * N3 + qp] = ws * dot3(rr1, rr1);
+    C[2 * N3 + qp] = ws * dot3(rr2, rr2);
+    C[3 * N3 + qp] = ws * dot3(r0, rr1);
+    C[4 * N3 + qp] = ws * dot3(r0, rr2);
+    C[5 * N3 + qp] = ws * dot3(rr1, rr2);
+    if (q1 == r1) M[q2 * N + q3] = a.beta * w * S;
   }
   __syncthreads();
-  double* Ac = a.A + (int64_t)blockIdx.x * N3 * N3;
-  if (*bad) {
-    if (tid == 0) set_flag(a.status, SFX_DEV_INVERTED);
-    for (int i = tid; i < N3 * N3; i += kMatThreads) Ac[i] = 0.0;
-    return;
-  }
   auto at = [&](int k, int q1, int q2, int q3) { return C[k * N3 + (q1 * N + q2) * N + q3]; };
   auto d = [&](int q, int i) { return D[q * N + i]; };
-  for (int e = tid; e < N3 * N3; e += kMatThreads) {
-    const int row = e / N3, col = e - (e / N3) * N3;
-    const int r1 = row / N2, r2 = (row / N) % N, r3 = row % N;
-    const int s1 = col / N2, s2 = (col / N) % N, s3 = col % N;
-    const bool e1 = r1 == s1, e2 = r2 == s2, e3 = r3 == s3;
-    double acc = 0.0;
-    if (e2 && e3)
-      for (int q = 0; q < N; ++q) acc = fma(at(0, q, r2, r3), d(q, r1) * d(q, s1), acc);
-    if (e1 && e3)
-      for (int q = 0; q < N; ++q) acc = fma(at(1, r1, q, r3), d(q, r2) * d(q, s2), acc);
-    if (e1 && e2)
-      for (int q = 0; q < N; ++q) acc = fma(at(2, r1, r2, q), d(q, r3) * d(q, s3), acc);
-    if (e3) {  // (k, l) = (1, 2) and (2, 1)
-      acc = fma(at(3, s1, r2, r3), d(s1, r1) * d(r2, s2), acc);
-      acc = fma(at(3, r1, s2, r3), d(s2, r2) * d(r1, s1), acc);
+  // the k = l sums and the folded off-diagonal coefficients of this r1
+  for (int i = tid; i < N3; i += nt) {
+    const int i0 = i / N2, i1 = (i / N) % N, i2 = i % N;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      t0 = fma(at(0, q, i1, i2), d(q, r1) * d(q, i0), t0);  // (s1, r2, r3) = (i0, i1, i2)
+      t1 = fma(at(1, r1, q, i2), d(q, i0) * d(q, i1), t1);  // (r2, s2, r3)
+      t2 = fma(at(2, r1, i0, q), d(q, i1) * d(q, i2), t2);  // (r2, r3, s3)
     }
-    if (e2) {  // (1, 3) and (3, 1)
-      acc = fma(at(4, s1, r2, r3), d(s1, r1) * d(r3, s3), acc);
-      acc = fma(at(4, r1, r2, s3), d(s3, r3) * d(r1, s1), acc);
-    }
-    if (e1) {  // (2, 3) and (3, 2)
-      acc = fma(at(5, r1, s2, r3), d(s2, r2) * d(r3, s3), acc);
-      acc = fma(at(5, r1, r2, s3), d(s3, r3) * d(r2, s2), acc);
-    }
-    if (row == col) acc += at(6, r1, r2, r3);
-    Ac[e] = acc;
+    Tt[0 * N3 + i] = t0;
+    Tt[1 * N3 + i] = t1;
+    Tt[2 * N3 + i] = t2;
+    Tt[3 * N3 + i] = at(3, i0, i1, i2) * d(i0, r1);  // a3[s1][r2][r3] = C_01(s1,r2,r3) D[s1][r1]
+    Tt[4 * N3 + i] = at(3, r1, i1, i2) * d(i1, i0);  // b3[r2][s2][r3] = C_01(r1,s2,r3) D[s2][r2]
+    Tt[5 * N3 + i] = at(4, i0, i1, i2) * d(i0, r1);  // a2[s1][r2][r3] = C_02(s1,r2,r3) D[s1][r1]
+    Tt[6 * N3 + i] = at(4, r1, i0, i2) * d(i2, i1);  // b2[r2][r3][s3] = C_02(r1,r2,s3) D[s3][r3]
+    Tt[7 * N3 + i] = at(5, r1, i1, i2) * d(i1, i0);  // a1[r2][s2][r3] = C_12(r1,s2,r3) D[s2][r2]
+    Tt[8 * N3 + i] = at(5, r1, i0, i2) * d(i2, i1);  // b1[r2][r3][s3] = C_12(r1,r2,s3) D[s3][r3]
   }
+  __syncthreads();
+  double* Ac = a.A + ((int64_t)(blockIdx.x / N) * N3 + (int64_t)r1 * N2) * N3;  // rows (r1, *, *)
+  if (*bad) {
+    if (tid == 0 && r1 == 0) set_flag(a.status, SFX_DEV_INVERTED);
+    for (int i = tid; i < N2 * N3; i += nt) Ac[i] = 0.0;
+    return;
+  }
+  const CollTabs t{Tt, Tt + N3, Tt + 2 * N3, Tt + 3 * N3, Tt + 4 * N3, Tt + 5 * N3,
+                   Tt + 6 * N3, Tt + 7 * N3, Tt + 8 * N3, D, M};
+  coll_class<N, false, false, false>(t, r1, Ac, tid, nt);
+  coll_class<N, false, false, true>(t, r1, Ac, tid, nt);
+  coll_class<N, false, true, false>(t, r1, Ac, tid, nt);
+  coll_class<N, true, false, false>(t, r1, Ac, tid, nt);
+  coll_class<N, false, true, true>(t, r1, Ac, tid, nt);
+  coll_class<N, true, false, true>(t, r1, Ac, tid, nt);
+  coll_class<N, true, true, false>(t, r1, Ac, tid, nt);
+  coll_class<N, true, true, true>(t, r1, Ac, tid, nt);
 }
 
 // ---------------------------------------------------------------- host side
@@ -479,10 +543,12 @@ int launch_cell_matrices(const sfx_space* sp, sfx_form form, sfx_algo algo, cons
 template <int N>
 int launch_coll(const MatArgs& a, cudaStream_t s) {
   constexpr int N2 = N * N, N3 = N2 * N;
-  const size_t smem = sizeof(double) * (N2 + 32 + 24 + 9 * N2 + 7 * N3) + 16;
+  const size_t smem = sizeof(double) * (N2 + 32 + 24 + 9 * N2 + 6 * N3 + N2 + 9 * N3) + 16;
   cudaError_t e = cudaFuncSetAttribute(k_cell_matrices_coll<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  k_cell_matrices_coll<N><<<(unsigned)a.ncells, kMatThreads, smem, s>>>(a);
+  // one CTA per (cell, first test index r1); small degrees use fewer threads
+  const int threads = N2 * N3 >= kMatThreads ? kMatThreads : ((N2 * N3 + 31) / 32) * 32;
+  k_cell_matrices_coll<N><<<(unsigned)(a.ncells * N), threads, smem, s>>>(a);
   return (int)cudaGetLastError();
 }
 

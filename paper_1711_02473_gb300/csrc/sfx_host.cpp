@@ -206,6 +206,7 @@ static int upload_tables(const Tab1D* t) {
   if (!e) e = upload_tab_batched(t);
   if (!e) e = upload_tab_scalar_coll(t);
   if (!e) e = upload_tab_scalar_mixed_coll(t);
+  if (!e) e = upload_tab_elastic_lin(t);
   return e;
 }
 
@@ -629,6 +630,70 @@ extern "C" sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, con
   else e = launch_action_hdivcurl(sp, form, prec, a, stream);
   if (e == -1) return SFX_ERR_UNSUPPORTED;
   return e ? SFX_ERR_CUDA : SFX_OK;
+}
+
+// Linearised hyperelastic operator: per colour, or per listed cell (cells != null).
+static sfx_status linearised(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params, const sfx_space* sp,
+                             const double* u, const double* du, double* y, int nrhs, int accumulate,
+                             const int64_t* cells, int64_t ncells, sfx_precision prec, void* stream) {
+  if (!ctx || !sp || !u || !du || !y || nrhs < 1 || nrhs > 64 || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
+  if (sp->family != SFX_VQ || (form != SFX_NEOHOOKE && form != SFX_SVK)) return SFX_ERR_ARG;
+  if (y == du || y == u) return SFX_ERR_ARG;
+  if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3) return SFX_ERR_ARG;
+  if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
+  if (ncells < 0 || (ncells > 0 && !cells)) return SFX_ERR_ARG;
+  sfx_form_params pr = params ? *params : default_params(form);
+  cudaStream_t s = (cudaStream_t)stream;
+  ActArgs a{};
+  a.map = sp->d_map;
+  a.vmap = sp->mesh->d_vmap;
+  a.xyz = sp->mesh->d_xyz;
+  a.x = du;
+  a.xs = u;
+  a.y = y;
+  a.nrhs = nrhs;
+  a.r0 = 0;
+  a.r1 = nrhs;
+  a.alpha = pr.alpha; a.beta = pr.beta; a.mu = pr.mu; a.lambda = pr.lambda;
+  a.status = ctx->d_status;
+  if (cells) {
+    if (ncells == 0) return SFX_OK;
+    a.cells64 = cells;
+    a.ncells = ncells;
+    a.cell_vectors = 1;
+    const int e = launch_linearised_elastic(sp, form, a, stream);
+    if (e == -1) return SFX_ERR_UNSUPPORTED;
+    return e ? SFX_ERR_CUDA : SFX_OK;
+  }
+  if (!accumulate) {
+    if (cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess) return SFX_ERR_CUDA;
+  }
+  for (int col = 0; col < sp->ncolour; ++col) {
+    a.cells = sp->d_cells + sp->colour_off[col];
+    a.ncells = sp->colour_off[col + 1] - sp->colour_off[col];
+    if (a.ncells == 0) continue;
+    const int e = launch_linearised_elastic(sp, form, a, stream);
+    if (e == -1) return SFX_ERR_UNSUPPORTED;
+    if (e) return SFX_ERR_CUDA;
+  }
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_assemble_linearised_action(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                                     const sfx_space* sp, const double* u, const double* du,
+                                                     double* y, int nrhs, int accumulate, sfx_precision prec,
+                                                     void* stream) {
+  return linearised(ctx, form, params, sp, u, du, y, nrhs, accumulate, nullptr, 0, prec, stream);
+}
+
+extern "C" sfx_status sfx_assemble_linearised_cell_vectors(sfx_ctx* ctx, sfx_form form,
+                                                           const sfx_form_params* params, const sfx_space* sp,
+                                                           const double* u, const double* du, int nrhs,
+                                                           const int64_t* cells, int64_t ncells, double* b,
+                                                           sfx_precision prec, void* stream) {
+  if (ncells > 0 && !cells) return SFX_ERR_ARG;
+  if (ncells == 0) return (ctx && sp && u && du && b) ? SFX_OK : SFX_ERR_ARG;
+  return linearised(ctx, form, params, sp, u, du, b, nrhs, 0, cells, ncells, prec, stream);
 }
 
 extern "C" sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,

@@ -93,6 +93,7 @@ struct ActArgs {
   const int32_t* vmap;    // ncell x 8
   const double* xyz;      // nvert x 3
   const double* x;        // ndof x nrhs
+  const double* xs;       // linearised operators: the state (ndof, one vector)
   double* y;              // ndof x nrhs (scatter) or ncells x nloc x nrhs (cell vectors)
   int nrhs;
   int r0, r1;             // right-hand sides handled by this launch: [r0, r1)
@@ -118,6 +119,8 @@ int launch_action_elastic_mixed(const sfx_space* sp, sfx_form form, sfx_precisio
 int launch_action_scalar_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
                                void* stream);
 int launch_action_scalar_naive(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+// Linearised hyperelastic operator at the state a.xs on the directions a.x (FP64).
+int launch_linearised_elastic(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
 // Q_p actions with the collocated GLL rule (B = I): FP64 and TF32x3.
 int launch_action_scalar_coll(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
 int launch_action_scalar_mixed_coll(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
@@ -183,5 +186,6 @@ int upload_tab_batched(const Tab1D* t);
 int upload_tab_qdata(const Tab1D* t);
 int upload_tab_scalar_coll(const Tab1D* t);
 int upload_tab_scalar_mixed_coll(const Tab1D* t);
+int upload_tab_elastic_lin(const Tab1D* t);
 
 }  // namespace sfx
