@@ -32,11 +32,11 @@ L2_FLUSH_BYTES = 256 << 20
 HBM_GBS = 6788.3             # GB300 HBM bandwidth, measured by a STREAM-style copy (GB/s)
 METRIC = "DoFs/s of the operator action (config-2 sweep)"
 # DRAM bytes (read + write) per cell of one colour launch, from the ncu captures of
-# the 32^3, p = 8 case (dram__bytes.sum.per_second x gpu__time_duration / 4096
-# cells); the full-size launch processes 8x the cells, and the traffic of these
-# kernels grows in proportion (x, map, y and factors are per cell).
-NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_mixed", "Q", 8): 104.5e6 / 4096,
-                           ("k_action_scalar_fp64", "Q", 8): 106.3e6 / 4096}
+# the 32^3, p = 8 Laplace case (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch / 4096 cells); the full-size launch processes 8x the cells, and the traffic
+# of these kernels grows in proportion (x, map, y and coordinates are per cell).
+NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_mixed", "Q", 8): (99.158528e6 + 5.254144e6) / 4096,
+                           ("k_action_scalar_fp64", "Q", 8): (99.228160e6 + 6.336000e6) / 4096}
 
 
 def parse():
