@@ -576,6 +576,10 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
     #     (delta-cancelled O(n^5) kernel vs the sum-factorised O(n^7) kernel)
     ex["underintegration"] = underint_block(sfx, torch, ctx, inputs, flush, stream)
     torch.cuda.empty_cache()
+    # --- assembled matrix vs matrix-free action (Sec. 4.2's MatVec comparison): Q_p Laplace, p = 1..6,
+    #     meshes sized to keep the CSR below ~6 GB; SpMV, assembly, FP64 and TF32x3 actions on the same mesh
+    ex["matvec_vs_action"] = matvec_block(sfx, torch, ctx, inputs, flush, stream)
+    torch.cuda.empty_cache()
     # --- element matrices (FP64): Q_p Laplace p=1..8 and NCF/NCE p=1..5 on 32^3,
     #     on a chunk of cells sized to ~1 GB of output; sum-factorised and, p <= 4, naive
     rows = []
@@ -607,6 +611,40 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
                   "flushed); DoFs/s follows the paper's N/t; dofs_per_s_paper for matrices scales N by the "
                   "fraction of cells assembled")
     return ex
+
+
+def matvec_block(sfx, torch, ctx, inputs, flush, stream):
+    """Assembled CSR matrix (pattern untimed, as the paper excludes sparsity
+    creation) vs matrix-free action, Q_p Laplace.  SpMV bytes per product:
+    12 per nonzero (value + column) + 24 per row (x, y, row pointer); the
+    achieved rate is against the measured HBM bandwidth."""
+    rows = []
+    for p, n in [(1, 64), (2, 48), (3, 32), (4, 24), (5, 20), (6, 16)]:
+        mesh = sfx.Mesh.box(ctx, n, n, n, perturb=0.1, seed=0)
+        sp = sfx.Space(mesh, "Q", p)
+        csr = sfx.Csr(sp)
+        vals = torch.empty(csr.nnz, dtype=torch.float64, device="cuda")
+        xd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
+        yd = torch.empty_like(xd)
+        ta = _time(torch, stream, flush, lambda: sfx.sfx_csr_assemble(ctx, "laplace", csr, vals, stream=stream),
+                   reps=2, warm=1)
+        tm = _time(torch, stream, flush, lambda: sfx.sfx_csr_spmv(ctx, csr, vals, xd, yd, stream=stream))
+        tf = _time(torch, stream, flush, lambda: sfx.sfx_assemble_action(ctx, "laplace", sp, xd, yd, stream=stream))
+        tt = _time(torch, stream, flush, lambda: sfx.sfx_assemble_action(ctx, "laplace", sp, xd, yd,
+                                                                         precision="tf32x3", stream=stream))
+        spmv_bytes = 12 * csr.nnz + 24 * csr.nrows
+        rows.append({"p": p, "mesh": "%d^3" % n, "ndof": sp.ndof, "nnz": csr.nnz,
+                     "assembly_ms": round(ta, 4), "spmv_ms": round(tm, 4), "action_fp64_ms": round(tf, 4),
+                     "action_tf32x3_ms": round(tt, 4), "spmv_dofs_per_s": sp.ndof / (tm * 1e-3),
+                     "action_fp64_dofs_per_s": sp.ndof / (tf * 1e-3),
+                     "action_tf32x3_dofs_per_s": sp.ndof / (tt * 1e-3),
+                     "spmv_gb_per_s": spmv_bytes / (tm * 1e-3) / 1e9,
+                     "spmv_frac_of_hbm": spmv_bytes / (tm * 1e-3) / 1e9 / HBM_GBS})
+        del vals, xd, yd, csr, sp, mesh
+        torch.cuda.empty_cache()
+    return {"rows": rows, "device_status": ctx.sync_status(),
+            "note": "pattern built on the host, untimed; assembly = sum-factorised element matrices + coloured "
+                    "scatter into the CSR values"}
 
 
 def underint_block(sfx, torch, ctx, inputs, flush, stream):

@@ -233,6 +233,36 @@ sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_for
                                       const sfx_space* space, int64_t cell_begin, int64_t cell_end,
                                       double* A, sfx_precision prec, sfx_algo algo, void* stream);
 
+/* ------------------------------------------------------- assembled matrix */
+
+/* Global sparse matrix of a scalar bilinear form (mass, Laplace, Helmholtz)
+ * on Q_p or DQ_p in CSR format: A = sum_K P_K^T A^K P_K, the local tensors
+ * added into the global matrix (Sec. 1.1), the assembled counterpart of the
+ * matrix-free action that Sec. 4.2 compares with.
+ * sfx_csr_create builds the sparsity pattern on the host (every pair of dofs
+ * that share a cell; rows sorted; Q_p from the Kronecker product of the 1D
+ * patterns of the structured mesh) and copies it to the device; it also holds
+ * a device scratch for the element matrices of one chunk of cells (<= 512 MB).
+ * Pattern: row_ptr int64 (nrows + 1), col int32 (nnz), host views owned by the
+ * object.  With a host-only context only the host pattern is built.
+ * Errors: SFX_ERR_ARG, SFX_ERR_UNSUPPORTED (family), SFX_ERR_ALLOC, SFX_ERR_CUDA. */
+typedef struct sfx_csr sfx_csr;
+sfx_status sfx_csr_create(const sfx_space* space, sfx_csr** out);
+sfx_status sfx_csr_info(const sfx_csr* csr, int64_t* nrows, int64_t* nnz, const int64_t** row_ptr_host,
+                        const int32_t** col_host);
+/* Fill values (device, nnz doubles, caller-owned; overwritten) with the
+ * assembled matrix of `form`: element matrices by sum factorisation (FP64, in
+ * chunks), then a scatter colour by colour (conflict-free, deterministic).
+ * Errors: SFX_ERR_ARG (null, form, host-only context), SFX_ERR_CUDA. */
+sfx_status sfx_csr_assemble(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params, const sfx_csr* csr,
+                            double* values, void* stream);
+/* y = A x with the given values (device, nnz); x, y device, nrows doubles,
+ * must not alias.  A group of lanes per row, fixed-order reduction
+ * (deterministic).  Errors: SFX_ERR_ARG, SFX_ERR_CUDA. */
+sfx_status sfx_csr_spmv(sfx_ctx* ctx, const sfx_csr* csr, const double* values, const double* x, double* y,
+                        void* stream);
+void sfx_csr_destroy(sfx_csr* csr);
+
 /* ----------------------------------------------- stored geometric factors */
 
 /* Geometric factors at the quadrature points of every cell of a Q_p / DQ_p

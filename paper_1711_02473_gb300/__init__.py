@@ -34,7 +34,8 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy",
            "sfx_padaptive_action_noalloc", "sfx_qdata_create", "sfx_qdata_destroy",
            "sfx_assemble_action_stored", "sfx_tune_set_cells_per_cta", "sfx_tune_get_cells_per_cta",
-           "sfx_assemble_linearised_action", "sfx_assemble_linearised_cell_vectors"]
+           "sfx_assemble_linearised_action", "sfx_assemble_linearised_cell_vectors",
+           "sfx_csr_create", "sfx_csr_info", "sfx_csr_assemble", "sfx_csr_spmv", "sfx_csr_destroy"]
 TUNE_KERNEL = {"fp64": 0, "mixed": 1, "mixed_stored": 2, "elastic_mixed": 3}
 QDATA = {"fp64": 1, "fp32": 2, "both": 3}
 EXEC = {"graph": 0, "per_launch": 1}
@@ -84,6 +85,12 @@ def lib():
         L.sfx_tabulate_1d.argtypes = [i, i, i, i, i, P, P, P]
         L.sfx_assemble_action.argtypes = [P, i, C.POINTER(_Params), P, P, P, i, i, i, i, P]
         L.sfx_assemble_linearised_action.argtypes = [P, i, C.POINTER(_Params), P, P, P, P, i, i, i, P]
+        L.sfx_csr_create.argtypes = [P, C.POINTER(P)]
+        L.sfx_csr_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(P), C.POINTER(P)]
+        L.sfx_csr_assemble.argtypes = [P, i, C.POINTER(_Params), P, P, P]
+        L.sfx_csr_spmv.argtypes = [P, P, P, P, P, P]
+        L.sfx_csr_destroy.argtypes = [P]
+        L.sfx_csr_destroy.restype = None
         L.sfx_assemble_linearised_cell_vectors.argtypes = [P, i, C.POINTER(_Params), P, P, P, i, P, i64, P, i, P]
         L.sfx_assemble_cell_vectors.argtypes = [P, i, C.POINTER(_Params), P, P, i, P, i64, P, i, P]
         L.sfx_assemble_cell_matrices.argtypes = [P, i, C.POINTER(_Params), P, i64, i64, P, i, i, P]
@@ -221,6 +228,53 @@ class Space:
             self.close()
         except Exception:
             pass
+
+
+class Csr:
+    """Global sparse matrix pattern (CSR) of a Q_p / DQ_p space; values are
+    caller-owned device arrays of nnz doubles (sfx_csr_assemble fills them)."""
+
+    def __init__(self, space):
+        self.space = space
+        self.h = C.c_void_p()
+        _check(lib().sfx_csr_create(space.h, C.byref(self.h)), "sfx_csr_create")
+        nr, nz, rp, cl = C.c_int64(), C.c_int64(), C.c_void_p(), C.c_void_p()
+        _check(lib().sfx_csr_info(self.h, C.byref(nr), C.byref(nz), C.byref(rp), C.byref(cl)), "sfx_csr_info")
+        self.nrows, self.nnz = nr.value, nz.value
+        self._rp, self._col = rp, cl
+
+    def pattern(self):
+        """Host copies (row_ptr int64, col int32)."""
+        rp = np.ctypeslib.as_array(C.cast(self._rp, C.POINTER(C.c_int64)), shape=(self.nrows + 1,)).copy()
+        col = np.ctypeslib.as_array(C.cast(self._col, C.POINTER(C.c_int32)), shape=(self.nnz,)).copy()
+        return rp, col
+
+    def close(self):
+        if self.h:
+            lib().sfx_csr_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sfx_csr_assemble(ctx, form, csr, values, params=None, stream=None):
+    if values.numel() != csr.nnz:
+        raise ValueError("values must hold nnz doubles")
+    _check(lib().sfx_csr_assemble(ctx.h, FORM[form], _params(params), csr.h, _dptr(values, "float64"),
+                                  _stream(stream)), "sfx_csr_assemble")
+    return values
+
+
+def sfx_csr_spmv(ctx, csr, values, x, y, stream=None):
+    if values.numel() != csr.nnz or x.numel() != csr.nrows or y.numel() != csr.nrows:
+        raise ValueError("values: nnz doubles; x, y: nrows doubles")
+    _check(lib().sfx_csr_spmv(ctx.h, csr.h, _dptr(values, "float64"), _dptr(x, "float64"), _dptr(y, "float64"),
+                              _stream(stream)), "sfx_csr_spmv")
+    return y
 
 
 def sfx_tabulate_1d(nodes, ndof1d, qrule, nq, deriv=0):

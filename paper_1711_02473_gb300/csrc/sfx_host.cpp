@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "sfx_internal.h"
 
@@ -720,6 +721,160 @@ extern "C" sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, co
                                       : launch_cell_matrices(sp, form, algo, a, stream);
   if (e == -1) return SFX_ERR_UNSUPPORTED;
   return e ? SFX_ERR_CUDA : SFX_OK;
+}
+
+// ------------------------------------------------------------ sparse matrix
+struct sfx_csr {
+  const sfx_space* space = nullptr;
+  int64_t nrows = 0, nnz = 0;
+  std::vector<int64_t> row_ptr;  // host, nrows + 1
+  std::vector<int32_t> col;      // host, nnz (sorted within each row)
+  int64_t* d_row_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  double* d_scratch = nullptr;   // element matrices of one chunk of cells
+  int64_t chunk = 0;             // cells per chunk
+  int lanes = 32;                // lanes per row in the product
+};
+
+namespace {
+// Column range [lo, hi] of 1D Q_p node I on a line of ncell cells: the nodes
+// of the cells that contain I (two cells for a vertex node inside the line).
+inline void q_range_1d(int64_t I, int p, int64_t ncell, int64_t* lo, int64_t* hi) {
+  int64_t cmin = I / p, cmax = I / p;
+  if (I % p == 0) cmin -= 1;
+  if (cmin < 0) cmin = 0;
+  if (cmax > ncell - 1) cmax = ncell - 1;
+  *lo = (int64_t)p * cmin;
+  *hi = (int64_t)p * (cmax + 1);
+}
+}  // namespace
+
+extern "C" sfx_status sfx_csr_create(const sfx_space* sp, sfx_csr** out) {
+  if (!sp || !out) return SFX_ERR_ARG;
+  *out = nullptr;
+  if (sp->family != SFX_Q && sp->family != SFX_DQ) return SFX_ERR_UNSUPPORTED;
+  const sfx_mesh* m = sp->mesh;
+  const int p = sp->p, n = p + 1, nloc = sp->nloc;
+  sfx_csr* c = new (std::nothrow) sfx_csr;
+  if (!c) return SFX_ERR_ALLOC;
+  c->space = sp;
+  c->nrows = sp->ndof;
+  const int64_t N[3] = {m->nx, m->ny, m->nz};
+  const int64_t M[3] = {p * N[0] + 1, p * N[1] + 1, p * N[2] + 1};
+  try {
+    c->row_ptr.resize((size_t)c->nrows + 1);
+  } catch (...) { delete c; return SFX_ERR_ALLOC; }
+  // row lengths: Q_p -- the pattern is the Kronecker product of the 1D
+  // patterns (two nodes share a cell iff they share a 1D cell along every
+  // axis), each a contiguous range; DQ_p -- the dofs of the row's own cell
+  c->row_ptr[0] = 0;
+  for (int64_t r = 0; r < c->nrows; ++r) {
+    int64_t len;
+    if (sp->family == SFX_DQ) {
+      len = nloc;
+    } else {
+      const int64_t I[3] = {r / (M[1] * M[2]), (r / M[2]) % M[1], r % M[2]};
+      len = 1;
+      for (int d = 0; d < 3; ++d) {
+        int64_t lo, hi;
+        q_range_1d(I[d], p, N[d], &lo, &hi);
+        len *= hi - lo + 1;
+      }
+    }
+    c->row_ptr[r + 1] = c->row_ptr[r] + len;
+  }
+  c->nnz = c->row_ptr[c->nrows];
+  try {
+    c->col.resize((size_t)c->nnz);
+  } catch (...) { delete c; return SFX_ERR_ALLOC; }
+  const unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (unsigned t = 0; t < nth; ++t) {
+    pool.emplace_back([&, t]() {
+      for (int64_t r = t; r < c->nrows; r += nth) {
+        int32_t* o = &c->col[(size_t)c->row_ptr[r]];
+        if (sp->family == SFX_DQ) {
+          const int64_t b = (r / nloc) * nloc;
+          for (int l = 0; l < nloc; ++l) o[l] = (int32_t)(b + l);
+          continue;
+        }
+        const int64_t I[3] = {r / (M[1] * M[2]), (r / M[2]) % M[1], r % M[2]};
+        int64_t lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) q_range_1d(I[d], p, N[d], &lo[d], &hi[d]);
+        for (int64_t a = lo[0]; a <= hi[0]; ++a)
+          for (int64_t b = lo[1]; b <= hi[1]; ++b)
+            for (int64_t k = lo[2]; k <= hi[2]; ++k) *o++ = (int32_t)((a * M[1] + b) * M[2] + k);
+      }
+    });
+  }
+  for (auto& th : pool) th.join();
+  const double avg = c->nrows ? (double)c->nnz / (double)c->nrows : 0.0;
+  c->lanes = avg < 24 ? 4 : (avg < 48 ? 8 : (avg < 128 ? 16 : 32));
+  (void)n;
+  if (m->ctx->device < 0) {
+    *out = c;
+    return SFX_OK;
+  }
+  sfx_status st = to_device(c->row_ptr.data(), c->row_ptr.size(), &c->d_row_ptr);
+  if (!st) st = to_device(c->col.data(), c->col.size(), &c->d_col);
+  if (!st) {
+    const int64_t per = (int64_t)nloc * nloc * (int64_t)sizeof(double);
+    c->chunk = std::max<int64_t>(1, std::min<int64_t>(m->ncell, (512LL << 20) / per));
+    if (cudaMalloc((void**)&c->d_scratch, (size_t)(c->chunk * per)) != cudaSuccess) {
+      c->d_scratch = nullptr;
+      st = SFX_ERR_ALLOC;
+    }
+  }
+  if (st) { sfx_csr_destroy(c); return st; }
+  *out = c;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_csr_info(const sfx_csr* c, int64_t* nrows, int64_t* nnz, const int64_t** row_ptr,
+                                   const int32_t** col) {
+  if (!c) return SFX_ERR_ARG;
+  if (nrows) *nrows = c->nrows;
+  if (nnz) *nnz = c->nnz;
+  if (row_ptr) *row_ptr = c->row_ptr.data();
+  if (col) *col = c->col.data();
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_csr_assemble(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                       const sfx_csr* c, double* values, void* stream) {
+  if (!ctx || !c || !values || ctx->device < 0 || !c->d_col) return SFX_ERR_ARG;
+  const sfx_space* sp = c->space;
+  if (form != SFX_MASS && form != SFX_LAPLACE && form != SFX_HELMHOLTZ) return SFX_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(values, 0, (size_t)c->nnz * sizeof(double), s) != cudaSuccess) return SFX_ERR_CUDA;
+  const int64_t ncell = sp->mesh->ncell;
+  for (int64_t b = 0; b < ncell; b += c->chunk) {
+    const int64_t e = std::min(ncell, b + c->chunk);
+    const sfx_status st = sfx_assemble_cell_matrices(ctx, form, params, sp, b, e, c->d_scratch, SFX_PREC_FP64,
+                                                     SFX_ALGO_SUMFACT, stream);
+    if (st) return st;
+    // colour by colour: cells of one colour share no dof, so no row
+    const int ncol = sp->family == SFX_DQ ? 1 : 8;
+    for (int col = 0; col < ncol; ++col)
+      if (launch_csr_scatter(c->d_scratch, b, e - b, sp->nloc, sp->d_map, c->d_row_ptr, c->d_col, values,
+                             sp->family == SFX_DQ ? -1 : col, sp->mesh->ny, sp->mesh->nz, ctx->d_status, stream))
+        return SFX_ERR_CUDA;
+  }
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_csr_spmv(sfx_ctx* ctx, const sfx_csr* c, const double* values, const double* x,
+                                   double* y, void* stream) {
+  if (!ctx || !c || !values || !x || !y || x == y || ctx->device < 0 || !c->d_col) return SFX_ERR_ARG;
+  return launch_csr_spmv(c->lanes, c->nrows, c->d_row_ptr, c->d_col, values, x, y, stream) ? SFX_ERR_CUDA : SFX_OK;
+}
+
+extern "C" void sfx_csr_destroy(sfx_csr* c) {
+  if (!c) return;
+  if (c->d_row_ptr) cudaFree(c->d_row_ptr);
+  if (c->d_col) cudaFree(c->d_col);
+  if (c->d_scratch) cudaFree(c->d_scratch);
+  delete c;
 }
 
 // -------------------------------------------------------------------- plans

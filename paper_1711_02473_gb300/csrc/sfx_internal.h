@@ -141,6 +141,13 @@ int launch_cell_matrices_coll(const sfx_space* sp, sfx_form form, const MatArgs&
 // plans); also used by the per-launch comparison mode.
 int launch_scalar_fp64_degree(int p, bool dq, sfx_form form, const ActArgs& a, int64_t ncell_total, void* stream);
 
+// Sparse matrix kernels (k_csr.cu).
+int launch_csr_scatter(const double* A, int64_t cell_begin, int64_t ncells, int nloc, const int32_t* map,
+                       const int64_t* row_ptr, const int32_t* col, double* values, int colour, int ny, int nz,
+                       uint32_t* status, void* stream);
+int launch_csr_spmv(int lanes, int64_t nrows, const int64_t* row_ptr, const int32_t* col, const double* values,
+                    const double* x, double* y, void* stream);
+
 // Persistent batched launch over a tile list (k_batched.cu).
 struct BatchTile {
   int32_t p, form, first, count;  // degree, form slot, range in the degree-sorted cell list
