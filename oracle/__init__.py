@@ -63,6 +63,9 @@ def lib():
         L.orc_cell_matrices_rule.argtypes = [i, i, i, i, i, P, i, i, i, P, i64, i64, P, i]
         L.orc_linearised_cell_vectors.argtypes = [i, i, i, P, i, i, i, P, P, P, i, P, i64, P, i]
         L.orc_linearised_action.argtypes = [i, i, i, P, i, i, i, P, P, P, P, i, i]
+        L.orc_weighted_cell_vectors.argtypes = [i, i, i, i, i, i, P, P, P, i, P, i64, P, i]
+        L.orc_weighted_action.argtypes = [i, i, i, i, i, i, P, P, P, P, i, i]
+        L.orc_weighted_cell_matrices.argtypes = [i, i, i, i, i, i, P, P, i64, i64, P, i]
         L.orc_q_node_coords.argtypes = [i, i, i, i, P, P]
         L.orc_interp_grad_q_to_nce.argtypes = [i, i, i, i, P, P]
         L.orc_interp_curl_nce_to_ncf.argtypes = [i, i, i, i, P, P]
@@ -161,6 +164,42 @@ def cell_matrices(family, form, p, dims, coords, cell_begin=0, cell_end=None, nq
     coords = _f64(coords)
     _check(lib().orc_cell_matrices_rule(FAMILIES[family], FORMS[form], p, nq or p + 1, QRULES[qrule], _p(pr),
                                         *dims, _p(coords), cell_begin, cell_end, _p(A), nthreads), "cell_matrices")
+    return A
+
+
+def weighted_action(family, p, dims, coords, kappa, x, nq=None, nthreads=0):
+    """y = A_kappa x for the weighted Laplace form int kappa grad u . grad v,
+    kappa given by its dofs in the same space."""
+    ndof, _ = space_size(family, p, dims)
+    x, kappa = _f64(x), _f64(kappa)
+    nrhs = 1 if x.ndim == 1 else x.shape[1]
+    assert kappa.shape == (ndof,) and x.shape[0] == ndof
+    y = np.zeros_like(x)
+    _check(lib().orc_weighted_action(FAMILIES[family], p, nq or p + 1, *dims, _p(_f64(coords)), _p(kappa), _p(x),
+                                     _p(y), nrhs, nthreads), "weighted_action")
+    return y
+
+
+def weighted_cell_vectors(family, p, dims, coords, kappa, x, cells, nq=None, nthreads=0):
+    ndof, nloc = space_size(family, p, dims)
+    x, kappa = _f64(x), _f64(kappa)
+    nrhs = 1 if x.ndim == 1 else x.shape[1]
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    b = np.zeros((len(cells), nloc, nrhs))
+    _check(lib().orc_weighted_cell_vectors(FAMILIES[family], p, nq or p + 1, *dims, _p(_f64(coords)), _p(kappa),
+                                           _p(x), nrhs, _p(cells), len(cells), _p(b), nthreads),
+           "weighted_cell_vectors")
+    return b[:, :, 0] if x.ndim == 1 else b
+
+
+def weighted_cell_matrices(family, p, dims, coords, kappa, cell_begin=0, cell_end=None, nq=None, nthreads=0):
+    ndof, nloc = space_size(family, p, dims)
+    ncell = dims[0] * dims[1] * dims[2]
+    cell_end = ncell if cell_end is None else cell_end
+    A = np.zeros((cell_end - cell_begin, nloc, nloc))
+    _check(lib().orc_weighted_cell_matrices(FAMILIES[family], p, nq or p + 1, *dims, _p(_f64(coords)),
+                                            _p(_f64(kappa)), cell_begin, cell_end, _p(A), nthreads),
+           "weighted_cell_matrices")
     return A
 
 

@@ -597,8 +597,11 @@ static int dpiola(int form, const double* params, double Hu[3][3], double dF[3][
 /* One cell: local vector b (nloc x nrhs) for coefficient xl (nloc x nrhs)    */
 /* ------------------------------------------------------------------------ */
 
+/* kap: the cell's dofs of the coefficient kappa of the weighted Laplace form
+ * int kappa grad u . grad v (Sec. 1.1, Eq. weighted_laplace), interpolated in
+ * the same space; NULL for every other form. */
 static int cell_vector(const elem_t* E, const tab_t* T, int form, const double* params,
-                       const double X[8][3], const double* xl, int nrhs, double* b) {
+                       const double X[8][3], const double* xl, int nrhs, const double* kap, double* b) {
   int nloc = E->nloc;
   memset(b, 0, sizeof(double) * nloc * nrhs);
   for (int q = 0; q < T->nq3; ++q) {
@@ -613,6 +616,11 @@ static int cell_vector(const elem_t* E, const tab_t* T, int form, const double* 
       if (E->family == ORC_Q || E->family == ORC_DQ) {
         double a_lap, b_mass;
         scalar_weights(form, params, &a_lap, &b_mass);
+        if (kap) { /* kappa(xi_q) = sum_l kappa_l psi_l(xi_q) */
+          a_lap = 0.0;
+          for (int l = 0; l < nloc; ++l) a_lap += kap[l] * val[l];
+          b_mass = 0.0;
+        }
         /* coefficient evaluation, Eq. coeff_eval: u and reference gradient */
         double u = 0.0, gu[3] = {0, 0, 0};
         for (int l = 0; l < nloc; ++l) {
@@ -714,10 +722,31 @@ int orc_cell_vectors(int family, int form, int p, int nq, const double* params,
                                nthreads);
 }
 
+static int cell_vectors_impl(int family, int form, int p, int nq, int qrule, const double* params,
+                             int nx, int ny, int nz, const double* coords, const double* kappa,
+                             const double* x, int nrhs, const int64_t* cells, int64_t ncells,
+                             double* b, int nthreads);
+
 int orc_cell_vectors_rule(int family, int form, int p, int nq, int qrule, const double* params,
                           int nx, int ny, int nz, const double* coords,
                           const double* x, int nrhs, const int64_t* cells, int64_t ncells,
                           double* b, int nthreads) {
+  return cell_vectors_impl(family, form, p, nq, qrule, params, nx, ny, nz, coords, NULL, x, nrhs, cells, ncells,
+                           b, nthreads);
+}
+
+int orc_weighted_cell_vectors(int family, int p, int nq, int nx, int ny, int nz, const double* coords,
+                              const double* kappa, const double* x, int nrhs, const int64_t* cells,
+                              int64_t ncells, double* b, int nthreads) {
+  if (!kappa || (family != ORC_Q && family != ORC_DQ)) return -1;
+  return cell_vectors_impl(family, ORC_LAPLACE, p, nq, ORC_GL, NULL, nx, ny, nz, coords, kappa, x, nrhs, cells,
+                           ncells, b, nthreads);
+}
+
+static int cell_vectors_impl(int family, int form, int p, int nq, int qrule, const double* params,
+                             int nx, int ny, int nz, const double* coords, const double* kappa,
+                             const double* x, int nrhs, const int64_t* cells, int64_t ncells,
+                             double* b, int nthreads) {
   elem_t E;
   if (make_elem(family, p, nx, ny, nz, &E) || !form_ok(family, form) || nrhs < 1) return -1;
   tab_t T;
@@ -729,6 +758,7 @@ int orc_cell_vectors_rule(int family, int form, int p, int nq, int qrule, const 
   {
     int64_t* dofs = (int64_t*)malloc(sizeof(int64_t) * E.nloc);
     double* xl = (double*)malloc(sizeof(double) * E.nloc * nrhs);
+    double* kl = (double*)malloc(sizeof(double) * E.nloc);
 #pragma omp for schedule(dynamic, 1)
     for (int64_t k = 0; k < ncells; ++k) {
       int64_t c = cells[k];
@@ -738,11 +768,14 @@ int orc_cell_vectors_rule(int family, int form, int p, int nq, int qrule, const 
       elem_cell_dofs(&E, ny, nz, c, dofs);
       for (int l = 0; l < E.nloc; ++l)
         for (int r = 0; r < nrhs; ++r) xl[l * nrhs + r] = x[dofs[l] * nrhs + r];
-      int e = cell_vector(&E, &T, form, params, X, xl, nrhs, &b[(size_t)k * E.nloc * nrhs]);
+      if (kappa)
+        for (int l = 0; l < E.nloc; ++l) kl[l] = kappa[dofs[l]];
+      int e = cell_vector(&E, &T, form, params, X, xl, nrhs, kappa ? kl : NULL, &b[(size_t)k * E.nloc * nrhs]);
       if (e) err = e;
     }
     free(dofs);
     free(xl);
+    free(kl);
   }
   tab_free(&T);
   return err;
@@ -754,9 +787,25 @@ int orc_action(int family, int form, int p, int nq, const double* params,
   return orc_action_rule(family, form, p, nq, ORC_GL, params, nx, ny, nz, coords, x, y, nrhs, nthreads);
 }
 
+static int action_impl(int family, int form, int p, int nq, int qrule, const double* params,
+                       int nx, int ny, int nz, const double* coords, const double* kappa,
+                       const double* x, double* y, int nrhs, int nthreads);
+
 int orc_action_rule(int family, int form, int p, int nq, int qrule, const double* params,
                     int nx, int ny, int nz, const double* coords,
                     const double* x, double* y, int nrhs, int nthreads) {
+  return action_impl(family, form, p, nq, qrule, params, nx, ny, nz, coords, NULL, x, y, nrhs, nthreads);
+}
+
+int orc_weighted_action(int family, int p, int nq, int nx, int ny, int nz, const double* coords,
+                        const double* kappa, const double* x, double* y, int nrhs, int nthreads) {
+  if (!kappa || (family != ORC_Q && family != ORC_DQ)) return -1;
+  return action_impl(family, ORC_LAPLACE, p, nq, ORC_GL, NULL, nx, ny, nz, coords, kappa, x, y, nrhs, nthreads);
+}
+
+static int action_impl(int family, int form, int p, int nq, int qrule, const double* params,
+                       int nx, int ny, int nz, const double* coords, const double* kappa,
+                       const double* x, double* y, int nrhs, int nthreads) {
   elem_t E;
   if (make_elem(family, p, nx, ny, nz, &E) || !form_ok(family, form) || nrhs < 1) return -1;
   memset(y, 0, sizeof(double) * E.ndof * nrhs);
@@ -769,8 +818,8 @@ int orc_action_rule(int family, int form, int p, int nq, int qrule, const double
   for (int64_t c0 = 0; c0 < ncell && !err; c0 += CH) {
     int64_t m = (ncell - c0 < CH) ? ncell - c0 : CH;
     for (int64_t k = 0; k < m; ++k) cells[k] = c0 + k;
-    err = orc_cell_vectors_rule(family, form, p, nq, qrule, params, nx, ny, nz, coords, x, nrhs, cells, m, b,
-                                nthreads);
+    err = cell_vectors_impl(family, form, p, nq, qrule, params, nx, ny, nz, coords, kappa, x, nrhs, cells, m, b,
+                            nthreads);
     /* global assembly y += P_K^T b^K, cells in order */
     for (int64_t k = 0; k < m && !err; ++k) {
       elem_cell_dofs(&E, ny, nz, c0 + k, dofs);
@@ -791,9 +840,27 @@ int orc_cell_matrices(int family, int form, int p, int nq, const double* params,
                                 nthreads);
 }
 
+static int cell_matrices_impl(int family, int form, int p, int nq, int qrule, const double* params,
+                              int nx, int ny, int nz, const double* coords, const double* kappa,
+                              int64_t cell_begin, int64_t cell_end, double* A, int nthreads);
+
 int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const double* params,
                            int nx, int ny, int nz, const double* coords,
                            int64_t cell_begin, int64_t cell_end, double* A, int nthreads) {
+  return cell_matrices_impl(family, form, p, nq, qrule, params, nx, ny, nz, coords, NULL, cell_begin, cell_end, A,
+                            nthreads);
+}
+
+int orc_weighted_cell_matrices(int family, int p, int nq, int nx, int ny, int nz, const double* coords,
+                               const double* kappa, int64_t cell_begin, int64_t cell_end, double* A, int nthreads) {
+  if (!kappa || (family != ORC_Q && family != ORC_DQ)) return -1;
+  return cell_matrices_impl(family, ORC_LAPLACE, p, nq, ORC_GL, NULL, nx, ny, nz, coords, kappa, cell_begin,
+                            cell_end, A, nthreads);
+}
+
+static int cell_matrices_impl(int family, int form, int p, int nq, int qrule, const double* params,
+                              int nx, int ny, int nz, const double* coords, const double* kappa,
+                              int64_t cell_begin, int64_t cell_end, double* A, int nthreads) {
   elem_t E;
   if (make_elem(family, p, nx, ny, nz, &E) || !form_ok(family, form)) return -1;
   if (form == ORC_NEOHOOKE || form == ORC_SVK) return -1;
@@ -810,12 +877,18 @@ int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const
     double* pv = (double*)malloc(sizeof(double) * nloc * 3);
     double* sv = (double*)malloc(sizeof(double) * nloc);
     double* pm = (double*)malloc(sizeof(double) * nloc * 3);
+    double* kl = (double*)malloc(sizeof(double) * nloc);
+    int64_t* kd = (int64_t*)malloc(sizeof(int64_t) * nloc);
 #pragma omp for schedule(dynamic, 1)
     for (int64_t c = cell_begin; c < cell_end; ++c) {
       double* Ac = &A[(size_t)(c - cell_begin) * nloc * nloc];
       memset(Ac, 0, sizeof(double) * nloc * nloc);
       double X[8][3];
       cell_vertices(nx, ny, nz, coords, c, X);
+      if (kappa) {
+        elem_cell_dofs(&E, ny, nz, c, kd);
+        for (int l = 0; l < nloc; ++l) kl[l] = kappa[kd[l]];
+      }
       for (int q = 0; q < T.nq3; ++q) {
         double xi[3];
         qpoint(&T, q, xi);
@@ -846,6 +919,11 @@ int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const
         if (E.family == ORC_Q || E.family == ORC_DQ) {
           double a_lap, b_mass;
           scalar_weights(form, params, &a_lap, &b_mass);
+          if (kappa) { /* weighted Laplace: kappa(xi_q) = sum_l kappa_l psi_l(xi_q) */
+            a_lap = 0.0;
+            for (int l = 0; l < nloc; ++l) a_lap += kl[l] * val[l];
+            b_mass = 0.0;
+          }
           double sw = (g_plant == 2) ? w : w * g.S;
           cA = sw * a_lap;
           cB = sw * b_mass;
@@ -871,6 +949,8 @@ int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const
     free(pv);
     free(sv);
     free(pm);
+    free(kl);
+    free(kd);
   }
   tab_free(&T);
   return err;

@@ -87,6 +87,16 @@ int orc_action_rule(int family, int form, int p, int nq, int qrule, const double
 int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const double* params,
                            int nx, int ny, int nz, const double* coords,
                            int64_t cell_begin, int64_t cell_end, double* A, int nthreads);
+/* Weighted Laplace form int kappa grad u . grad v (Sec. 1.1, Eq.
+ * weighted_laplace) on Q_p / DQ_p, the coefficient kappa given by its dofs in
+ * the same space (ndof values): per-cell vectors, action, element matrices. */
+int orc_weighted_cell_vectors(int family, int p, int nq, int nx, int ny, int nz, const double* coords,
+                              const double* kappa, const double* x, int nrhs, const int64_t* cells,
+                              int64_t ncells, double* b, int nthreads);
+int orc_weighted_action(int family, int p, int nq, int nx, int ny, int nz, const double* coords,
+                        const double* kappa, const double* x, double* y, int nrhs, int nthreads);
+int orc_weighted_cell_matrices(int family, int p, int nq, int nx, int ny, int nz, const double* coords,
+                               const double* kappa, int64_t cell_begin, int64_t cell_end, double* A, int nthreads);
 /* Linearised hyperelastic operator (NEOHOOKE or SVK) at the state u (ndof):
  * per-cell vectors and the assembled action on the directions du (ndof x
  * nrhs), b^K_(a,j) = sum_q w_q |J| dP(F(u); grad du) : grad(psi_j e_a). */
