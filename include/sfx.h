@@ -195,6 +195,22 @@ sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, const sfx_form
                                      const int64_t* cells, int64_t ncells, double* b,
                                      sfx_precision prec, void* stream);
 
+/* Weighted Laplace form a(u, v) = int kappa grad u . grad v (Sec. 1.1, Eq.
+ * weighted_laplace) on Q_p / DQ_p, FP64: kappa is a coefficient given by its
+ * dofs in the same space (device, ndof doubles, read-only), interpolated to
+ * the Gauss points like u (Sec. 3.3, Eq. coeff_eval).
+ * Action: x, y device, ndof x nrhs (y must alias neither x nor kappa);
+ * accumulate as in sfx_assemble_action; deterministic colour passes.
+ * Element matrices: A device, (cell_end - cell_begin) x nloc x nloc, row =
+ * test, by sum factorisation (kappa evaluated at each point).
+ * Errors: SFX_ERR_ARG (null, aliasing, family, range), SFX_ERR_UNSUPPORTED
+ * (precision), SFX_ERR_CUDA. */
+sfx_status sfx_assemble_weighted_action(sfx_ctx* ctx, const sfx_space* space, const double* kappa, const double* x,
+                                        double* y, int nrhs, int accumulate, sfx_precision prec, void* stream);
+sfx_status sfx_assemble_weighted_cell_matrices(sfx_ctx* ctx, const sfx_space* space, const double* kappa,
+                                               int64_t cell_begin, int64_t cell_end, double* A, sfx_precision prec,
+                                               void* stream);
+
 /* Action of the linearised hyperelastic operator (the Jacobian of the
  * SFX_NEOHOOKE / SFX_SVK residual; Sec. 4.1 times the action of this
  * operator for the Saint Venant-Kirchhoff law) on vector Q_p:

@@ -35,7 +35,8 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_padaptive_action_noalloc", "sfx_qdata_create", "sfx_qdata_destroy",
            "sfx_assemble_action_stored", "sfx_tune_set_cells_per_cta", "sfx_tune_get_cells_per_cta",
            "sfx_assemble_linearised_action", "sfx_assemble_linearised_cell_vectors",
-           "sfx_csr_create", "sfx_csr_info", "sfx_csr_assemble", "sfx_csr_spmv", "sfx_csr_destroy"]
+           "sfx_csr_create", "sfx_csr_info", "sfx_csr_assemble", "sfx_csr_spmv", "sfx_csr_destroy",
+           "sfx_assemble_weighted_action", "sfx_assemble_weighted_cell_matrices"]
 TUNE_KERNEL = {"fp64": 0, "mixed": 1, "mixed_stored": 2, "elastic_mixed": 3}
 QDATA = {"fp64": 1, "fp32": 2, "both": 3}
 EXEC = {"graph": 0, "per_launch": 1}
@@ -86,6 +87,8 @@ def lib():
         L.sfx_assemble_action.argtypes = [P, i, C.POINTER(_Params), P, P, P, i, i, i, i, P]
         L.sfx_assemble_linearised_action.argtypes = [P, i, C.POINTER(_Params), P, P, P, P, i, i, i, P]
         L.sfx_csr_create.argtypes = [P, C.POINTER(P)]
+        L.sfx_assemble_weighted_action.argtypes = [P, P, P, P, P, i, i, i, P]
+        L.sfx_assemble_weighted_cell_matrices.argtypes = [P, P, P, i64, i64, P, i, P]
         L.sfx_csr_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(P), C.POINTER(P)]
         L.sfx_csr_assemble.argtypes = [P, i, C.POINTER(_Params), P, P, P]
         L.sfx_csr_spmv.argtypes = [P, P, P, P, P, P]
@@ -294,6 +297,26 @@ def sfx_assemble_action(ctx, form, space, x, y, nrhs=None, accumulate=False, pre
                                      _dptr(y, "float64"), nrhs, int(bool(accumulate)), PRECISION[precision],
                                      ALGO[algo], _stream(stream)), "sfx_assemble_action")
     return y
+
+
+def sfx_assemble_weighted_action(ctx, space, kappa, x, y, nrhs=None, accumulate=False, precision="fp64",
+                                 stream=None):
+    nrhs = nrhs if nrhs is not None else (1 if x.dim() == 1 else x.shape[1])
+    if kappa.numel() != space.ndof or x.numel() != space.ndof * nrhs or y.numel() != space.ndof * nrhs:
+        raise ValueError("kappa must hold ndof doubles; x and y ndof * nrhs")
+    _check(lib().sfx_assemble_weighted_action(ctx.h, space.h, _dptr(kappa, "float64"), _dptr(x, "float64"),
+                                              _dptr(y, "float64"), nrhs, int(bool(accumulate)),
+                                              PRECISION[precision], _stream(stream)), "sfx_assemble_weighted_action")
+    return y
+
+
+def sfx_assemble_weighted_cell_matrices(ctx, space, kappa, cell_begin, cell_end, A, precision="fp64", stream=None):
+    if A.numel() != (cell_end - cell_begin) * space.nloc * space.nloc or kappa.numel() != space.ndof:
+        raise ValueError("A must hold ncells * nloc * nloc doubles, kappa ndof")
+    _check(lib().sfx_assemble_weighted_cell_matrices(ctx.h, space.h, _dptr(kappa, "float64"), cell_begin, cell_end,
+                                                     _dptr(A, "float64"), PRECISION[precision], _stream(stream)),
+           "sfx_assemble_weighted_cell_matrices")
+    return A
 
 
 def sfx_assemble_linearised_action(ctx, form, space, u, du, y, nrhs=None, accumulate=False, precision="fp64",

@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(kMatThreads) k_cell_matrices(const MatArgs a, 
   double* T2 = T1 + kMaxTerm * Q2;                   // up to 4 x Q x 81
   double* X = T2 + 4 * Q * kMaxN * kMaxN;            // 24
   double* Jc = X + 24;                               // 3 x Q2 x 3
-  int* bad = reinterpret_cast<int*>(Jc + 9 * Q2);
+  double* KL = Jc + 9 * Q2;                          // kappa's dofs of the cell (weighted Laplace)
+  int* bad = reinterpret_cast<int*>(KL + (a.kappa ? d.nloc : 0));
   const int tid = threadIdx.x;
   const int64_t cell = a.cell_begin + blockIdx.x;
 
@@ -96,6 +97,8 @@ __global__ void __launch_bounds__(kMatThreads) k_cell_matrices(const MatArgs a, 
     X[tid] = a.xyz[(int64_t)a.vmap[cell * 8 + v] * 3 + k];
   }
   if (tid == 0) *bad = 0;
+  if (a.kappa)
+    for (int l = tid; l < d.nloc; l += kMatThreads) KL[l] = a.kappa[a.map[cell * d.nloc + l]];
   __syncthreads();
   // Jacobian column tables (see jacobian_columns): Jc[(col*Q2 + ab)*3 + k]
   for (int i = tid; i < Q2; i += kMatThreads) {
@@ -129,7 +132,16 @@ __global__ void __launch_bounds__(kMatThreads) k_cell_matrices(const MatArgs a, 
     const double* cc[3] = {c0, c1, c2};
     const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
     if (d.kind == CF_SCALAR) {
-      const double ws = a.alpha * w / S;  // alpha = 1 for Laplace, 0 for mass
+      double kap = 1.0;  // weighted Laplace: kappa(xi_q) = sum_l kappa_l psi_l(xi_q)
+      if (a.kappa) {
+        const int tk = a.kappa_dq ? TB_ID : TB_BC;
+        kap = 0.0;
+        for (int l = 0; l < d.nloc; ++l) {
+          const int i1 = l / Q2, i2 = (l / Q) % Q, i3 = l % Q;
+          kap += KL[l] * tab(tb, tk, q1, i1) * tab(tb, tk, q2, i2) * tab(tb, tk, q3, i3);
+        }
+      }
+      const double ws = kap * a.alpha * w / S;  // alpha = 1 for Laplace, 0 for mass
       for (int s = 0; s < 6; ++s) coef[s * Q3 + qp] = ws * dot3(r[pa[s]], r[pb[s]]);
       coef[6 * Q3 + qp] = a.beta * w * S;
     } else if (d.kind == CF_NCF) {
@@ -525,7 +537,7 @@ int launch_cell_matrices(const sfx_space* sp, sfx_form form, sfx_algo algo, cons
   }
   const int Q = sp->p + 1;
   const size_t smem = sizeof(double) * (NTAB * kMaxQ * kMaxN + kMaxCoef * Q * Q * Q + kMaxTerm * Q * Q +
-                                        4 * Q * kMaxN * kMaxN + 24 + 9 * Q * Q) + 16;
+                                        4 * Q * kMaxN * kMaxN + 24 + 9 * Q * Q + (a.kappa ? d.nloc : 0)) + 16;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if (algo == SFX_ALGO_NAIVE) {

@@ -27,7 +27,7 @@
 namespace sfx {
 namespace {
 
-template <int N, int FORM>
+template <int N, int FORM, bool KAP = false>
 struct ScalarShape {
   static constexpr int N2 = N * N, N3 = N * N * N;
   static constexpr bool LAP = FORM != SFX_MASS;
@@ -36,9 +36,10 @@ struct ScalarShape {
   static constexpr int LEAN = N3 + (LAP ? 3 * N3 : 0) + 24 + 9 * N2 + 1;
   // plus the staged factors K[6] (LAP) and WS (MAS) when geo_once
   static constexpr int FULL = LEAN + (LAP ? 6 * N3 : 0) + (MAS ? N3 : 0);
-  static constexpr int TEAM = FULL;
+  static constexpr int TEAM = FULL + (KAP ? N3 : 0);
   static constexpr int MAXCB = (256 / N2) > 0 ? 256 / N2 : 1;
-  static constexpr int team_doubles(bool geo_once) { return geo_once ? FULL : LEAN; }
+  // KAP: the coefficient kappa at the points follows (weighted Laplace)
+  static constexpr int team_doubles(bool geo_once) { return (geo_once ? FULL : LEAN) + (KAP ? N3 : 0); }
 };
 
 // The factors at point qp of a cell: P (6 symmetric entries, scaled by alpha)
@@ -68,10 +69,14 @@ __device__ __forceinline__ double point_factors(const double (*Jc)[N * N][3], co
 // "underintegration" in Sec. 4.1): the points are the nodes, so B = I as for
 // DQ_p, the derivative table is the GLL collocation matrix and the geometry is
 // evaluated at the GLL points with the GLL weights.
-template <int N, bool DQ, int FORM, bool STORED = false, bool COLL = false>
+// KAP: the weighted Laplace form int kappa grad u . grad v (Sec. 1.1, Eq.
+// weighted_laplace): kappa (a.kappa, dofs in the same space) is gathered once
+// per cell, interpolated to the points by the same B contractions, and scales
+// the geometric factor P at each point.
+template <int N, bool DQ, int FORM, bool STORED = false, bool COLL = false, bool KAP = false>
 __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t ncell_total, const int64_t slot0,
                                                  const int cb, double* sm, const bool geo_once) {
-  using Sh = ScalarShape<N, FORM>;
+  using Sh = ScalarShape<N, FORM, KAP>;
   constexpr int N2 = Sh::N2, N3 = Sh::N3;
   constexpr bool LAP = Sh::LAP, MAS = Sh::MAS;
   const Tab1D& T = c_tab[N - 1];
@@ -95,6 +100,7 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
   int* bad = reinterpret_cast<int*>(X0 + 24 + 9 * N2);
   double* K = X0 + 24 + 9 * N2 + 1;                  // K[c][qp] (geo_once only)
   double* WS = K + (LAP ? 6 * N3 : 0);               // WS[qp]   (geo_once only)
+  double* KA = base + Sh::team_doubles(geo_once) - (KAP ? N3 : 0);  // kappa at the points (KAP only)
 
   const double* tw = COLL ? T.wg : T.w;
   const double(*TD)[kMaxQ] = COLL ? T.Dg : T.Dq;  // derivative at the points
@@ -123,6 +129,21 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
   __syncthreads();
   if (!STORED && member) jacobian_columns<N>(X, xq, Jc, t);
   __syncthreads();
+  if (KAP) {
+    const int32_t* krow = a.map ? a.map + (int64_t)cell * N3 : nullptr;
+    const int64_t koff = a.dq_off ? a.dq_off[cell] : 0;
+    for (int l = member ? t : N3; l < N3; l += N2)
+      KA[l] = active ? a.kappa[krow ? (int64_t)krow[l] : koff + l] : 0.0;
+    __syncthreads();
+    if (!DQ && !COLL) {
+      if (member) contract<N, N, N, 0, N, false, false, kMaxN>(KA, KA, T.Bc, t);
+      __syncthreads();
+      if (member) contract<N, N, N, 1, N, false, false, kMaxN>(KA, KA, T.Bc, t);
+      __syncthreads();
+      if (member) contract<N, N, N, 2, N, false, false, kMaxN>(KA, KA, T.Bc, t);
+      __syncthreads();
+    }
+  }
   if (geo_once) {
     // factors at the thread's points qp = k*N2 + t, staged for all RHS
 #pragma unroll 1
@@ -136,8 +157,9 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
         double kk[6], wsm = 0.0;
         const double S = point_factors<N, LAP, MAS>(Jc, W3, qp, alpha, beta, kk, &wsm);
         if (!(S > 0.0)) *bad = 1;
+        const double kap = KAP ? KA[qp] : 1.0;
         if (LAP)
-          for (int j = 0; j < 6; ++j) K[j * N3 + qp] = kk[j];
+          for (int j = 0; j < 6; ++j) K[j * N3 + qp] = KAP ? kap * kk[j] : kk[j];
         if (MAS) WS[qp] = wsm;
       }
     }
@@ -188,7 +210,7 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
         const double S = point_rows<N, LAP>(Jc, qp, r0, r1, r2);
         if (!(S > 0.0)) *bad = 1;
         if (LAP) {
-          const double tw = alpha * W3[qp] * recip_nr<2>(S);
+          const double tw = (KAP ? alpha * W3[qp] * KA[qp] : alpha * W3[qp]) * recip_nr<2>(S);
           const double g0 = G0[qp], g1 = G1[qp], g2 = G2[qp];
           double v[3];
 #pragma unroll

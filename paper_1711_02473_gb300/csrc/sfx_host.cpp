@@ -208,6 +208,7 @@ static int upload_tables(const Tab1D* t) {
   if (!e) e = upload_tab_scalar_coll(t);
   if (!e) e = upload_tab_scalar_mixed_coll(t);
   if (!e) e = upload_tab_elastic_lin(t);
+  if (!e) e = upload_tab_scalar_kappa(t);
   return e;
 }
 
@@ -629,6 +630,69 @@ extern "C" sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, con
   if (sp->family == SFX_Q || sp->family == SFX_DQ) e = launch_action_scalar(sp, form, prec, SFX_ALGO_SUMFACT, a, stream);
   else if (sp->family == SFX_VQ) e = launch_action_elastic(sp, form, prec, a, stream);
   else e = launch_action_hdivcurl(sp, form, prec, a, stream);
+  if (e == -1) return SFX_ERR_UNSUPPORTED;
+  return e ? SFX_ERR_CUDA : SFX_OK;
+}
+
+// Weighted Laplace form int kappa grad u . grad v (Sec. 1.1, Eq. weighted_laplace).
+extern "C" sfx_status sfx_assemble_weighted_action(sfx_ctx* ctx, const sfx_space* sp, const double* kappa,
+                                                   const double* x, double* y, int nrhs, int accumulate,
+                                                   sfx_precision prec, void* stream) {
+  if (!ctx || !sp || !kappa || !x || !y || nrhs < 1 || nrhs > 64 || ctx->device < 0 || !sp->d_map)
+    return SFX_ERR_ARG;
+  if (sp->family != SFX_Q && sp->family != SFX_DQ) return SFX_ERR_ARG;
+  if (y == x || y == kappa) return SFX_ERR_ARG;
+  if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3) return SFX_ERR_ARG;
+  if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!accumulate) {
+    if (cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess) return SFX_ERR_CUDA;
+  }
+  ActArgs a{};
+  a.map = sp->d_map;
+  a.vmap = sp->mesh->d_vmap;
+  a.xyz = sp->mesh->d_xyz;
+  a.x = x;
+  a.kappa = kappa;
+  a.y = y;
+  a.nrhs = nrhs;
+  a.r0 = 0;
+  a.r1 = nrhs;
+  a.alpha = 1.0;
+  a.beta = 0.0;
+  a.status = ctx->d_status;
+  for (int col = 0; col < sp->ncolour; ++col) {
+    a.cells = sp->d_cells + sp->colour_off[col];
+    a.ncells = sp->colour_off[col + 1] - sp->colour_off[col];
+    if (a.ncells == 0) continue;
+    const int e = launch_action_weighted(sp, a, stream);
+    if (e == -1) return SFX_ERR_UNSUPPORTED;
+    if (e) return SFX_ERR_CUDA;
+  }
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_assemble_weighted_cell_matrices(sfx_ctx* ctx, const sfx_space* sp, const double* kappa,
+                                                          int64_t cell_begin, int64_t cell_end, double* A,
+                                                          sfx_precision prec, void* stream) {
+  if (!ctx || !sp || !kappa || !A || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
+  if (sp->family != SFX_Q && sp->family != SFX_DQ) return SFX_ERR_ARG;
+  if (cell_begin < 0 || cell_end > sp->mesh->ncell || cell_begin > cell_end) return SFX_ERR_ARG;
+  if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
+  if (cell_end == cell_begin) return SFX_OK;
+  MatArgs a{};
+  a.vmap = sp->mesh->d_vmap;
+  a.xyz = sp->mesh->d_xyz;
+  a.cell_begin = cell_begin;
+  a.ncells = cell_end - cell_begin;
+  a.A = A;
+  a.alpha = 1.0;
+  a.beta = 0.0;
+  a.map = sp->d_map;
+  a.kappa = kappa;
+  a.kappa_dq = sp->family == SFX_DQ;
+  a.status = ctx->d_status;
+  const int e = launch_cell_matrices(sp, SFX_LAPLACE, SFX_ALGO_SUMFACT, a, stream);
   if (e == -1) return SFX_ERR_UNSUPPORTED;
   return e ? SFX_ERR_CUDA : SFX_OK;
 }

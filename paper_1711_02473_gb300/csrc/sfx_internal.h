@@ -94,6 +94,7 @@ struct ActArgs {
   const double* xyz;      // nvert x 3
   const double* x;        // ndof x nrhs
   const double* xs;       // linearised operators: the state (ndof, one vector)
+  const double* kappa;    // weighted Laplace: the coefficient's dofs (ndof, one vector)
   double* y;              // ndof x nrhs (scatter) or ncells x nloc x nrhs (cell vectors)
   int nrhs;
   int r0, r1;             // right-hand sides handled by this launch: [r0, r1)
@@ -124,6 +125,8 @@ int launch_linearised_elastic(const sfx_space* sp, sfx_form form, const ActArgs&
 // Q_p actions with the collocated GLL rule (B = I): FP64 and TF32x3.
 int launch_action_scalar_coll(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
 int launch_action_scalar_mixed_coll(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+// Weighted Laplace action int kappa grad u . grad v on Q_p / DQ_p (FP64).
+int launch_action_weighted(const sfx_space* sp, const ActArgs& a, void* stream);
 
 struct MatArgs {
   const int32_t* vmap;
@@ -131,6 +134,9 @@ struct MatArgs {
   int64_t cell_begin, ncells;
   double* A;              // ncells x nloc x nloc
   double alpha, beta;
+  const int32_t* map;     // weighted Laplace: the space's cell-node map, and
+  const double* kappa;    // the coefficient's dofs (null: kappa = 1);
+  int kappa_dq;           // 1 if the space is DQ_p (identity value table)
   uint32_t* status;
 };
 int launch_cell_matrices(const sfx_space* sp, sfx_form form, sfx_algo algo, const MatArgs& a, void* stream);
@@ -194,5 +200,6 @@ int upload_tab_qdata(const Tab1D* t);
 int upload_tab_scalar_coll(const Tab1D* t);
 int upload_tab_scalar_mixed_coll(const Tab1D* t);
 int upload_tab_elastic_lin(const Tab1D* t);
+int upload_tab_scalar_kappa(const Tab1D* t);
 
 }  // namespace sfx
