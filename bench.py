@@ -573,20 +573,20 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
     ex["naive_vs_sumfact_Q_laplace_32cube"] = rows
     # --- weighted Laplace int kappa grad u . grad v (Sec. 1.1, Eq. weighted_laplace), FP64, Q_p on 64^3:
     #     the coefficient's interpolation (3 B contractions per cell) beside the plain Laplace action
-    mesh = sfx.Mesh.box(ctx, 64, 64, 64, perturb=0.1, seed=0)
-    rows = []
+    wmesh = sfx.Mesh.box(ctx, 64, 64, 64, perturb=0.1, seed=0)
+    wrows = []
     for p in range(1, 9):
-        sp = sfx.Space(mesh, "Q", p)
+        sp = sfx.Space(wmesh, "Q", p)
         xd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
         kd = 1.0 + 0.5 * torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=7)).cuda()
         yd = torch.empty_like(xd)
         tw = _time(torch, stream, flush, lambda: sfx.sfx_assemble_weighted_action(ctx, sp, kd, xd, yd, stream=stream))
         tl = _time(torch, stream, flush, lambda: sfx.sfx_assemble_action(ctx, "laplace", sp, xd, yd, stream=stream))
-        rows.append({"p": p, "ndof": sp.ndof, "weighted_ms": round(tw, 4), "laplace_ms": round(tl, 4),
+        wrows.append({"p": p, "ndof": sp.ndof, "weighted_ms": round(tw, 4), "laplace_ms": round(tl, 4),
                      "weighted_dofs_per_s": sp.ndof / (tw * 1e-3), "overhead": tw / tl})
         del xd, kd, yd, sp
-    del mesh
-    ex["weighted_laplace_fp64_64cube"] = rows
+    del wmesh
+    ex["weighted_laplace_fp64_64cube"] = wrows
     torch.cuda.empty_cache()
     # --- underintegration (Sec. 4.1): Q_p Laplace on the collocated Gauss-Lobatto rule (B = I) vs the
     #     (p+1)-point Gauss rule; actions on 64^3 (FP64, TF32x3), element matrices on a 32^3 chunk

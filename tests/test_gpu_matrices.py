@@ -47,7 +47,7 @@ def test_scalar_matrices(gpu, orc, fam, form, p):
 
 
 @pytest.mark.parametrize("fam,form", [("NCF", "ncf_mass_divdiv"), ("NCE", "nce_curlcurl")])
-@pytest.mark.parametrize("p", range(1, 7))
+@pytest.mark.parametrize("p", range(1, 9))
 def test_hdivcurl_matrices(gpu, orc, fam, form, p):
     sfx, torch, ctx = gpu
     d = dims_for(p, fam)
