@@ -78,13 +78,14 @@ def fp64_ops_per_cell(fam, p, form):
     (78 per (a, b) entry); per point for the Laplace part the adjugate rows (3
     cross products, 18), det J (3), the weight (1, +1 for Helmholtz), a two-step
     Newton reciprocal (4), the flux t R (R^T g) (21), and for the mass part
-    w S u (3; 12 with det J when alone); the scatter adds one per dof."""
+    w S u (3; 12 with det J when alone).  The scatter's adds run in L2
+    (red.global.add.f64), off the FP64 pipe, and are not counted."""
     n = p + 1
     lap = form != "mass"
     mas = form != "laplace"
     ncontr = (0 if fam == "DQ" else 6) + (6 if lap else 0)
     pt = (47 + (1 if form == "helmholtz" else 0) if lap else 0) + ((3 if lap else 12) if mas else 0)
-    return ncontr * n ** 4 + 78 * n ** 2 + (pt + 1) * n ** 3
+    return ncontr * n ** 4 + 78 * n ** 2 + pt * n ** 3
 
 
 def launches_per_action(fam):
@@ -346,21 +347,22 @@ def mixed_fp64_ops_per_cell(fam, p, form):
     adjugate-row tables per cell -- edge vectors (126), 1D vectors (108 per
     point, 42 for mass alone), 2D tables (22 per (a, b) entry, 10 for mass) --
     then per point the rows (9), det J (3), the weight (1), a one-step Newton
-    reciprocal (2), w/S (1, +1 for Helmholtz) and the scaling of the six
-    factors (6); mass adds w S (2), or 9 with det J when alone.  n <= 3: the
-    Jacobian column tables (78 per entry) and cross products at the point
-    (32 / 13).  The scatter adds one per dof."""
+    reciprocal (2), t = w/S (1, +1 for Helmholtz) and the scaling of R^T g by
+    t (3; the flux R (t R^T g) runs in FP32 otherwise); mass adds w S (2), or
+    9 with det J when alone.  n <= 3: the Jacobian column tables (78 per
+    entry) and cross products at the point (29 / 13).  The scatter's adds
+    run in L2 (red.global.add.f64), off the FP64 pipe, and are not counted."""
     n = p + 1
     lap = form != "mass"
     mas = form != "laplace"
     helm = 1 if form == "helmholtz" else 0
     if n >= 4:
         tables = 126 + (108 if lap else 42) * n + (22 if lap else 10) * n ** 2
-        pt = (22 + helm if lap else 0) + ((2 if lap else 9) if mas else 0)
+        pt = (19 + helm if lap else 0) + ((2 if lap else 9) if mas else 0)
     else:
         tables = 78 * n ** 2
-        pt = (32 + helm if lap else 0) + ((2 if lap else 13) if mas else 0)
-    return tables + (pt + 1) * n ** 3
+        pt = (29 + helm if lap else 0) + ((2 if lap else 13) if mas else 0)
+    return tables + pt * n ** 3
 
 
 def time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, arm, flush, stream, ws, local):

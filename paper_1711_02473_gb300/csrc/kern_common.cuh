@@ -120,6 +120,13 @@ __device__ __forceinline__ double point_rows(const double (*Jc)[N * N][3], int q
   return dot3(c0, r0);
 }
 
+// s > 0 (and finite) decided on the integer bits of s, off the FP64 pipe:
+// positive finite doubles are exactly the bit patterns in (0, 0x7ff0...0).
+__device__ __forceinline__ bool positive_finite(double s) {
+  const long long b = __double_as_longlong(s);
+  return b > 0 && b < 0x7ff0000000000000LL;
+}
+
 // 1/s in FP64 by the Newton-Raphson iteration r <- r + r (1 - s r), seeded
 // with the FP32 approximate reciprocal (PTX rcp.approx, relative error below
 // 2^-22 including the rounding of s to FP32).  Each step squares the relative

@@ -156,7 +156,7 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
       } else {
         double kk[6], wsm = 0.0;
         const double S = point_factors<N, LAP, MAS>(Jc, W3, qp, alpha, beta, kk, &wsm);
-        if (!(S > 0.0)) *bad = 1;
+        if (!positive_finite(S)) *bad = 1;
         const double kap = KAP ? KA[qp] : 1.0;
         if (LAP)
           for (int j = 0; j < 6; ++j) K[j * N3 + qp] = KAP ? kap * kk[j] : kk[j];
@@ -208,7 +208,7 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
         // applied as R (t R^T g) without forming the six entries of P
         double r0[3], r1[3], r2[3];
         const double S = point_rows<N, LAP>(Jc, qp, r0, r1, r2);
-        if (!(S > 0.0)) *bad = 1;
+        if (!positive_finite(S)) *bad = 1;
         if (LAP) {
           const double tw = (KAP ? alpha * W3[qp] * KA[qp] : alpha * W3[qp]) * recip_nr<2>(S);
           const double g0 = G0[qp], g1 = G1[qp], g2 = G2[qp];
@@ -253,7 +253,9 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
       if (a.cell_vectors) {
         for (int l = t; l < N3; l += N2) a.y[(slot * N3 + l) * a.nrhs + r] = U[l];
       } else {
-        for (int l = t; l < N3; l += N2) a.y[dof(l) * a.nrhs + r] += U[l];
+        // reduction in L2 (red.global.add.f64): cells of one launch share no
+        // dof, so each address is added to once per launch, in launch order
+        for (int l = t; l < N3; l += N2) atomicAdd(&a.y[dof(l) * a.nrhs + r], U[l]);
       }
     } else if (active && a.cell_vectors) {
       for (int l = t; l < N3; l += N2) a.y[(slot * N3 + l) * a.nrhs + r] = 0.0;

@@ -96,6 +96,44 @@ __device__ __forceinline__ double mixed_point_factors(const double* tab, const d
   return S;
 }
 
+// Flux at point qp of a cell for one RHS, without forming the factors: the
+// adjugate rows R (FP64, rounded once to FP32), S = det J and t = alpha w / S
+// (FP64, one-step Newton reciprocal) give P g = t R R^T g, applied as R (t R^T g):
+// R^T g and the final R v in FP32, the scaling of the three entries of R^T g
+// by t in FP64.  g (in/out): the reference gradient, replaced by the flux;
+// *u (in/out): the value, scaled by beta w S (mass part).  Returns S.
+template <int N, bool LAP, bool MAS>
+__device__ __forceinline__ double mixed_point_flux(const double* tab, const double* xq, const double* wq, int qp,
+                                                   double alpha, double beta, float* g, float* u) {
+  constexpr int N2 = N * N;
+  constexpr int REC23 = LAP ? 16 : 4;
+  const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
+  double r0[3], r1[3], r2[3], w, S;
+  if (N >= 4) {
+    S = adj_rows<N, REC23, LAP>(tab, tab + N2 * REC23, xq, wq, q1, q2, q3, r0, r1, r2, &w);
+  } else {
+    S = point_rows<N, LAP>(reinterpret_cast<const double(*)[N2][3]>(tab), qp, r0, r1, r2);
+    w = wq[q1] * wq[q2] * wq[q3];
+  }
+  if (LAP) {
+    const double t = (alpha * w) * recip_nr<1>(S);
+    float f0[3], f1[3], f2[3], v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      f0[k] = d2f_int(r0[k]);
+      f1[k] = d2f_int(r1[k]);
+      f2[k] = d2f_int(r2[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = d2f_int(t * f2d_int(fmaf(f0[k], g[0], fmaf(f1[k], g[1], f2[k] * g[2]))));
+    g[0] = fmaf(f0[0], v[0], fmaf(f0[1], v[1], f0[2] * v[2]));
+    g[1] = fmaf(f1[0], v[0], fmaf(f1[1], v[1], f1[2] * v[2]));
+    g[2] = fmaf(f2[0], v[0], fmaf(f2[1], v[1], f2[2] * v[2]));
+  }
+  if (MAS) *u = d2f_int((beta * w) * S) * *u;
+  return S;
+}
+
 // STORED: the FP32 factors come from a.qd32 (sfx_qdata) and no FP64 geometry
 // runs in the kernel.  geo_once: stage the factors once per cell for all RHS.
 // COLL: the collocated Gauss-Lobatto rule on the GLL nodes of Q_p (the points
@@ -199,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
       } else {
         const double S = mixed_point_factors<N, LAP, MAS>(tab_of(c), xq, wq, qp, alpha, beta,
                                                           kk, &wsm);
-        if (!(S > 0.0)) flags[2 * c + 1] = 1;
+        if (!positive_finite(S)) flags[2 * c + 1] = 1;
       }
       if (LAP)
         for (int j = 0; j < 6; ++j) K[(j * cb + c) * N3 + qp] = kk[j];
@@ -246,9 +284,17 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
           if (MAS) wsm = fb * qd[6 * N3 + qp];
         }
       } else {
-        const double S = mixed_point_factors<N, LAP, MAS>(tab_of(c), xq, wq, qp, alpha, beta,
-                                                          kk, &wsm);
-        if (!(S > 0.0)) flags[2 * c + 1] = 1;
+        // factors at the point: flux R (t R^T g) without forming them
+        float g[3] = {LAP ? G0[i] : 0.f, LAP ? G1[i] : 0.f, LAP ? G2[i] : 0.f}, u = U[i];
+        const double S = mixed_point_flux<N, LAP, MAS>(tab_of(c), xq, wq, qp, alpha, beta, g, &u);
+        if (!positive_finite(S)) flags[2 * c + 1] = 1;
+        if (LAP) {
+          G0[i] = g[0];
+          G1[i] = g[1];
+          G2[i] = g[2];
+        }
+        if (MAS) U[i] = u;
+        continue;
       }
       if (LAP) {
         const float g0 = G0[i], g1 = G1[i], g2 = G2[i];
@@ -284,7 +330,10 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
       if (a.cell_vectors) {
         a.y[(slot * N3 + l) * a.nrhs + r] = ok ? f2d_int(U[i]) : 0.0;
       } else if (ok) {
-        a.y[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r] += f2d_int(U[i]);
+        // reduction in L2 (red.global.add.f64), not on the SM's FP64 pipe; cells
+        // of one launch share no dof, so every address is added to once per
+        // launch and the order of the sums is that of the launches
+        atomicAdd(&a.y[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r], f2d_int(U[i]));
       }
     }
     if (r == 0)
