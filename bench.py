@@ -35,8 +35,8 @@ METRIC = "DoFs/s of the operator action (config-2 sweep)"
 # the 32^3, p = 8 Laplace case (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch / 4096 cells); the full-size launch processes 8x the cells, and the traffic
 # of these kernels grows in proportion (x, map, y and coordinates are per cell).
-NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_mixed", "Q", 8): (99.158528e6 + 5.254144e6) / 4096,
-                           ("k_action_scalar_fp64", "Q", 8): (99.228160e6 + 6.336000e6) / 4096}
+NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_mixed", "Q", 8): (94.201856e6 + 4.166144e6) / 4096,
+                           ("k_action_scalar_fp64", "Q", 8): (94.203392e6 + 5.303552e6) / 4096}
 
 
 def parse():
