@@ -23,7 +23,7 @@ int launch(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int64_t grid = (a.ncells + cb - 1) / cb;
-  kern<<<(unsigned)grid, kThreads, smem, s>>>(a, ncell_total, cb, geo_once);
+  kern<<<(unsigned)grid, Sh::NT, smem, s>>>(a, ncell_total, cb, geo_once);
   return (int)cudaGetLastError();
 }
 

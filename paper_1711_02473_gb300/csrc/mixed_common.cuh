@@ -64,8 +64,9 @@ __device__ __forceinline__ int faddr(int c, int f, int k) {
 // fiber of every cell in the CTA (TRANS: M[k][r]).  One warp owns 8 fibers at a
 // time (the n dimension of the mma); in-place use is safe because a warp reads
 // all of its fibers before writing them and no other warp touches them.
-template <int N, int AX, bool TRANS, bool ACC, int PREC>
+template <int N, int AX, bool TRANS, bool ACC, int PREC, int NT = kThreads>
 __device__ __forceinline__ void tc_contract(const float* in, float* out, const TabF& M, int ncell) {
+  constexpr int NW = NT / 32;
   constexpr int N2 = N * N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, tq = lane & 3;
@@ -83,7 +84,7 @@ __device__ __forceinline__ void tc_contract(const float* in, float* out, const T
       split_tf32(A(g, k0 + 4), ah[ks][2], al[ks][2]);
       split_tf32(A(g + 8, k0 + 4), ah[ks][3], al[ks][3]);
     }
-    for (int tile = warp; tile < ntiles; tile += kWarps) {
+    for (int tile = warp; tile < ntiles; tile += NW) {
       const int fb = tile * 8 + g;
       const bool vb = fb < nfib;
       const int cb = vb ? fb / N2 : 0, lb = vb ? fb - cb * N2 : 0;
@@ -126,7 +127,7 @@ __device__ __forceinline__ void tc_contract(const float* in, float* out, const T
         al[q] = pack_bf16(l[2 * q], l[2 * q + 1]);
       }
     }
-    for (int tile = warp; tile < ntiles; tile += kWarps) {
+    for (int tile = warp; tile < ntiles; tile += NW) {
       const int fb = tile * 8 + g;
       const bool vb = fb < nfib;
       const int cb = vb ? fb / N2 : 0, lb = vb ? fb - cb * N2 : 0;

@@ -29,6 +29,11 @@ struct MixedShape {
   static constexpr int N2 = N * N, N3 = N2 * N;
   static constexpr bool LAP = FORM != SFX_MASS;
   static constexpr bool MAS = FORM != SFX_LAPLACE;
+  // threads per CTA, chosen by measurement on the 64^3 sweep: 128 at n = 7
+  // (smaller CTAs, more per SM, so one CTA's FP64 geometry overlaps another's
+  // tensor-core phases: 7-16% faster), 256 elsewhere (128 was 5-12% slower
+  // at n = 8, 9)
+  static constexpr int NT = N == 7 ? 128 : 256;
   // Geometry tables: for N >= 4 the staged adjugate-row tables (see adj_rows;
   // 2D record per (q2,q3): all three rows for the Laplace part, only c0 for
   // mass); for N <= 3, where a cell has at most 27 points and the staged build
@@ -140,10 +145,10 @@ __device__ __forceinline__ double mixed_point_flux(const double* tab, const doub
 // are the nodes: B = I, derivative table = GLL collocation matrix, geometry at
 // the GLL points with the GLL weights; Sec. 2.5 and "underintegration" in 4.1).
 template <int N, bool DQ, int FORM, int PREC, bool STORED, bool COLL = false>
-__global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs a, const int64_t ncell_total,
+__global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed(const ActArgs a, const int64_t ncell_total,
                                                                   const int cb, const bool geo_once) {
   using Sh = MixedShape<N, FORM>;
-  constexpr int N2 = Sh::N2, N3 = Sh::N3;
+  constexpr int N2 = Sh::N2, N3 = Sh::N3, NT = Sh::NT;
   constexpr bool LAP = Sh::LAP, MAS = Sh::MAS;
   const Tab1D& T = c_tab[N - 1];
   extern __shared__ double smd[];
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
   int* flags = reinterpret_cast<int*>(cf + (size_t)cb * Sh::cellf(geo_once));  // per cell: id or -1, bad
 
   const int tid = threadIdx.x;
-  for (int i = tid; i < 16 * 16; i += kThreads) {
+  for (int i = tid; i < 16 * 16; i += NT) {
     const int r = i / 16, k = i % 16;
     tabs[0].v[r][k] = (r < N && k < N) ? (float)T.Bc[r][k] : 0.f;
     tabs[1].v[r][k] = (r < N && k < N) ? (float)(COLL ? T.Dg[r][k] : T.Dq[r][k]) : 0.f;
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
     xq[tid] = COLL ? T.xg[tid] : T.x[tid];
     wq[tid] = COLL ? T.wg[tid] : T.w[tid];
   }
-  for (int c = tid; c < cb; c += kThreads) {
+  for (int c = tid; c < cb; c += NT) {
     int cell = -1;
     if (!slot_cell(a, (int64_t)blockIdx.x * cb + c, ncell_total, &cell)) cell = -1;
     flags[2 * c] = cell;
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
     return cd + (size_t)c * Sh::celld(false) + (Sh::TMP_IN_F ? 0 : Sh::TMPD);
   };
   if (!STORED) {
-    for (int i = tid; i < cb * 24; i += kThreads) {
+    for (int i = tid; i < cb * 24; i += NT) {
       const int c = i / 24, v = (i % 24) / 3, k = i % 3;
       const int cell = flags[2 * c];
       tmp_of(c)[v * 3 + k] =
@@ -197,26 +202,26 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
     }
     __syncthreads();
     if (!Sh::HIER) {
-      for (int i = tid; i < cb * N2; i += kThreads) {
+      for (int i = tid; i < cb * N2; i += NT) {
         const int c = i / N2, t = i - c * N2;
         jacobian_columns<N>(reinterpret_cast<const double(*)[3]>(tmp_of(c)), xq,
                             reinterpret_cast<double(*)[N2][3]>(const_cast<double*>(tab_of(c))), t);
       }
       __syncthreads();
     } else {
-      for (int i = tid; i < cb * kAdjEdge; i += kThreads) {
+      for (int i = tid; i < cb * kAdjEdge; i += NT) {
         const int c = i / kAdjEdge;
         double* X = tmp_of(c);
         adj_edges(reinterpret_cast<const double(*)[3]>(X), X + 24, i - c * kAdjEdge);
       }
       __syncthreads();
-      for (int i = tid; i < cb * 3 * N; i += kThreads) {
+      for (int i = tid; i < cb * 3 * N; i += NT) {
         const int c = i / (3 * N), r = i - c * (3 * N);
         double* X = tmp_of(c);
         adj_1d<LAP>(X + 24, xq, X + 24 + kAdjEdge, r / N, r % N);
       }
       __syncthreads();
-      for (int i = tid; i < cb * N2; i += kThreads) {
+      for (int i = tid; i < cb * N2; i += NT) {
         const int c = i / N2, t = i - c * N2;
         double* R23 = const_cast<double*>(tab_of(c));
         adj_2d<N, Sh::REC23>(tmp_of(c) + 24 + kAdjEdge, xq, wq, R23, R23 + N2 * Sh::REC23, t);
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
     }
   }
   if (geo_once) {
-    for (int i = tid; i < cb * N3; i += kThreads) {
+    for (int i = tid; i < cb * N3; i += NT) {
       const int c = i / N3, qp = i - c * N3;
       const int cell = flags[2 * c];
       float kk[6], wsm = 0.f;
@@ -248,27 +253,27 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
 
 #pragma unroll 1
   for (int r = 0; r < a.nrhs; ++r) {
-    for (int i = tid; i < cb * N3; i += kThreads) {
+    for (int i = tid; i < cb * N3; i += NT) {
       const int c = i / N3, l = i - c * N3;
       const int cell = flags[2 * c];
       U[i] = cell >= 0 ? d2f_int(a.x[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r]) : 0.f;
     }
     __syncthreads();
     if (!DQ && !COLL) {
-      tc_contract<N, 0, false, false, PREC>(U, U, tabs[0], cb);
+      tc_contract<N, 0, false, false, PREC, NT>(U, U, tabs[0], cb);
       __syncthreads();
-      tc_contract<N, 1, false, false, PREC>(U, U, tabs[0], cb);
+      tc_contract<N, 1, false, false, PREC, NT>(U, U, tabs[0], cb);
       __syncthreads();
-      tc_contract<N, 2, false, false, PREC>(U, U, tabs[0], cb);
+      tc_contract<N, 2, false, false, PREC, NT>(U, U, tabs[0], cb);
       __syncthreads();
     }
     if (LAP) {
-      tc_contract<N, 0, false, false, PREC>(U, G0, tabs[1], cb);
-      tc_contract<N, 1, false, false, PREC>(U, G1, tabs[1], cb);
-      tc_contract<N, 2, false, false, PREC>(U, G2, tabs[1], cb);
+      tc_contract<N, 0, false, false, PREC, NT>(U, G0, tabs[1], cb);
+      tc_contract<N, 1, false, false, PREC, NT>(U, G1, tabs[1], cb);
+      tc_contract<N, 2, false, false, PREC, NT>(U, G2, tabs[1], cb);
       __syncthreads();
     }
-    for (int i = tid; i < cb * N3; i += kThreads) {
+    for (int i = tid; i < cb * N3; i += NT) {
       const int c = i / N3, qp = i - c * N3;
       const int cell = flags[2 * c];
       float kk[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, wsm = 0.f;
@@ -306,22 +311,22 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
     }
     __syncthreads();
     if (LAP) {
-      tc_contract<N, 0, true, MAS, PREC>(G0, U, tabs[1], cb);
+      tc_contract<N, 0, true, MAS, PREC, NT>(G0, U, tabs[1], cb);
       __syncthreads();
-      tc_contract<N, 1, true, true, PREC>(G1, U, tabs[1], cb);
+      tc_contract<N, 1, true, true, PREC, NT>(G1, U, tabs[1], cb);
       __syncthreads();
-      tc_contract<N, 2, true, true, PREC>(G2, U, tabs[1], cb);
+      tc_contract<N, 2, true, true, PREC, NT>(G2, U, tabs[1], cb);
       __syncthreads();
     }
     if (!DQ && !COLL) {
-      tc_contract<N, 0, true, false, PREC>(U, U, tabs[0], cb);
+      tc_contract<N, 0, true, false, PREC, NT>(U, U, tabs[0], cb);
       __syncthreads();
-      tc_contract<N, 1, true, false, PREC>(U, U, tabs[0], cb);
+      tc_contract<N, 1, true, false, PREC, NT>(U, U, tabs[0], cb);
       __syncthreads();
-      tc_contract<N, 2, true, false, PREC>(U, U, tabs[0], cb);
+      tc_contract<N, 2, true, false, PREC, NT>(U, U, tabs[0], cb);
       __syncthreads();
     }
-    for (int i = tid; i < cb * N3; i += kThreads) {
+    for (int i = tid; i < cb * N3; i += NT) {
       const int c = i / N3, l = i - c * N3;
       const int cell = flags[2 * c];
       if (cell < 0) continue;
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_action_scalar_mixed(const ActArgs 
       }
     }
     if (r == 0)
-      for (int c = tid; c < cb; c += kThreads)
+      for (int c = tid; c < cb; c += NT)
         if (flags[2 * c] >= 0 && flags[2 * c + 1]) set_flag(a.status, SFX_DEV_INVERTED);
     __syncthreads();
   }
