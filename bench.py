@@ -328,7 +328,9 @@ def main():
                                   "%dx%dx%d perturbed hex mesh, (p+1)^3 Gauss points" % (args.degrees, *dims),
                       "precision": prec, "families": args.families, "degrees": args.degrees,
                       "l2": "flushed between cases (256 MiB write)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
-           "gpu_launches": sum(launches_per_action(f) for f, _, _ in wl) * args.steps * len(precs),
+           # kernel launches of the headline arm's timed steps (one per colour pass: 8 per Q_p action,
+           # 1 per DQ_p action); the other arms are timed in their own regions
+           "gpu_launches": sum(launches_per_action(f) for f, _, _ in wl) * args.steps,
            "clocks": head["clocks"], "roofline": roofline, "per_case": head["per_case"],
            "autotune": ({k: {str(p): v["best"] for p, v in per.items()} for k, per in tuning.items()}
                         if tuning else None),
