@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in cells-per-CTA instead of tuning them first (untimed)")
+    ap.add_argument("--extras-only", default="",
+                    help="comma list of extra workloads (names of the 'extras' keys) to measure alone, without "
+                         "the sweep; prints their JSON")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the measurements of the other configurations (structured elements, "
                          "p-adaptive batching, naive kernels, element matrices)")
@@ -261,6 +264,15 @@ def main():
         dist.init_process_group("nccl")
     sfx.build()
     ctx = sfx.Context(local)
+    if args.extras_only:
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        only = set(args.extras_only.split(","))
+        unknown = only - set(EXTRAS)
+        if unknown:
+            raise SystemExit("unknown extras: %s (known: %s)" % (sorted(unknown), ", ".join(EXTRAS)))
+        print(json.dumps(run_extras(sfx, torch, ctx, inputs, flush, torch.cuda.current_stream(), only=only)),
+              flush=True)
+        return
     dims = tuple(int(v) for v in args.dims.split(","))
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     wl = cases(args)
@@ -508,9 +520,9 @@ def matrix_flops(p, fam):
     return 3 * (9 * n ** 5 + 9 * n ** 6 + 4 * n ** 7)
 
 
-def run_extras(sfx, torch, ctx, inputs, flush, stream):
-    ex = {}
-    # --- structured elements (NCF/NCE on 32^3, p=1..6; neo-Hookean on 48^3, p=2..6)
+def extra_structured(sfx, torch, ctx, inputs, flush, stream):
+    """NCF mass + div-div and NCE curl-curl on 32^3 (p = 1..6), neo-Hookean
+    residual on 48^3 (p = 2..6), FP64."""
     rows = []
     for fam, form, dims, ps in [("NCF", "ncf_mass_divdiv", (32, 32, 32), range(1, 7)),
                                 ("NCE", "nce_curlcurl", (32, 32, 32), range(1, 7)),
@@ -527,11 +539,13 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
                          "ms": round(t, 4), "dofs_per_s": sp.ndof / (t * 1e-3)})
             del xd, yd, sp
         del mesh
-    ex["structured_fp64"] = rows
-    if ctx.sync_status() != 0:
-        ex["structured_status"] = "device status flagged"
-    # --- linearised hyperelastic operator K(u) du (the Jacobian of the residual; the operator whose
-    #     action Sec. 4.1 times), vector Q_p on 48^3, p = 2..6, state = the residual's displacement
+    return {"rows": rows, "device_status": ctx.sync_status()}
+
+
+def extra_linearised(sfx, torch, ctx, inputs, flush, stream):
+    """Linearised hyperelastic operator K(u) du (the Jacobian of the residual;
+    the operator whose action Sec. 4.1 times), vector Q_p on 48^3, p = 2..6,
+    state = the residual's displacement, FP64."""
     rows = []
     dims = (48, 48, 48)
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
@@ -547,15 +561,13 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
                          "ndof": sp.ndof, "ms": round(t, 4), "dofs_per_s": sp.ndof / (t * 1e-3)})
             del ud, dd, yd, sp
     del mesh
-    ex["linearised_hyperelastic_fp64"] = rows
-    if ctx.sync_status() != 0:
-        ex["linearised_status"] = "device status flagged"
-    # --- precision: Laplace (Q_p) and neo-Hookean residual (vector Q_p) on 64^3, p=3..8,
-    #     FP64 vs TF32x3 vs BF16x3 split contractions; error against the FP64 GPU action
-    ex["precision_64cube"] = precision_block(sfx, torch, ctx, inputs, flush, stream)
-    torch.cuda.empty_cache()
-    # --- p-adaptive batching: 200,000 cells (40x50x100), p in 1..8 with P(p) ~ 1/p,
-    #     DQ_p per cell, Laplace + mass on 16 RHS (seeds 0..15)
+    return {"rows": rows, "device_status": ctx.sync_status()}
+
+
+def extra_padaptive(sfx, torch, ctx, inputs, flush, stream):
+    """p-adaptive batching: 200,000 cells (40x50x100), p in 1..8 with
+    P(p) ~ 1/p, DQ_p per cell, Laplace + mass on 16 RHS (seeds 0..15): one
+    graph-captured persistent launch vs one launch per (form, degree, RHS)."""
     dims = (40, 50, 100)
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     deg = inputs.padaptive_degrees(int(np.prod(dims)), 8, seed=2)
@@ -570,7 +582,7 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
     work = plan.ndof * R * len(forms)
     ndeg = len(np.unique(deg))
     fl = sum(dq_multi_ops(int(p), f, R) * int((deg == p).sum()) for p in np.unique(deg) for f in forms)
-    ex["padaptive_batched_fp64"] = {
+    out = {
         "cells": int(np.prod(dims)), "ndof": int(plan.ndof), "nrhs": R, "forms": forms, "tiles": int(plan.ntiles),
         "graph_ms": round(tg, 3), "per_launch_ms": round(tl, 3),
         "graph_dofs_per_s": work / (tg * 1e-3), "per_launch_dofs_per_s": work / (tl * 1e-3),
@@ -578,8 +590,11 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
         "roofline": {"bound": "alu", "achieved": round(fl / (tg * 1e-3) / 1e9, 2), "peak": round(FP64_PEAK_GOPS, 1),
                      "unit": "G FP64 op/s", "frac": round(fl / (tg * 1e-3) / 1e9 / FP64_PEAK_GOPS, 4)}}
     del xd, ys, plan, mesh
-    torch.cuda.empty_cache()
-    # --- naive (un-factorised) vs sum-factorised action, Q_p Laplace, 32^3
+    return out
+
+
+def extra_naive(sfx, torch, ctx, inputs, flush, stream):
+    """Naive (un-factorised) vs sum-factorised action, Q_p Laplace, 32^3."""
     mesh = sfx.Mesh.box(ctx, 32, 32, 32, perturb=0.1, seed=0)
     rows = []
     for p in range(1, 9):
@@ -592,35 +607,32 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
         rows.append({"p": p, "sumfact_ms": round(ts, 4), "naive_ms": round(tn, 4), "speedup": tn / ts,
                      "sumfact_dofs_per_s": sp.ndof / (ts * 1e-3), "naive_dofs_per_s": sp.ndof / (tn * 1e-3)})
         del xd, yd, sp
-    ex["naive_vs_sumfact_Q_laplace_32cube"] = rows
-    # --- weighted Laplace int kappa grad u . grad v (Sec. 1.1, Eq. weighted_laplace), FP64, Q_p on 64^3:
-    #     the coefficient's interpolation (3 B contractions per cell) beside the plain Laplace action
-    wmesh = sfx.Mesh.box(ctx, 64, 64, 64, perturb=0.1, seed=0)
-    wrows = []
+    return rows
+
+
+def extra_weighted(sfx, torch, ctx, inputs, flush, stream):
+    """Weighted Laplace int kappa grad u . grad v (Sec. 1.1, Eq.
+    weighted_laplace), FP64, Q_p on 64^3, beside the plain Laplace action."""
+    mesh = sfx.Mesh.box(ctx, 64, 64, 64, perturb=0.1, seed=0)
+    rows = []
     for p in range(1, 9):
-        sp = sfx.Space(wmesh, "Q", p)
+        sp = sfx.Space(mesh, "Q", p)
         xd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
         kd = 1.0 + 0.5 * torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=7)).cuda()
         yd = torch.empty_like(xd)
         tw = _time(torch, stream, flush, lambda: sfx.sfx_assemble_weighted_action(ctx, sp, kd, xd, yd, stream=stream))
         tl = _time(torch, stream, flush, lambda: sfx.sfx_assemble_action(ctx, "laplace", sp, xd, yd, stream=stream))
-        wrows.append({"p": p, "ndof": sp.ndof, "weighted_ms": round(tw, 4), "laplace_ms": round(tl, 4),
+        rows.append({"p": p, "ndof": sp.ndof, "weighted_ms": round(tw, 4), "laplace_ms": round(tl, 4),
                      "weighted_dofs_per_s": sp.ndof / (tw * 1e-3), "overhead": tw / tl})
         del xd, kd, yd, sp
-    del wmesh
-    ex["weighted_laplace_fp64_64cube"] = wrows
-    torch.cuda.empty_cache()
-    # --- underintegration (Sec. 4.1): Q_p Laplace on the collocated Gauss-Lobatto rule (B = I) vs the
-    #     (p+1)-point Gauss rule; actions on 64^3 (FP64, TF32x3), element matrices on a 32^3 chunk
-    #     (delta-cancelled O(n^5) kernel vs the sum-factorised O(n^7) kernel)
-    ex["underintegration"] = underint_block(sfx, torch, ctx, inputs, flush, stream)
-    torch.cuda.empty_cache()
-    # --- assembled matrix vs matrix-free action (Sec. 4.2's MatVec comparison): Q_p Laplace, p = 1..6,
-    #     meshes sized to keep the CSR below ~6 GB; SpMV, assembly, FP64 and TF32x3 actions on the same mesh
-    ex["matvec_vs_action"] = matvec_block(sfx, torch, ctx, inputs, flush, stream)
-    torch.cuda.empty_cache()
-    # --- element matrices (FP64): Q_p Laplace p=1..8 and NCF/NCE p=1..5 on 32^3,
-    #     on a chunk of cells sized to ~1 GB of output; sum-factorised and, p <= 4, naive
+    return rows
+
+
+def extra_matrices(sfx, torch, ctx, inputs, flush, stream):
+    """Element matrices (FP64): Q_p Laplace p = 1..8 and NCF/NCE p = 1..5 on
+    32^3, on a chunk of cells sized to ~1 GB of output; sum-factorised and,
+    p <= 4, naive."""
+    mesh = sfx.Mesh.box(ctx, 32, 32, 32, perturb=0.1, seed=0)
     rows = []
     for fam, form, ps in [("Q", "laplace", range(1, 9)), ("NCF", "ncf_mass_divdiv", range(1, 6)),
                           ("NCE", "nce_curlcurl", range(1, 6))]:
@@ -645,7 +657,30 @@ def run_extras(sfx, torch, ctx, inputs, flush, stream):
             rows.append(row)
             del A, sp
             torch.cuda.empty_cache()
-    ex["cell_matrices_fp64_32cube"] = rows
+    return rows
+
+
+# the other workloads, by name (in the order the default run measures them)
+EXTRAS = {
+    "structured_fp64": extra_structured,
+    "linearised_hyperelastic_fp64": extra_linearised,
+    "precision_64cube": lambda *a: precision_block(*a),
+    "padaptive_batched_fp64": extra_padaptive,
+    "naive_vs_sumfact_Q_laplace_32cube": extra_naive,
+    "weighted_laplace_fp64_64cube": extra_weighted,
+    "underintegration": lambda *a: underint_block(*a),
+    "matvec_vs_action": lambda *a: matvec_block(*a),
+    "cell_matrices_fp64_32cube": extra_matrices,
+}
+
+
+def run_extras(sfx, torch, ctx, inputs, flush, stream, only=None):
+    ex = {}
+    for name, fn in EXTRAS.items():
+        if only and name not in only:
+            continue
+        ex[name] = fn(sfx, torch, ctx, inputs, flush, stream)
+        torch.cuda.empty_cache()
     ex["note"] = ("extras are measured once per configuration with CUDA events (median of 1-3 runs, L2 "
                   "flushed); DoFs/s follows the paper's N/t; dofs_per_s_paper for matrices scales N by the "
                   "fraction of cells assembled")

@@ -10,8 +10,10 @@
 // colour (cells of one colour share no dof, hence no row), so the sums are
 // conflict-free and run-to-run deterministic.
 //
-// Product y = A x: a group of L lanes per row, each lane striding over the
-// row, then a butterfly reduction inside the group (fixed order).
+// Product y = A x: a group of L lanes per row (4 to 32 by row length: the
+// reduction's FP64 adds cost a full warp slot of the FP64 pipe each, so short
+// rows take few lanes), each lane striding over the row, then a butterfly
+// reduction inside the group (fixed order).
 #include "kern_common.cuh"
 
 namespace sfx {

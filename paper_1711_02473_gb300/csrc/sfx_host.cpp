@@ -872,8 +872,12 @@ extern "C" sfx_status sfx_csr_create(const sfx_space* sp, sfx_csr** out) {
     });
   }
   for (auto& th : pool) th.join();
+  // lanes per row, by measurement: few for short rows, because on this GPU an
+  // FP64 add of a whole warp costs 16 clocks of the SM's FP64 pipe and the
+  // tree reduction over L lanes adds log2(L) of them per row; long rows (Q_5,
+  // Q_6) gain more from the extra loads in flight than the reduction costs
   const double avg = c->nrows ? (double)c->nnz / (double)c->nrows : 0.0;
-  c->lanes = avg < 24 ? 4 : (avg < 48 ? 8 : (avg < 128 ? 16 : 32));
+  c->lanes = avg < 32 ? 4 : (avg < 160 ? 8 : (avg < 400 ? 16 : 32));
   (void)n;
   if (m->ctx->device < 0) {
     *out = c;
