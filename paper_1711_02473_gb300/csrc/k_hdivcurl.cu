@@ -348,7 +348,7 @@ int launch_h(const ActArgs& a, int64_t nc, cudaStream_t s) {
   const size_t per_team = Sh::TEAM * sizeof(double);
   const size_t fixed = (Sh::Q3 + 16) * sizeof(double);
   int cb = Sh::MAXCB;
-  while (cb > 1 && fixed + cb * per_team > 200 * 1024) --cb;
+  while (cb > 1 && fixed + cb * per_team > 110 * 1024) --cb;  // two CTAs per SM
   const size_t smem = fixed + cb * per_team;
   auto kern = k_action_hdivcurl_fp64<P, NCF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
