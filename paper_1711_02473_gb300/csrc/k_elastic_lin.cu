@@ -235,7 +235,9 @@ int launch_l(const ActArgs& a, int64_t nc, cudaStream_t s) {
   const size_t per_team = Sh::TEAM * sizeof(double);
   const size_t fixed = (Sh::N3 + 16) * sizeof(double);
   int cb = Sh::MAXCB;
-  while (cb > 1 && fixed + cb * per_team > 110 * 1024) --cb;  // two CTAs per SM
+  // two CTAs per SM (110 KB each), even at one cell per CTA (measured faster
+  // at Q_6 than one CTA of two cells)
+  while (cb > 1 && fixed + cb * per_team > 110 * 1024) --cb;
   const size_t smem = fixed + cb * per_team;
   auto kern = k_linearised_elastic_fp64<N, NEO>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

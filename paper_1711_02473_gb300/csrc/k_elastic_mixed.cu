@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kThreads) k_residual_elastic_mixed(const ActAr
         if (a.cell_vectors) {
           a.y[(slot * 3 * N3 + comp * N3 + l) * a.nrhs + r] = ok ? f2d_int(H2[i]) : 0.0;
         } else if (ok) {
-          a.y[(int64_t)a.map[(int64_t)cell * 3 * N3 + comp * N3 + l] * a.nrhs + r] += f2d_int(H2[i]);
+          // reduction in L2 (red.global.add.f64): a launch adds to each address once
+          atomicAdd(&a.y[(int64_t)a.map[(int64_t)cell * 3 * N3 + comp * N3 + l] * a.nrhs + r], f2d_int(H2[i]));
         }
       }
     }
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_elastic_mixed(const ActAr
 template <int N, bool NEO, int PREC>
 int launch_em(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   using Sh = EMShape<N>;
-  const size_t budget = 200 * 1024;
+  const size_t budget = 110 * 1024;  // two CTAs per SM
   int cb = tuned_cells_per_cta(SFX_TUNE_ELASTIC_MIXED, N - 1, (N <= 3) ? 32 : 16);
   if (cb < 1) cb = 1;
   while (cb > 1 && Sh::bytes(cb) > budget) --cb;

@@ -348,7 +348,13 @@ int launch_h(const ActArgs& a, int64_t nc, cudaStream_t s) {
   const size_t per_team = Sh::TEAM * sizeof(double);
   const size_t fixed = (Sh::Q3 + 16) * sizeof(double);
   int cb = Sh::MAXCB;
-  while (cb > 1 && fixed + cb * per_team > 110 * 1024) --cb;  // two CTAs per SM
+  // two CTAs per SM (110 KB each) while that still gives a CTA two or more
+  // cells; otherwise one larger CTA, as for the hyperelastic residual
+  while (cb > 1 && fixed + cb * per_team > 110 * 1024) --cb;
+  if (cb < 2) {
+    cb = Sh::MAXCB;
+    while (cb > 1 && fixed + cb * per_team > 200 * 1024) --cb;
+  }
   const size_t smem = fixed + cb * per_team;
   auto kern = k_action_hdivcurl_fp64<P, NCF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
