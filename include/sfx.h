@@ -309,7 +309,8 @@ sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_for
 /* ------------------------------------------------------------------ tuning */
 
 /* Cells per CTA of the split-precision and FP64 action kernels, per kernel kind and degree
- * (1..8): 0 restores the built-in choice.  Kinds: 0 = FP64 (capped at the
+ * (1..8): 0 restores the built-in choice (for kinds 0-2 a table of the
+ * autotuner's GB300 results; for kind 3 16 cells, 32 at p <= 2).  Kinds: 0 = FP64 (capped at the
  * 256-thread team limit, 256 / (p+1)^2), 1 = split precision with on-the-fly
  * geometry, 2 = split precision with stored factors, 3 = split-precision
  * hyperelastic residual (vector Q_p).  Every kernel reduces

@@ -228,11 +228,22 @@ int upload_all_tables() {
 // ------------------------------------------------------------------- tuning
 namespace {
 int g_tune[SFX_TUNE_NKERNEL][kMaxDeg + 1] = {{0}};
+// Built-in cells per CTA by degree 1..8: the autotuner's choice on GB300
+// (Q_p Laplace, 32^3 tuning mesh), the same in repeated tunings up to one
+// entry.  0 = the launcher's own default.
+constexpr int kBuiltinCells[SFX_TUNE_NKERNEL][kMaxDeg + 1] = {
+    {0, 16, 7, 2, 10, 7, 5, 4, 3},  // FP64
+    {0, 8, 6, 8, 4, 4, 2, 2, 2},    // split precision, geometry at the point
+    {0, 8, 6, 6, 6, 3, 3, 3, 3},    // split precision, stored factors
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision hyperelastic residual
+};
 }
 namespace sfx {
 int tuned_cells_per_cta(int kernel, int degree, int fallback) {
-  const int v = (kernel >= 0 && kernel < SFX_TUNE_NKERNEL && degree >= 1 && degree <= kMaxDeg) ? g_tune[kernel][degree] : 0;
-  return v > 0 ? v : fallback;
+  if (kernel < 0 || kernel >= SFX_TUNE_NKERNEL || degree < 1 || degree > kMaxDeg) return fallback;
+  if (g_tune[kernel][degree] > 0) return g_tune[kernel][degree];
+  if (kBuiltinCells[kernel][degree] > 0) return kBuiltinCells[kernel][degree];
+  return fallback;
 }
 }  // namespace sfx
 

@@ -176,7 +176,8 @@ int batched_tile_sizes(int* cb_per_degree /*[kMaxDeg+1]*/);
 int launch_qdata(const sfx_space* sp, sfx_qdata* q, uint32_t* status, void* stream);
 
 // Cells per CTA of the action kernels: the autotuner's choice per (kernel,
-// degree), 0 = not tuned (the launcher's default).  Host-side table.
+// degree) if one was set, else a built-in measured table, else the launcher's
+// default.  Host-side tables.
 enum {
   SFX_TUNE_SCALAR_FP64 = 0,
   SFX_TUNE_SCALAR_MIXED = 1,
