@@ -63,6 +63,7 @@ def lib():
         L.orc_cell_matrices_rule.argtypes = [i, i, i, i, i, P, i, i, i, P, i64, i64, P, i]
         L.orc_linearised_cell_vectors.argtypes = [i, i, i, P, i, i, i, P, P, P, i, P, i64, P, i]
         L.orc_linearised_action.argtypes = [i, i, i, P, i, i, i, P, P, P, P, i, i]
+        L.orc_linearised_cell_matrices.argtypes = [i, i, i, P, i, i, i, P, P, i64, i64, P, i]
         L.orc_weighted_cell_vectors.argtypes = [i, i, i, i, i, i, P, P, P, i, P, i64, P, i]
         L.orc_weighted_action.argtypes = [i, i, i, i, i, i, P, P, P, P, i, i]
         L.orc_weighted_cell_matrices.argtypes = [i, i, i, i, i, i, P, P, i64, i64, P, i]
@@ -228,6 +229,22 @@ def linearised_cell_vectors(form, p, dims, coords, u, du, cells, nq=None, params
                                              _p(du), nrhs, _p(cells), len(cells), _p(b), nthreads),
            "linearised_cell_vectors")
     return b[:, :, 0] if du.ndim == 1 else b
+
+
+def linearised_cell_matrices(form, p, dims, coords, u, cell_begin=0, cell_end=None, nq=None, params=None,
+                             nthreads=0):
+    """Tangent matrices of the hyperelastic residual at the state u (Sec. 4.1),
+    (cells, nloc, nloc), row = test, column = trial."""
+    ndof, nloc = space_size("VQ", p, dims)
+    ncell = dims[0] * dims[1] * dims[2]
+    cell_end = ncell if cell_end is None else cell_end
+    u = _f64(u)
+    assert u.shape == (ndof,)
+    A = np.zeros((cell_end - cell_begin, nloc, nloc))
+    pr = _params(form, params)
+    _check(lib().orc_linearised_cell_matrices(FORMS[form], p, nq or p + 1, _p(pr), *dims, _p(_f64(coords)), _p(u),
+                                              cell_begin, cell_end, _p(A), nthreads), "linearised_cell_matrices")
+    return A
 
 
 def energy(form, p, dims, coords, x, nq=None, params=None):

@@ -1040,6 +1040,78 @@ int orc_linearised_cell_vectors(int form, int p, int nq, const double* params,
   return err;
 }
 
+/* Tangent (element) matrices of the hyperelastic residual at the state u
+ * (Sec. 4.1: the linearised operator whose action the paper times, here
+ * assembled per cell): row (a,i) = test psi_i e_a, column (b,j) = trial
+ * psi_j e_b,
+ *   A^K_((a,i),(b,j)) = sum_q w_q |J| dP(F(u); e_b (x) grad psi_j) : (e_a (x) grad psi_i),
+ * i.e. the cell vector of the linearised operator for each trial basis
+ * function as the direction.  Cells [cell_begin, cell_end), A row-major
+ * (cell, nloc, nloc). */
+int orc_linearised_cell_matrices(int form, int p, int nq, const double* params,
+                                 int nx, int ny, int nz, const double* coords, const double* u,
+                                 int64_t cell_begin, int64_t cell_end, double* A, int nthreads) {
+  elem_t E;
+  if (make_elem(ORC_VQ, p, nx, ny, nz, &E) || !(form == ORC_NEOHOOKE || form == ORC_SVK)) return -1;
+  int64_t ncell = (int64_t)nx * ny * nz;
+  if (cell_begin < 0 || cell_end > ncell || cell_begin > cell_end) return -1;
+  tab_t T;
+  if (tabulate(&E, nq, ORC_GL, &T)) return -1;
+  int nloc = E.nloc;
+  int err = 0;
+  int nt = nthreads_of(nthreads);
+#pragma omp parallel num_threads(nt)
+  {
+    int64_t* dofs = (int64_t*)malloc(sizeof(int64_t) * nloc);
+    double* ul = (double*)malloc(sizeof(double) * nloc);
+    double* gx = (double*)malloc(sizeof(double) * nloc * 3); /* physical gradients of the basis at a point */
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t c = cell_begin; c < cell_end; ++c) {
+      double X[8][3];
+      cell_vertices(nx, ny, nz, coords, c, X);
+      elem_cell_dofs(&E, ny, nz, c, dofs);
+      for (int l = 0; l < nloc; ++l) ul[l] = u[dofs[l]];
+      double* Ac = &A[(size_t)(c - cell_begin) * nloc * nloc];
+      memset(Ac, 0, sizeof(double) * nloc * nloc);
+      for (int q = 0; q < T.nq3; ++q) {
+        double xi[3];
+        qpoint(&T, q, xi);
+        geo_t g;
+        if (geometry(X, xi, &g)) { err = -2; break; }
+        double wS = qweight(&T, q) * g.S;
+        const double* grd = &T.grad[(size_t)q * nloc * 3];
+        for (int l = 0; l < nloc; ++l) /* grad psi_l = G^T grad^ psi_l */
+          for (int bb = 0; bb < 3; ++bb) {
+            double t = 0.0;
+            for (int k = 0; k < 3; ++k) t += grd[l * 3 + k] * g.G[k][bb];
+            gx[l * 3 + bb] = t;
+          }
+        double Hu[3][3] = {{0}};
+        for (int l = 0; l < nloc; ++l)
+          for (int bb = 0; bb < 3; ++bb) Hu[T.comp[l]][bb] += ul[l] * gx[l * 3 + bb];
+        for (int j = 0; j < nloc; ++j) {
+          double dF[3][3] = {{0}}, dP[3][3];
+          for (int bb = 0; bb < 3; ++bb) {
+            if (g_plant == 9) dF[bb][T.comp[j]] = gx[j * 3 + bb]; /* planted: transposed direction */
+            else dF[T.comp[j]][bb] = gx[j * 3 + bb];
+          }
+          if (dpiola(form, params, Hu, dF, dP)) { err = -3; break; }
+          for (int i = 0; i < nloc; ++i) {
+            const int a = T.comp[i];
+            Ac[(size_t)i * nloc + j] += wS * (dP[a][0] * gx[i * 3 + 0] + dP[a][1] * gx[i * 3 + 1] +
+                                              dP[a][2] * gx[i * 3 + 2]);
+          }
+        }
+      }
+    }
+    free(dofs);
+    free(ul);
+    free(gx);
+  }
+  tab_free(&T);
+  return err;
+}
+
 int orc_linearised_action(int form, int p, int nq, const double* params,
                           int nx, int ny, int nz, const double* coords,
                           const double* u, const double* du, double* y, int nrhs, int nthreads) {

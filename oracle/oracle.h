@@ -107,6 +107,11 @@ int orc_linearised_cell_vectors(int form, int p, int nq, const double* params,
 int orc_linearised_action(int form, int p, int nq, const double* params,
                           int nx, int ny, int nz, const double* coords,
                           const double* u, const double* du, double* y, int nrhs, int nthreads);
+/* Tangent matrices of the hyperelastic residual at the state u, cells
+ * [cell_begin, cell_end), row = test (a,i), column = trial (b,j). */
+int orc_linearised_cell_matrices(int form, int p, int nq, const double* params,
+                                 int nx, int ny, int nz, const double* coords, const double* u,
+                                 int64_t cell_begin, int64_t cell_end, double* A, int nthreads);
 /* Hyperelastic stored energy W(u) (NEOHOOKE or SVK), summed over cells. */
 int orc_energy(int form, int p, int nq, const double* params,
                int nx, int ny, int nz, const double* coords,

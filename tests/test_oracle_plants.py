@@ -89,6 +89,24 @@ def linearisation_ok(orc):
     return np.abs(k - fd).max() <= 1e-7 * np.abs(k).max()
 
 
+def tangent_ok(orc):
+    p, d = 1, (2, 1, 2)
+    X = inputs.box_coords(*d, perturb=0.1, seed=4)
+    ndof, nloc = orc.space_size("VQ", p, d)
+    u = 0.03 * inputs.random_vector(ndof, 1, seed=9)
+    cell = 1
+    A = orc.linearised_cell_matrices("svk", p, d, X, u, cell, cell + 1)[0]
+    cmap = orc.cell_map("VQ", p, d)
+    e = 1e-5
+    fd = np.zeros((nloc, nloc))
+    for j in range(nloc):
+        v = np.zeros(ndof)
+        v[cmap[cell][j]] = e
+        fd[:, j] = (orc.cell_vectors("VQ", "svk", p, d, X, u + v, [cell])[0]
+                    - orc.cell_vectors("VQ", "svk", p, d, X, u - v, [cell])[0]) / (2 * e)
+    return np.abs(A - fd).max() <= 1e-7 * np.abs(A).max()
+
+
 PLANTS = {
     1: ("G used where G^T belongs", patch_ok),
     2: ("|J| dropped from the scalar forms", moments_ok),
@@ -98,6 +116,7 @@ PLANTS = {
     6: ("a term dropped from the Lagrange derivative", lagrange_ok),
     7: ("1/|J| dropped from the contravariant Piola map", piola_scale_ok),
     8: ("lambda ln J dropped from the neo-Hookean linearisation", linearisation_ok),
+    9: ("trial direction transposed in the tangent matrix", tangent_ok),
 }
 
 
