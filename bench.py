@@ -32,11 +32,13 @@ L2_FLUSH_BYTES = 256 << 20
 HBM_GBS = 6788.3             # GB300 HBM bandwidth, measured by a STREAM-style copy (GB/s)
 METRIC = "DoFs/s of the operator action (config-2 sweep)"
 # DRAM bytes (read + write) per cell of one colour launch, from the ncu captures of
-# the 32^3, p = 8 Laplace case (dram__bytes_read.sum + dram__bytes_write.sum of one
-# launch / 4096 cells); the full-size launch processes 8x the cells, and the traffic
-# of these kernels grows in proportion (x, map, y and coordinates are per cell).
-NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_mixed", "Q", 8): (94.201856e6 + 4.166144e6) / 4096,
-                           ("k_action_scalar_fp64", "Q", 8): (94.203392e6 + 5.303552e6) / 4096}
+# the 32^3, p = 8 cases (dram__bytes_read.sum + dram__bytes_write.sum of one launch /
+# 4096 cells), keyed by kernel, family, degree and form; the full-size launch processes
+# 8x the cells, and the traffic of these kernels grows in proportion (x, map, y and
+# coordinates are per cell).
+NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_mixed", "Q", 8, "laplace"): (94.201856e6 + 4.166144e6) / 4096,
+                           ("k_action_scalar_mixed", "Q", 8, "helmholtz"): (94.149376e6 + 3.642880e6) / 4096,
+                           ("k_action_scalar_fp64", "Q", 8, "laplace"): (94.203392e6 + 5.303552e6) / 4096}
 
 
 def parse():
@@ -311,7 +313,7 @@ def main():
     if prec == "fp64":
         ops = fp64_ops_per_cell(fam, p, form) * mesh_cells
         achieved = ops / (dom["ms"] * 1e-3) / 1e9
-        tpc = NCU_DRAM_BYTES_PER_CELL.get(("k_action_scalar_fp64", fam, p))
+        tpc = NCU_DRAM_BYTES_PER_CELL.get(("k_action_scalar_fp64", fam, p, form))
         roofline = {"bound": "alu", "kernel": "k_action_scalar_fp64 %s p=%d %s" % (fam, p, form),
                     "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GOPS, 1), "unit": "G FP64 op/s",
                     "frac": round(achieved / FP64_PEAK_GOPS, 4),
@@ -321,7 +323,7 @@ def main():
     else:
         ops = mixed_fp64_ops_per_cell(fam, p, form) * mesh_cells
         achieved = ops / (dom["ms"] * 1e-3) / 1e9
-        tpc = NCU_DRAM_BYTES_PER_CELL.get(("k_action_scalar_mixed", fam, p)) if ":" not in prec else None
+        tpc = NCU_DRAM_BYTES_PER_CELL.get(("k_action_scalar_mixed", fam, p, form)) if ":" not in prec else None
         roofline = {"bound": "alu", "kernel": "k_action_scalar_mixed %s p=%d %s %s" % (fam, p, form, prec),
                     "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GOPS, 1), "unit": "G FP64 op/s",
                     "frac": round(achieved / FP64_PEAK_GOPS, 4),
