@@ -662,6 +662,32 @@ def extra_matrices(sfx, torch, ctx, inputs, flush, stream):
     return rows
 
 
+def extra_tangent(sfx, torch, ctx, inputs, flush, stream):
+    """Tangent (element) matrices of the hyperelastic residual, vector Q_p on
+    the 48^3 hyperelastic mesh, p = 1..6, both laws, state = the residual's
+    displacement, FP64, on a chunk of cells sized to ~1 GB of output."""
+    dims = (48, 48, 48)
+    mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    rows = []
+    for form in ("svk", "neohooke"):
+        for p in range(1, 7):
+            sp = sfx.Space(mesh, "VQ", p)
+            ud = torch.from_numpy(inputs.displacement(sp.ndof, p, dims[0], seed=1)).cuda()
+            nc = int(min(sp.ncell, max(8, (1 << 30) // (sp.nloc * sp.nloc * 8))))
+            A = torch.empty(nc * sp.nloc * sp.nloc, dtype=torch.float64, device="cuda")
+            t = _time(torch, stream, flush,
+                      lambda: sfx.sfx_assemble_linearised_cell_matrices(ctx, form, sp, ud, 0, nc, A, stream=stream),
+                      reps=2, warm=1)
+            rows.append({"family": "VQ", "form": form + "_tangent", "p": p, "cells": nc, "nloc": sp.nloc,
+                         "ms": round(t, 4), "cells_per_s": nc / (t * 1e-3),
+                         "dofs_per_s_paper": sp.ndof * (nc / sp.ncell) / (t * 1e-3),
+                         "gb_per_s_written": nc * sp.nloc ** 2 * 8 / (t * 1e-3) / 1e9})
+            del A, ud, sp
+            torch.cuda.empty_cache()
+    del mesh
+    return {"rows": rows, "device_status": ctx.sync_status()}
+
+
 # the other workloads, by name (in the order the default run measures them)
 EXTRAS = {
     "structured_fp64": extra_structured,
@@ -673,6 +699,7 @@ EXTRAS = {
     "underintegration": lambda *a: underint_block(*a),
     "matvec_vs_action": lambda *a: matvec_block(*a),
     "cell_matrices_fp64_32cube": extra_matrices,
+    "tangent_matrices_fp64_48cube": extra_tangent,
 }
 
 

@@ -238,6 +238,26 @@ sfx_status sfx_assemble_linearised_cell_vectors(sfx_ctx* ctx, sfx_form form, con
                                                 int nrhs, const int64_t* cells, int64_t ncells, double* b,
                                                 sfx_precision prec, void* stream);
 
+/* Element (tangent) matrices of the same operator at the state u: the
+ * Jacobian of the cell residual, A^K = d b^K / d u_K, for cells
+ * [cell_begin, cell_end) of the mesh:
+ *   A^K_((a,i),(b,j)) = sum_q w_q S dP(F; e_b (x) grad^psi_j G) : (e_a (x) grad^psi_i G),
+ * row = test (a,i), column = trial (b,j), local numbering component-major
+ * (a * (p+1)^3 + i).  Column (b,j) is the per-cell vector of
+ * sfx_assemble_linearised_cell_vectors for the unit local direction e_(b,j)
+ * (bit for bit: same contractions).  Sum-factorised, O(p^7) per cell.
+ *   u  device, ndof doubles (read-only)
+ *   A  device, (cell_end - cell_begin) x nloc x nloc doubles, row-major per
+ *      cell (nloc = 3 (p+1)^3; at p = 8, 38 MB per cell: callers chunk the range).
+ * Cells with det J <= 0 get zero matrices and set SFX_DEV_INVERTED; points
+ * with det F <= 0 (neo-Hookean) contribute zero and set SFX_DEV_DETF.
+ * An empty range is a no-op (A may then be null).  FP64 only.
+ * Errors: SFX_ERR_ARG (null, aliasing, family/form, range),
+ * SFX_ERR_UNSUPPORTED (precision), SFX_ERR_CUDA. */
+sfx_status sfx_assemble_linearised_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
+                                                 const sfx_space* space, const double* u, int64_t cell_begin,
+                                                 int64_t cell_end, double* A, sfx_precision prec, void* stream);
+
 /* Local element matrices A[c][j][i] (row = test j, column = trial i) of the
  * bilinear forms for cells [cell_begin, cell_end) (Sec. 3.2: argument
  * factorisation into P^(k,l) factors and sum factorisation, O(n^7) per cell;

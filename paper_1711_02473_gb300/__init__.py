@@ -35,6 +35,7 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_padaptive_action_noalloc", "sfx_qdata_create", "sfx_qdata_destroy",
            "sfx_assemble_action_stored", "sfx_tune_set_cells_per_cta", "sfx_tune_get_cells_per_cta",
            "sfx_assemble_linearised_action", "sfx_assemble_linearised_cell_vectors",
+           "sfx_assemble_linearised_cell_matrices",
            "sfx_csr_create", "sfx_csr_info", "sfx_csr_assemble", "sfx_csr_spmv", "sfx_csr_destroy",
            "sfx_assemble_weighted_action", "sfx_assemble_weighted_cell_matrices"]
 TUNE_KERNEL = {"fp64": 0, "mixed": 1, "mixed_stored": 2, "elastic_mixed": 3}
@@ -95,6 +96,7 @@ def lib():
         L.sfx_csr_destroy.argtypes = [P]
         L.sfx_csr_destroy.restype = None
         L.sfx_assemble_linearised_cell_vectors.argtypes = [P, i, C.POINTER(_Params), P, P, P, i, P, i64, P, i, P]
+        L.sfx_assemble_linearised_cell_matrices.argtypes = [P, i, C.POINTER(_Params), P, P, i64, i64, P, i, P]
         L.sfx_assemble_cell_vectors.argtypes = [P, i, C.POINTER(_Params), P, P, i, P, i64, P, i, P]
         L.sfx_assemble_cell_matrices.argtypes = [P, i, C.POINTER(_Params), P, i64, i64, P, i, i, P]
         L.sfx_plan_create_padaptive.argtypes = [P, P, P, i, P, P, i, C.POINTER(P)]
@@ -342,6 +344,17 @@ def sfx_assemble_linearised_cell_vectors(ctx, form, space, u, du, cells, b, nrhs
                                                       PRECISION[precision], _stream(stream)),
            "sfx_assemble_linearised_cell_vectors")
     return b
+
+
+def sfx_assemble_linearised_cell_matrices(ctx, form, space, u, cell_begin, cell_end, A, precision="fp64",
+                                          params=None, stream=None):
+    if A.numel() != (cell_end - cell_begin) * space.nloc * space.nloc:
+        raise ValueError("A must hold (cell_end - cell_begin) * nloc * nloc doubles")
+    _check(lib().sfx_assemble_linearised_cell_matrices(ctx.h, FORM[form], _params(params), space.h,
+                                                       _dptr(u, "float64"), cell_begin, cell_end,
+                                                       _dptr(A, "float64"), PRECISION[precision], _stream(stream)),
+           "sfx_assemble_linearised_cell_matrices")
+    return A
 
 
 def sfx_assemble_cell_vectors(ctx, form, space, x, cells, b, nrhs=None, precision="fp64", params=None,

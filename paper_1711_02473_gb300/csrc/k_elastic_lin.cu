@@ -14,6 +14,15 @@
 //   neo-Hookean  dP = mu dF + (mu - lambda ln J) F^{-T} dF^T F^{-T} + lambda tr(F^{-1} dF) F^{-T}
 //   SVK          dP = dF S + F (lambda tr(dE) I + 2 mu dE),  dE = sym(F^T dF)
 // A point with det F <= 0 (neo-Hookean) contributes zero and sets SFX_DEV_DETF.
+//
+// Element (tangent) matrices, a.unit_cols > 0: the directions are the cell's
+// trial basis functions psi_j e_b themselves.  Column (b,j) of A^K is the
+// cell vector above for the unit local direction e_(b,j), formed by the same
+// contractions (a unit vector in place of the gathered dofs), so it equals
+// the action's per-cell vector for that direction bit for bit.  Cost per
+// cell: 3 n^3 directions x O(n^4) contractions = O(n^7), the order of the
+// sum-factorised element matrices (Sec. 3.2); the state's gradient and the
+// geometry are formed once per CTA for its chunk of columns.
 #include "kern_common.cuh"
 
 namespace sfx {
@@ -131,6 +140,26 @@ __device__ __forceinline__ void component_gradient(const Tab1D& T, const double*
   __syncthreads();
 }
 
+// Reference gradient of the unit local direction (component comp, node lj)
+// into H[(comp*3 + k)*N3 + qp]: the contractions of component_gradient on the
+// unit vector.
+template <int N>
+__device__ __forceinline__ void unit_gradient(const Tab1D& T, int lj, int comp, double* U, double* H, int t) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  for (int l = t; l < N3; l += N2) U[l] = l == lj ? 1.0 : 0.0;
+  __syncthreads();
+  contract<N, N, N, 0, N, false, false, kMaxN>(U, U, T.Bc, t);
+  __syncthreads();
+  contract<N, N, N, 1, N, false, false, kMaxN>(U, U, T.Bc, t);
+  __syncthreads();
+  contract<N, N, N, 2, N, false, false, kMaxN>(U, U, T.Bc, t);
+  __syncthreads();
+  contract<N, N, N, 0, N, false, false, kMaxQ>(U, H + (comp * 3 + 0) * N3, T.Dq, t);
+  contract<N, N, N, 1, N, false, false, kMaxQ>(U, H + (comp * 3 + 1) * N3, T.Dq, t);
+  contract<N, N, N, 2, N, false, false, kMaxQ>(U, H + (comp * 3 + 2) * N3, T.Dq, t);
+  __syncthreads();
+}
+
 template <int N, bool NEO>
 __global__ void __launch_bounds__(256) k_linearised_elastic_fp64(const ActArgs a, const int64_t ncell_total) {
   using Sh = LShape<N>;
@@ -181,9 +210,27 @@ __global__ void __launch_bounds__(256) k_linearised_elastic_fp64(const ActArgs a
   // the state's reference gradient, once per cell
   for (int comp = 0; comp < 3; ++comp) component_gradient<N>(T, a.xs, 1, 0, mrow, ok, comp, U, Hs, t);
 
+  // action: the RHS r = 0..nrhs-1; element matrices: this CTA's chunk of
+  // trial columns (the same for every team of the CTA)
+  constexpr int NLOC = 3 * N3;
+  const bool mat = a.unit_cols > 0;
+  const int rb = mat ? (int)blockIdx.y * a.unit_cols : 0;
+  const int re = mat ? min(NLOC, rb + a.unit_cols) : a.nrhs;
 #pragma unroll 1
-  for (int r = 0; r < a.nrhs; ++r) {
-    for (int comp = 0; comp < 3; ++comp) component_gradient<N>(T, a.x, a.nrhs, r, mrow, ok, comp, U, Hd, t);
+  for (int r = rb; r < re; ++r) {
+    if (mat) {
+      const int bc = r / N3;
+      for (int comp = 0; comp < 3; ++comp) {
+        if (comp == bc) {
+          unit_gradient<N>(T, r - bc * N3, comp, U, Hd, t);
+        } else {
+          for (int l = t; l < 3 * N3; l += N2) Hd[comp * 3 * N3 + l] = 0.0;
+        }
+      }
+      __syncthreads();
+    } else {
+      for (int comp = 0; comp < 3; ++comp) component_gradient<N>(T, a.x, a.nrhs, r, mrow, ok, comp, U, Hd, t);
+    }
     for (int qp = t; qp < N3; qp += N2) {
       double R[3][3];
       const double S = point_rows<N, true>(Jc, qp, R[0], R[1], R[2]);
@@ -215,7 +262,10 @@ __global__ void __launch_bounds__(256) k_linearised_elastic_fp64(const ActArgs a
       __syncthreads();
       contract<N, N, N, 2, N, true, false, kMaxN>(U, U, T.Bc, t);
       __syncthreads();
-      if (ok) {
+      if (mat) {
+        if (active)
+          for (int l = t; l < N3; l += N2) a.y[(slot * NLOC + comp * N3 + l) * NLOC + r] = ok ? U[l] : 0.0;
+      } else if (ok) {
         if (a.cell_vectors) {
           for (int l = t; l < N3; l += N2) a.y[(slot * 3 * N3 + comp * N3 + l) * a.nrhs + r] = U[l];
         } else {
@@ -242,7 +292,8 @@ int launch_l(const ActArgs& a, int64_t nc, cudaStream_t s) {
   auto kern = k_linearised_elastic_fp64<N, NEO>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  kern<<<(unsigned)((a.ncells + cb - 1) / cb), cb * Sh::N2, smem, s>>>(a, nc);
+  const unsigned chunks = a.unit_cols > 0 ? (unsigned)((3 * Sh::N3 + a.unit_cols - 1) / a.unit_cols) : 1u;
+  kern<<<dim3((unsigned)((a.ncells + cb - 1) / cb), chunks), cb * Sh::N2, smem, s>>>(a, nc);
   return (int)cudaGetLastError();
 }
 

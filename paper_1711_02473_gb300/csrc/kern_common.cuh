@@ -30,7 +30,7 @@ __device__ __forceinline__ bool slot_cell(const ActArgs& a, int64_t slot, int64_
     *cell = (int)c;
     return true;
   }
-  *cell = (int)slot;
+  *cell = (int)(a.cell0 + slot);
   return true;
 }
 

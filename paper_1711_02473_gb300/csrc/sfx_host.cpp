@@ -772,6 +772,46 @@ extern "C" sfx_status sfx_assemble_linearised_cell_vectors(sfx_ctx* ctx, sfx_for
   return linearised(ctx, form, params, sp, u, du, b, nrhs, 0, cells, ncells, prec, stream);
 }
 
+extern "C" sfx_status sfx_assemble_linearised_cell_matrices(sfx_ctx* ctx, sfx_form form,
+                                                            const sfx_form_params* params, const sfx_space* sp,
+                                                            const double* u, int64_t cell_begin, int64_t cell_end,
+                                                            double* A, sfx_precision prec, void* stream) {
+  if (!ctx || !sp || !u || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
+  if (sp->family != SFX_VQ || (form != SFX_NEOHOOKE && form != SFX_SVK)) return SFX_ERR_ARG;
+  if (cell_begin < 0 || cell_end > sp->mesh->ncell || cell_begin > cell_end) return SFX_ERR_ARG;
+  if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3) return SFX_ERR_ARG;
+  if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
+  if (cell_begin == cell_end) return SFX_OK;  // nothing written: A may be null
+  if (!A || A == u) return SFX_ERR_ARG;
+  const sfx_form_params pr = params ? *params : default_params(form);
+  const int n3 = (sp->p + 1) * (sp->p + 1) * (sp->p + 1);
+  ActArgs a{};
+  a.map = sp->d_map;
+  a.vmap = sp->mesh->d_vmap;
+  a.xyz = sp->mesh->d_xyz;
+  a.xs = u;
+  a.y = A;
+  a.nrhs = 1;
+  a.r0 = 0;
+  a.r1 = 1;
+  a.ncells = cell_end - cell_begin;
+  a.cell0 = cell_begin;
+  // trial columns per CTA: at least three chunks (one per component), more
+  // when few cells are asked for, so that cells x chunks fills the GPU
+  // (>= 16 per SM); at least 8 columns per chunk to amortise the state's
+  // gradient and the geometry, which every chunk forms again.  Each column's
+  // arithmetic is the same whatever the chunking.
+  const int64_t ncells = cell_end - cell_begin;
+  int64_t chunks = std::max<int64_t>(3, (152 * 16 + ncells - 1) / ncells);
+  chunks = std::min<int64_t>(chunks, std::max(3, 3 * n3 / 8));
+  a.unit_cols = (int)((3 * n3 + chunks - 1) / chunks);
+  a.alpha = pr.alpha; a.beta = pr.beta; a.mu = pr.mu; a.lambda = pr.lambda;
+  a.status = ctx->d_status;
+  const int e = launch_linearised_elastic(sp, form, a, stream);
+  if (e == -1) return SFX_ERR_UNSUPPORTED;
+  return e ? SFX_ERR_CUDA : SFX_OK;
+}
+
 extern "C" sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
                                                  const sfx_space* sp, int64_t cell_begin, int64_t cell_end,
                                                  double* A, sfx_precision prec, sfx_algo algo, void* stream) {

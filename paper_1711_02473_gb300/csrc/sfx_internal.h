@@ -102,6 +102,9 @@ struct ActArgs {
   const double* qd64;     // stored geometric factors (FP64), [cell][7][q^3], or null
   const float* qd32;      // stored geometric factors (FP32), [cell][7][q^3], or null
   int cell_vectors;       // 1: write b^K per slot instead of scattering
+  int unit_cols;          // linearised operator only: > 0 selects element matrices, this many
+                          //    trial columns (unit directions) per CTA (blockIdx.y picks the chunk)
+  int64_t cell0;          // no cell list: cell = cell0 + slot
   int stage_factors;      // 1: stage the per-point factors once per cell even for one RHS (the
                           //    arithmetic of the persistent batched kernel, for bitwise comparison)
   double alpha, beta, mu, lambda;
