@@ -469,7 +469,8 @@ static void block_curl(int c, const double* gf, double* out) {
 
 static int form_ok(int family, int form) {
   switch (form) {
-    case ORC_MASS: case ORC_LAPLACE: case ORC_HELMHOLTZ: return family == ORC_Q || family == ORC_DQ;
+    case ORC_MASS: case ORC_LAPLACE: case ORC_HELMHOLTZ:
+      return family == ORC_Q || family == ORC_DQ || family == ORC_VQ;
     case ORC_NCF_MASS_DIVDIV: return family == ORC_NCF;
     case ORC_NCE_CURLCURL: return family == ORC_NCE;
     case ORC_NEOHOOKE: case ORC_SVK: return family == ORC_VQ;
@@ -673,6 +674,31 @@ static int cell_vector(const elem_t* E, const tab_t* T, int form, const double* 
           vh[cc] = val[l];
           push_grad(&g, vh, pv);
           b[l * nrhs + r] += w * (params[1] / g.S * dot3(Jc, Jcl) + params[0] * g.S * dot3(pu, pv));
+        }
+      } else if (form == ORC_MASS || form == ORC_LAPLACE || form == ORC_HELMHOLTZ) {
+        /* vector forms on vector Q_p (Sec. 3.3, Eq. vector_mass_form and its
+         * Laplace analogue): a_lap int grad u : grad v + b_mass int u . v with
+         * the basis psi_l e_comp(l); written with full vectors and 3x3
+         * gradients, so the component delta follows from e_a . e_b */
+        double a_lap, b_mass;
+        scalar_weights(form, params, &a_lap, &b_mass);
+        double u[3] = {0, 0, 0}, gu[3][3] = {{0}}; /* gu[a][.] = physical gradient of u_a */
+        for (int l = 0; l < nloc; ++l) {
+          double c = xl[l * nrhs + r], pg[3];
+          int a = T->comp[l];
+          push_grad(&g, &grd[l * 3], pg);
+          u[a] += c * val[l];
+          for (int k = 0; k < 3; ++k) gu[a][k] += c * pg[k];
+        }
+        for (int l = 0; l < nloc; ++l) {
+          double v[3] = {0, 0, 0}, gv[3][3] = {{0}}, pg[3];
+          int a = T->comp[l];
+          push_grad(&g, &grd[l * 3], pg);
+          v[a] = val[l];
+          for (int k = 0; k < 3; ++k) gv[a][k] = pg[k];
+          double dd = 0.0;
+          for (int i = 0; i < 3; ++i) dd += dot3(gu[i], gv[i]);
+          b[l * nrhs + r] += w * g.S * (a_lap * dd + b_mass * dot3(u, v));
         }
       } else { /* ORC_VQ hyperelastic residual */
         double H[3][3] = {{0}}; /* reference displacement gradient H_ac */
@@ -900,8 +926,8 @@ static int cell_matrices_impl(int family, int form, int p, int nq, int qrule, co
         double cA = 0.0, cB = 0.0; /* weights of the two parts of the form */
         for (int l = 0; l < nloc; ++l) {
           int cc = T.comp[l];
-          if (E.family == ORC_Q || E.family == ORC_DQ) {
-            push_grad(&g, &grd[l * 3], &pv[l * 3]);   /* physical gradient */
+          if (E.family == ORC_Q || E.family == ORC_DQ || E.family == ORC_VQ) {
+            push_grad(&g, &grd[l * 3], &pv[l * 3]);   /* physical gradient (of the component) */
             sv[l] = val[l];
           } else if (E.family == ORC_NCF) {
             double vh[3] = {0, 0, 0};
@@ -930,6 +956,25 @@ static int cell_matrices_impl(int family, int form, int p, int nq, int qrule, co
           for (int j = 0; j < nloc; ++j)
             for (int i = 0; i < nloc; ++i)
               Ac[(size_t)j * nloc + i] += cA * dot3(&pv[i * 3], &pv[j * 3]) + cB * sv[i] * sv[j];
+        } else if (E.family == ORC_VQ) {
+          /* vector forms (Sec. 3.3): basis psi_l e_comp(l); u . v and
+           * grad u : grad v summed over the three components, no delta assumed */
+          double a_lap, b_mass;
+          scalar_weights(form, params, &a_lap, &b_mass);
+          cA = w * g.S * a_lap;
+          cB = w * g.S * b_mass;
+          for (int j = 0; j < nloc; ++j)
+            for (int i = 0; i < nloc; ++i) {
+              double vv = 0.0, gg = 0.0;
+              for (int k = 0; k < 3; ++k) {
+                const double vik = (T.comp[i] == k) ? sv[i] : 0.0;
+                const double vjk = (T.comp[g_plant == 10 ? i : j] == k) ? sv[j] : 0.0; /* 10: planted */
+                vv += vik * vjk;
+                for (int m = 0; m < 3; ++m)
+                  gg += ((T.comp[i] == k) ? pv[i * 3 + m] : 0.0) * ((T.comp[j] == k) ? pv[j * 3 + m] : 0.0);
+              }
+              Ac[(size_t)j * nloc + i] += cA * gg + cB * vv;
+            }
         } else if (E.family == ORC_NCF) {
           double inv = (g_plant == 7) ? 1.0 : 1.0 / g.S;
           cA = w * params[0] * inv;

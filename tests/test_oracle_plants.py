@@ -107,6 +107,20 @@ def tangent_ok(orc):
     return np.abs(A - fd).max() <= 1e-7 * np.abs(A).max()
 
 
+def vector_delta_ok(orc):
+    p, d = 1, (2, 1, 2)
+    X = inputs.box_coords(*d, perturb=0.1, seed=4)
+    A = orc.cell_matrices("VQ", "mass", p, d, X)
+    As = orc.cell_matrices("Q", "mass", p, d, X)
+    n3 = A.shape[1] // 3
+    for a in range(3):
+        for b in range(3):
+            blk = A[:, a * n3:(a + 1) * n3, b * n3:(b + 1) * n3]
+            if (a != b and blk.any()) or (a == b and np.abs(blk - As).max() > 1e-14 * np.abs(As).max()):
+                return False
+    return True
+
+
 PLANTS = {
     1: ("G used where G^T belongs", patch_ok),
     2: ("|J| dropped from the scalar forms", moments_ok),
@@ -117,6 +131,7 @@ PLANTS = {
     7: ("1/|J| dropped from the contravariant Piola map", piola_scale_ok),
     8: ("lambda ln J dropped from the neo-Hookean linearisation", linearisation_ok),
     9: ("trial direction transposed in the tangent matrix", tangent_ok),
+    10: ("test component used for the trial in the vector mass matrix", vector_delta_ok),
 }
 
 
