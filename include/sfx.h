@@ -64,7 +64,11 @@ typedef enum { SFX_Q = 0, SFX_DQ = 1, SFX_NCF = 2, SFX_NCE = 3, SFX_VQ = 4 } sfx
  *   SFX_NEOHOOKE        residual (linear form in v): S P(F) : (grad^v G), F = I + grad^u G,
  *                       P = mu (F - F^{-T}) + lambda ln(det F) F^{-T}
  *   SFX_SVK             residual with P = F (lambda tr(E) I + 2 mu E), E = (F^T F - I)/2
- *                       (Sec. 4.1, Saint Venant-Kirchhoff)                                   */
+ *                       (Sec. 4.1, Saint Venant-Kirchhoff)
+ * On vector Q_p, SFX_MASS / SFX_LAPLACE / SFX_HELMHOLTZ are the vector forms
+ * S u.v and S (grad u G):(grad v G) (Sec. 3.3, Eq. vector_mass_form): the
+ * component delta makes them three copies of the scalar form, one per
+ * component block (actions and element matrices; not the per-cell vectors). */
 typedef enum {
   SFX_MASS = 0,
   SFX_LAPLACE = 1,
@@ -263,8 +267,12 @@ sfx_status sfx_assemble_linearised_cell_matrices(sfx_ctx* ctx, sfx_form form, co
  * factorisation into P^(k,l) factors and sum factorisation, O(n^7) per cell;
  * Sec. 3.5 for the H(div)/H(curl) blocks).  A: device,
  * (cell_end - cell_begin) x nloc x nloc doubles.  algo NAIVE uses the dense
- * tabulation (O(n^9)).  Errors: SFX_ERR_ARG (range, null, residual forms),
- * SFX_ERR_UNSUPPORTED, SFX_ERR_CUDA. */
+ * tabulation (O(n^9)).  Vector Q_p with the vector forms: the scalar block of
+ * each cell (any algo available on Q_p) written to the three diagonal blocks,
+ * the off-diagonal blocks zero (delta cancellation across the assignment,
+ * Sec. 3.3); this path takes a stream-ordered scratch of at most 256 MB.
+ * Errors: SFX_ERR_ARG (range, null, residual forms), SFX_ERR_UNSUPPORTED,
+ * SFX_ERR_ALLOC (vector scratch), SFX_ERR_CUDA. */
 sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
                                       const sfx_space* space, int64_t cell_begin, int64_t cell_end,
                                       double* A, sfx_precision prec, sfx_algo algo, void* stream);

@@ -18,6 +18,7 @@
 // The H(div)/H(curl) forms are the same with one term list per block pair
 // (split Concatenate, Sec. 3.5).  The naive variant evaluates every entry as a
 // sum over all q^3 points (O(n^9)).
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -582,6 +583,28 @@ int launch_cell_matrices_coll(const sfx_space* sp, sfx_form form, const MatArgs&
     case 8: return launch_coll<9>(a, s);
   }
   return -1;
+}
+
+// Vector Q_p element matrices of the vector mass / Laplace / Helmholtz forms
+// (Sec. 3.3): the component delta makes them block diagonal with the scalar
+// matrix in every diagonal block.  One thread per output entry (coalesced
+// writes); HBM-bound.
+__global__ void k_vq_expand(const double* __restrict__ S, int64_t ncells, int n3, double* __restrict__ A) {
+  const int64_t nl = 3 * (int64_t)n3, per = nl * nl, total = ncells * per;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / per, rc = e - c * per;
+    const int64_t row = rc / nl, col = rc - row * nl;
+    const int64_t a = row / n3, b = col / n3;
+    A[e] = a == b ? S[(c * n3 + (row - a * n3)) * n3 + (col - b * n3)] : 0.0;
+  }
+}
+
+int launch_vq_expand(const double* S, int64_t ncells, int n3, double* A, void* stream) {
+  const int64_t total = ncells * 9 * (int64_t)n3 * n3;
+  if (total == 0) return 0;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 32);
+  k_vq_expand<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(S, ncells, n3, A);
+  return (int)cudaGetLastError();
 }
 
 }  // namespace sfx

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -52,7 +53,7 @@ void legendre(int n, double t, double* P, double* dP) {
 bool family_ok(sfx_family f) { return f >= SFX_Q && f <= SFX_VQ; }
 bool form_ok(sfx_family fam, sfx_form form) {
   switch (form) {
-    case SFX_MASS: case SFX_LAPLACE: case SFX_HELMHOLTZ: return fam == SFX_Q || fam == SFX_DQ;
+    case SFX_MASS: case SFX_LAPLACE: case SFX_HELMHOLTZ: return fam == SFX_Q || fam == SFX_DQ || fam == SFX_VQ;
     case SFX_NCF_MASS_DIVDIV: return fam == SFX_NCF;
     case SFX_NCE_CURLCURL: return fam == SFX_NCE;
     case SFX_NEOHOOKE: case SFX_SVK: return fam == SFX_VQ;
@@ -538,8 +539,28 @@ extern "C" sfx_status sfx_space_info(const sfx_space* s, int64_t* ndof, int* nlo
   return SFX_OK;
 }
 
+namespace {
+std::mutex g_scalar_mutex;
+
+bool linear_form(sfx_form f) { return f == SFX_MASS || f == SFX_LAPLACE || f == SFX_HELMHOLTZ; }
+
+// The scalar Q_p space of a vector Q_p space's components, created on first use.
+sfx_status vq_scalar(const sfx_space* sp, const sfx_space** out) {
+  std::lock_guard<std::mutex> lock(g_scalar_mutex);
+  if (!sp->scalar) {
+    sfx_space* s = nullptr;
+    const sfx_status st = sfx_space_create(sp->mesh, SFX_Q, sp->p, &s);
+    if (st) return st;
+    sp->scalar = s;
+  }
+  *out = sp->scalar;
+  return SFX_OK;
+}
+}  // namespace
+
 extern "C" void sfx_space_destroy(sfx_space* s) {
   if (!s) return;
+  if (s->scalar) sfx_space_destroy(s->scalar);
   if (s->d_map) cudaFree(s->d_map);
   if (s->d_cells) cudaFree(s->d_cells);
   if (s->d_naive) cudaFree(s->d_naive);
@@ -573,6 +594,20 @@ extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx
   if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3 ||
       (algo != SFX_ALGO_SUMFACT && algo != SFX_ALGO_NAIVE && algo != SFX_ALGO_COLLOCATED))
     return SFX_ERR_ARG;
+  if (sp->family == SFX_VQ && linear_form(form)) {
+    // vector forms (Sec. 3.3): the component delta leaves one scalar action per
+    // component, on the component's contiguous slice of x and y
+    const sfx_space* S = nullptr;
+    const sfx_status st = vq_scalar(sp, &S);
+    if (st) return st;
+    for (int c = 0; c < 3; ++c) {
+      const int64_t off = (int64_t)c * S->ndof * nrhs;
+      const sfx_status e = sfx_assemble_action(ctx, form, params, S, x + off, y + off, nrhs, accumulate, prec,
+                                               algo, stream);
+      if (e) return e;
+    }
+    return SFX_OK;
+  }
   if (algo == SFX_ALGO_COLLOCATED &&
       (sp->family != SFX_Q || (prec != SFX_PREC_FP64 && prec != SFX_PREC_TF32X3)))
     return SFX_ERR_UNSUPPORTED;
@@ -620,6 +655,7 @@ extern "C" sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, con
   if (ncells > 0 && !cells) return SFX_ERR_ARG;
   if (!form_ok(sp->family, form)) return SFX_ERR_ARG;
   if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3) return SFX_ERR_ARG;
+  if (sp->family == SFX_VQ && linear_form(form)) return SFX_ERR_UNSUPPORTED;
   if (ncells == 0) return SFX_OK;
   sfx_form_params pr = params ? *params : default_params(form);
   ActArgs a{};
@@ -820,8 +856,31 @@ extern "C" sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, co
   if (cell_begin < 0 || cell_end > sp->mesh->ncell || cell_begin > cell_end) return SFX_ERR_ARG;
   if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
   if (algo != SFX_ALGO_SUMFACT && algo != SFX_ALGO_NAIVE && algo != SFX_ALGO_COLLOCATED) return SFX_ERR_ARG;
-  if (algo == SFX_ALGO_COLLOCATED && sp->family != SFX_Q) return SFX_ERR_UNSUPPORTED;
+  if (algo == SFX_ALGO_COLLOCATED && sp->family != SFX_Q && sp->family != SFX_VQ) return SFX_ERR_UNSUPPORTED;
   if (cell_end == cell_begin) return SFX_OK;
+  if (sp->family == SFX_VQ) {
+    // vector forms: delta cancellation across the assignment (Sec. 3.3) -- the
+    // scalar block once per cell, written to the three diagonal blocks of the
+    // cleared matrix.  Scalar blocks go through a stream-ordered scratch of at
+    // most 256 MB, chunk by chunk.
+    const sfx_space* S = nullptr;
+    sfx_status st = vq_scalar(sp, &S);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n3 = S->nloc;
+    const size_t per_cell = (size_t)n3 * n3 * sizeof(double);
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(cell_end - cell_begin, (256 << 20) / per_cell));
+    double* scratch = nullptr;
+    if (cudaMallocAsync((void**)&scratch, (size_t)chunk * per_cell, s) != cudaSuccess) return SFX_ERR_ALLOC;
+    for (int64_t c0 = cell_begin; c0 < cell_end && !st; c0 += chunk) {
+      const int64_t m = std::min(chunk, cell_end - c0);
+      st = sfx_assemble_cell_matrices(ctx, form, params, S, c0, c0 + m, scratch, prec, algo, stream);
+      if (!st && launch_vq_expand(scratch, m, n3, A + (size_t)(c0 - cell_begin) * 9 * n3 * n3, stream))
+        st = SFX_ERR_CUDA;
+    }
+    if (cudaFreeAsync(scratch, s) != cudaSuccess && !st) st = SFX_ERR_CUDA;
+    return st;
+  }
   sfx_form_params pr = params ? *params : default_params(form);
   MatArgs a{};
   a.vmap = sp->mesh->d_vmap;

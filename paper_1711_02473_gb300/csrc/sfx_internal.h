@@ -69,6 +69,10 @@ struct sfx_space {
   std::vector<int64_t> colour_off; // ncolour + 1 offsets into d_cells
   int32_t* d_cells = nullptr;
   sfx::Tab1D tab;                  // 1D tables of degree p
+  // vector Q_p only: the scalar Q_p space of one component (component a's
+  // global dofs are a * scalar->ndof + the scalar numbering), built on first
+  // use by the vector mass / Laplace / Helmholtz forms (delta structure)
+  mutable sfx_space* scalar = nullptr;
 };
 
 // Geometric factors at the quadrature points of every cell, computed once in
@@ -173,6 +177,9 @@ struct BatchArgs {
   int form_id[4];
   int64_t ncell_total;
 };
+// Vector Q_p element matrices of the linear vector forms from the scalar ones:
+// A[c][(a,i)][(b,j)] = (a == b) S[c][i][j], all other entries zero (n3 = (p+1)^3).
+int launch_vq_expand(const double* S, int64_t ncells, int n3, double* A, void* stream);
 int batched_config(int* cb_per_degree /*[kMaxDeg+1]*/, size_t* smem, int* grid);
 int batched_launch(const BatchArgs& b, int grid, size_t smem, void* stream);
 int batched_tile_sizes(int* cb_per_degree /*[kMaxDeg+1]*/);
