@@ -3,9 +3,11 @@ sfx_assemble_linearised_cell_matrices (the Jacobian of the Sec. 4.1 residual,
 assembled per cell), through the C ABI against the oracle.
 
 Bar: per cell max|A - A_ref| / max|A_ref| <= 1e-12 (FP64).  Column (b,j) must
-equal, bit for bit, the GPU per-cell vector of the linearised operator for the
-unit direction at that dof (same contractions), and the assembled matrices must
-reproduce the GPU action.  At 48^3 (the hyperelastic mesh of the structured
+equal the GPU per-cell vector of the linearised operator for the unit direction
+at that dof to rounding (1e-13: the matrix kernel takes the direction's
+gradient from the tabulated derivative and a rank-one dP, the action from
+contractions and the full dP), and the assembled matrices must reproduce the
+GPU action.  At 48^3 (the hyperelastic mesh of the structured
 workload) a range of cells is compared with the oracle."""
 import numpy as np
 import pytest
@@ -47,8 +49,9 @@ def test_tangent_parity(gpu, orc, form, p):
     assert ctx.sync_status() == 0
 
 
+@pytest.mark.parametrize("form", ["neohooke", "svk"])
 @pytest.mark.parametrize("p", [2, 5])
-def test_columns_are_the_cell_vectors_of_unit_directions(gpu, orc, p):
+def test_columns_are_the_cell_vectors_of_unit_directions(gpu, orc, p, form):
     sfx, torch, ctx = gpu
     d = (3, 2, 2)
     mesh = sfx.Mesh.box(ctx, *d, perturb=0.1, seed=0)
@@ -56,16 +59,17 @@ def test_columns_are_the_cell_vectors_of_unit_directions(gpu, orc, p):
     u = torch.from_numpy(inputs.displacement(sp.ndof, p, d[0], seed=1, amplitude=0.1)).cuda()
     cell = 7
     A = torch.empty(sp.nloc * sp.nloc, dtype=torch.float64, device="cuda")
-    sfx.sfx_assemble_linearised_cell_matrices(ctx, "neohooke", sp, u, cell, cell + 1, A)
+    sfx.sfx_assemble_linearised_cell_matrices(ctx, form, sp, u, cell, cell + 1, A)
     A = A.view(sp.nloc, sp.nloc)
     cmap = orc.cell_map("VQ", p, d)
     cells = torch.tensor([cell], dtype=torch.int64, device="cuda")
     b = torch.empty(sp.nloc, dtype=torch.float64, device="cuda")
+    scale = A.abs().max().item()
     for j in sorted({0, 1, sp.nloc // 3, sp.nloc // 2, sp.nloc - 1}):
         du = torch.zeros(sp.ndof, dtype=torch.float64, device="cuda")
         du[int(cmap[cell][j])] = 1.0
-        sfx.sfx_assemble_linearised_cell_vectors(ctx, "neohooke", sp, u, du, cells, b)
-        assert torch.equal(A[:, j], b)
+        sfx.sfx_assemble_linearised_cell_vectors(ctx, form, sp, u, du, cells, b)
+        assert (A[:, j] - b).abs().max().item() <= 1e-13 * scale
 
 
 @pytest.mark.parametrize("form", ["neohooke", "svk"])
