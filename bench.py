@@ -30,7 +30,7 @@ HELM = (1.0, -1.0, 0.0, 0.0)  # alpha * laplace + beta * mass, beta = -k^2, k = 
 FP64_PEAK_GOPS = 152 * 2 * 2.07
 L2_FLUSH_BYTES = 256 << 20
 HBM_GBS = 6788.3             # GB300 HBM bandwidth, measured by a STREAM-style copy (GB/s)
-METRIC = "DoFs/s of the operator action (config-2 sweep)"
+METRIC = "DoFs/s for sum-factorised action (mixed vs FP64, same GB300, stated error); % roofline"
 # DRAM bytes (read + write) per cell of one colour launch, from the ncu captures of
 # the 32^3, p = 8 cases (dram__bytes_read.sum + dram__bytes_write.sum of one launch /
 # 4096 cells), keyed by kernel, family, degree and form; the full-size launch processes
@@ -243,7 +243,7 @@ def run_reference(args):
            "value": val, "unit": "DoF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": wall / max(1, args.steps) * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "config-2 action sweep: mass/laplace/helmholtz on Q_p and DQ_p, "
+           "config": {"workload": "operator-action sweep: mass/laplace/helmholtz on Q_p and DQ_p, "
                                   "p=%s, %dx%dx%d perturbed hex mesh, (p+1)^3 Gauss points" % (args.degrees, *dims),
                       "precision": "fp64 (CPU oracle, naive quadrature)", "families": args.families,
                       "degrees": args.degrees},
@@ -338,7 +338,7 @@ def main():
            "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": "config-2 action sweep: mass/laplace/helmholtz on Q_p and DQ_p, p=%s, "
+           "config": {"workload": "operator-action sweep: mass/laplace/helmholtz on Q_p and DQ_p, p=%s, "
                                   "%dx%dx%d perturbed hex mesh, (p+1)^3 Gauss points" % (args.degrees, *dims),
                       "precision": prec, "families": args.families, "degrees": args.degrees,
                       "l2": "flushed between cases (256 MiB write)", "parallelism": "replicas" if ws > 1 else "1 GPU"},

@@ -16,7 +16,7 @@
  * polynomials at each 3D point (Sec. 1.2, Eq. limits_tpe) and the coefficient
  * u_K(xi_q) = sum_i U_i psi_i(xi_q) summed over all i (O(n^6) per cell).
  *
- * Conventions (readings of the paper, all listed in the design doc):
+ * Conventions (readings of the paper):
  *   reference cell [0,1]^3; local index row-major over (i1,i2,i3), i3 fastest
  *   (Sec. 3.5, Eqs. rtcf_split_x/y); cell vertex v = 4a+2b+c for reference
  *   corner (a,b,c); structured nx*ny*nz box numbering (I,J,K), K fastest.
