@@ -28,6 +28,9 @@ HELM = (1.0, -1.0, 0.0, 0.0)  # alpha * laplace + beta * mass, beta = -k^2, k = 
 # nominal GB300 FP64 pipe: 152 SMs x 2 FP64 operations (add, multiply or FMA) per
 # clock x 2.07 GHz; as flops (FMA = 2) this is the 1.26 TFLOP/s nominal figure
 FP64_PEAK_GOPS = 152 * 2 * 2.07
+# FP64 FMA throughput that a DFMA-only kernel (independent chains, 32 warps per
+# SM) sustained on GB300, G op/s: context for the nominal peak above
+FP64_DFMA_PROBE_GOPS = 500.6
 L2_FLUSH_BYTES = 256 << 20
 HBM_GBS = 6788.3             # GB300 HBM bandwidth, measured by a STREAM-style copy (GB/s)
 METRIC = "DoFs/s for sum-factorised action (mixed vs FP64, same GB300, stated error); % roofline"
@@ -317,6 +320,8 @@ def main():
         roofline = {"bound": "alu", "kernel": "k_action_scalar_fp64 %s p=%d %s" % (fam, p, form),
                     "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GOPS, 1), "unit": "G FP64 op/s",
                     "frac": round(achieved / FP64_PEAK_GOPS, 4),
+                    "dfma_probe_peak": FP64_DFMA_PROBE_GOPS,
+                    "frac_of_dfma_probe": round(achieved / FP64_DFMA_PROBE_GOPS, 4),
                     "traffic": round(tpc * mesh_cells / launches_per_action(fam)) if tpc else None,
                     "note": "algorithmic FP64 operations per action (all colour launches; add, multiply or FMA "
                             "= 1) / event time; peak = 152 SMs x 2 FP64 op/clk x 2.07 GHz, of nominal"}
@@ -327,6 +332,8 @@ def main():
         roofline = {"bound": "alu", "kernel": "k_action_scalar_mixed %s p=%d %s %s" % (fam, p, form, prec),
                     "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GOPS, 1), "unit": "G FP64 op/s",
                     "frac": round(achieved / FP64_PEAK_GOPS, 4),
+                    "dfma_probe_peak": FP64_DFMA_PROBE_GOPS,
+                    "frac_of_dfma_probe": round(achieved / FP64_DFMA_PROBE_GOPS, 4),
                     "traffic": round(tpc * mesh_cells / launches_per_action(fam)) if tpc else None,
                     "note": "binding resource = FP64 pipe (adjugate rows, det J, w/S and the factor scaling per "
                             "point, the FP64 scatter; the contractions run on the tensor cores); achieved = "
