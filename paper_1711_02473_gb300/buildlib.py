@@ -15,7 +15,10 @@ SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsfx.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+# host code: no FMA contraction (gcc contracts a*b+c by default where the ISA has
+# an FMA, as on aarch64), so the mesh coordinates and 1D rules computed on the
+# host are bit-identical on x86 and Arm hosts; device code keeps nvcc's default
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr",
               "-Xptxas", "-O3"] + ARCH
 
 

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kMatThreads) k_cell_matrices(const MatArgs a, 
   }
   double* Ac = a.A + (int64_t)blockIdx.x * d.nloc * d.nloc;
 
-  if (NAIVE) {
+  if constexpr (NAIVE) {
     // every entry as a full sum over the q^3 points: O(n^9) per cell
     for (int bt = 0; bt < d.nblk; ++bt)
       for (int bs = 0; bs < d.nblk; ++bs) {
@@ -191,60 +191,59 @@ __global__ void __launch_bounds__(kMatThreads) k_cell_matrices(const MatArgs a, 
           Ac[(int64_t)(d.off[bt] + it) * d.nloc + d.off[bs] + is] = acc;
         }
       }
-    return;
-  }
-
-  for (int bt = 0; bt < d.nblk; ++bt)
-    for (int bs = 0; bs < d.nblk; ++bs) {
-      const int pr = bt * 3 + bs;
-      const int tb0 = d.pair_begin[pr], tb1 = d.pair_end[pr], nterm = tb1 - tb0, nzg = d.pair_nzg[pr];
-      const int* nt = d.dims[bt];
-      const int* ns = d.dims[bs];
-      for (int i1 = 0; i1 < nt[0]; ++i1)
-        for (int j1 = 0; j1 < ns[0]; ++j1) {
-          // stage 1: T1[term][q2][q3] = sum_q1 X_t[q1][i1] X_s[q1][j1] C(q)
-          for (int e = tid; e < nterm * Q2; e += kMatThreads) {
-            const int tm = e / Q2, q23 = e % Q2;
-            const MatTerm& m = d.term[tb0 + tm];
-            double acc = 0.0;
-            for (int q1 = 0; q1 < Q; ++q1)
-              acc += tab(tb, m.tt[0], q1, i1) * tab(tb, m.ts[0], q1, j1) * coef[m.cid * Q3 + q1 * Q2 + q23];
-            T1[e] = m.sign * acc;
-          }
-          __syncthreads();
-          // stage 2: T2[zg][q3][i2][j2] = sum_{terms in zg} sum_q2 Y_t Y_s T1
-          for (int e = tid; e < nzg * Q * nt[1] * ns[1]; e += kMatThreads) {
-            const int zg = e / (Q * nt[1] * ns[1]);
-            const int q3 = (e / (nt[1] * ns[1])) % Q;
-            const int i2 = (e / ns[1]) % nt[1], j2 = e % ns[1];
-            double acc = 0.0;
-            for (int tm = 0; tm < nterm; ++tm) {
+  } else {
+    for (int bt = 0; bt < d.nblk; ++bt)
+      for (int bs = 0; bs < d.nblk; ++bs) {
+        const int pr = bt * 3 + bs;
+        const int tb0 = d.pair_begin[pr], tb1 = d.pair_end[pr], nterm = tb1 - tb0, nzg = d.pair_nzg[pr];
+        const int* nt = d.dims[bt];
+        const int* ns = d.dims[bs];
+        for (int i1 = 0; i1 < nt[0]; ++i1)
+          for (int j1 = 0; j1 < ns[0]; ++j1) {
+            // stage 1: T1[term][q2][q3] = sum_q1 X_t[q1][i1] X_s[q1][j1] C(q)
+            for (int e = tid; e < nterm * Q2; e += kMatThreads) {
+              const int tm = e / Q2, q23 = e % Q2;
               const MatTerm& m = d.term[tb0 + tm];
-              if (m.zg != zg) continue;
-              for (int q2 = 0; q2 < Q; ++q2)
-                acc += tab(tb, m.tt[1], q2, i2) * tab(tb, m.ts[1], q2, j2) * T1[tm * Q2 + q2 * Q + q3];
+              double acc = 0.0;
+              for (int q1 = 0; q1 < Q; ++q1)
+                acc += tab(tb, m.tt[0], q1, i1) * tab(tb, m.ts[0], q1, j1) * coef[m.cid * Q3 + q1 * Q2 + q23];
+              T1[e] = m.sign * acc;
             }
-            T2[((zg * Q + q3) * kMaxN + i2) * kMaxN + j2] = acc;
-          }
-          __syncthreads();
-          // stage 3: A[(i1,i2,i3),(j1,j2,j3)] = sum_zg sum_q3 Z_t Z_s T2 (j3 fastest: contiguous runs)
-          const int nout = nt[1] * nt[2] * ns[1] * ns[2];
-          for (int e = tid; e < nout; e += kMatThreads) {
-            const int j3 = e % ns[2], j2 = (e / ns[2]) % ns[1];
-            const int i3 = (e / (ns[1] * ns[2])) % nt[2], i2 = e / (ns[1] * ns[2] * nt[2]);
-            double acc = 0.0;
-            for (int zg = 0; zg < nzg; ++zg) {
-              const int zt = d.zg_t[tb0 + zg], zs = d.zg_s[tb0 + zg];
-              for (int q3 = 0; q3 < Q; ++q3)
-                acc += tab(tb, zt, q3, i3) * tab(tb, zs, q3, j3) * T2[((zg * Q + q3) * kMaxN + i2) * kMaxN + j2];
+            __syncthreads();
+            // stage 2: T2[zg][q3][i2][j2] = sum_{terms in zg} sum_q2 Y_t Y_s T1
+            for (int e = tid; e < nzg * Q * nt[1] * ns[1]; e += kMatThreads) {
+              const int zg = e / (Q * nt[1] * ns[1]);
+              const int q3 = (e / (nt[1] * ns[1])) % Q;
+              const int i2 = (e / ns[1]) % nt[1], j2 = e % ns[1];
+              double acc = 0.0;
+              for (int tm = 0; tm < nterm; ++tm) {
+                const MatTerm& m = d.term[tb0 + tm];
+                if (m.zg != zg) continue;
+                for (int q2 = 0; q2 < Q; ++q2)
+                  acc += tab(tb, m.tt[1], q2, i2) * tab(tb, m.ts[1], q2, j2) * T1[tm * Q2 + q2 * Q + q3];
+              }
+              T2[((zg * Q + q3) * kMaxN + i2) * kMaxN + j2] = acc;
             }
-            const int row = d.off[bt] + (i1 * nt[1] + i2) * nt[2] + i3;
-            const int col = d.off[bs] + (j1 * ns[1] + j2) * ns[2] + j3;
-            Ac[(int64_t)row * d.nloc + col] = acc;
+            __syncthreads();
+            // stage 3: A[(i1,i2,i3),(j1,j2,j3)] = sum_zg sum_q3 Z_t Z_s T2 (j3 fastest: contiguous runs)
+            const int nout = nt[1] * nt[2] * ns[1] * ns[2];
+            for (int e = tid; e < nout; e += kMatThreads) {
+              const int j3 = e % ns[2], j2 = (e / ns[2]) % ns[1];
+              const int i3 = (e / (ns[1] * ns[2])) % nt[2], i2 = e / (ns[1] * ns[2] * nt[2]);
+              double acc = 0.0;
+              for (int zg = 0; zg < nzg; ++zg) {
+                const int zt = d.zg_t[tb0 + zg], zs = d.zg_s[tb0 + zg];
+                for (int q3 = 0; q3 < Q; ++q3)
+                  acc += tab(tb, zt, q3, i3) * tab(tb, zs, q3, j3) * T2[((zg * Q + q3) * kMaxN + i2) * kMaxN + j2];
+              }
+              const int row = d.off[bt] + (i1 * nt[1] + i2) * nt[2] + i3;
+              const int col = d.off[bs] + (j1 * ns[1] + j2) * ns[2] + j3;
+              Ac[(int64_t)row * d.nloc + col] = acc;
+            }
+            __syncthreads();
           }
-          __syncthreads();
-        }
-    }
+      }
+  }
 }
 
 // Element matrices of the scalar forms on Q_p with the collocated Gauss-

@@ -16,8 +16,6 @@ using namespace sfx;
 
 namespace {
 
-sfx_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SFX_OK : SFX_ERR_CUDA; }
-
 template <class T>
 sfx_status to_device(const T* h, size_t n, T** d) {
   *d = nullptr;
@@ -312,7 +310,7 @@ extern "C" const char* sfx_status_string(sfx_status s) {
 
 // --------------------------------------------------------------------- mesh
 static sfx_status mesh_finish(sfx_mesh* m) {
-  const int nx = m->nx, ny = m->ny, nz = m->nz;
+  const int ny = m->ny, nz = m->nz;
   std::vector<int32_t> vmap((size_t)m->ncell * 8);
   for (int64_t c = 0; c < m->ncell; ++c) {
     int64_t k = c % nz, j = (c / nz) % ny, i = c / ((int64_t)ny * nz);
