@@ -78,13 +78,19 @@ def apply(table):
             sfx_tune_set_cells_per_cta(kind, int(p), int(rec["best"]))
 
 
+def cache_dir():
+    """Directory of the per-GPU tables: $SFX_AUTOTUNE_CACHE if set, else the
+    package's build directory."""
+    return os.environ.get("SFX_AUTOTUNE_CACHE") or _BUILD
+
+
 def cache_path(gpu_name):
     safe = "".join(c if c.isalnum() else "_" for c in gpu_name)
-    return os.path.join(_BUILD, "autotune_%s.json" % safe)
+    return os.path.join(cache_dir(), "autotune_%s.json" % safe)
 
 
 def save(table, gpu_name):
-    os.makedirs(_BUILD, exist_ok=True)
+    os.makedirs(cache_dir(), exist_ok=True)
     with open(cache_path(gpu_name), "w") as f:
         json.dump({"gpu": gpu_name, "table": table}, f, indent=1)
 
@@ -115,4 +121,5 @@ def ensure(ctx, gpu_name, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_st
     return {k: {p: v for p, v in per.items() if p in degrees} for k, per in table.items() if k in kinds}
 
 
-__all__ = ["tune", "apply", "save", "load", "ensure", "candidates", "TUNE_KERNEL", "Context"]
+__all__ = ["tune", "apply", "save", "load", "ensure", "candidates", "cache_dir", "cache_path", "TUNE_KERNEL",
+           "Context"]

@@ -1,0 +1,30 @@
+"""The autotuner's per-GPU cache on the host: tables round-trip through JSON,
+GPU names map to safe file names, $SFX_AUTOTUNE_CACHE relocates the cache, and
+an absent cache reads as None (the tuner then measures)."""
+from paper_1711_02473_gb300 import autotune
+
+
+def test_cache_round_trip_and_location(tmp_path, monkeypatch):
+    monkeypatch.setenv("SFX_AUTOTUNE_CACHE", str(tmp_path / "tune"))
+    name = "NVIDIA GB300 (x/y)"
+    assert autotune.load(name) is None
+    table = {"mixed": {8: {"best": 2, "ms": {"1": 1.9, "2": 1.8}}}, "fp64": {3: {"best": 4, "ms": {"4": 0.5}}}}
+    autotune.save(table, name)
+    path = autotune.cache_path(name)
+    assert path.startswith(str(tmp_path / "tune"))
+    assert all(c.isalnum() or c in "_." for c in path.rsplit("/", 1)[1])
+    back = autotune.load(name)
+    assert back["mixed"]["8"]["best"] == 2 and back["fp64"]["3"]["ms"]["4"] == 0.5
+
+
+def test_default_location_is_the_build_directory(monkeypatch):
+    monkeypatch.delenv("SFX_AUTOTUNE_CACHE", raising=False)
+    assert autotune.cache_dir().endswith("_build")
+
+
+def test_candidates_are_valid_team_counts():
+    for p in range(1, 9):
+        n2 = (p + 1) ** 2
+        fp = autotune.candidates("fp64", p)
+        assert fp and all(1 <= c <= max(1, 256 // n2) for c in fp)
+        assert all(1 <= c <= 32 for c in autotune.candidates("mixed", p))
