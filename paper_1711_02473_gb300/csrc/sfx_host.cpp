@@ -12,9 +12,20 @@
 
 #include "sfx_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace sfx;
 
 namespace {
+
+// Named range around a library entry point, for profilers and tracers (NVTX;
+// a no-op unless a tool is attached to the process).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 template <class T>
 sfx_status to_device(const T* h, size_t n, T** d) {
@@ -586,6 +597,7 @@ extern "C" sfx_status sfx_tabulate_1d(sfx_nodes nodes, int ndof1d, sfx_nodes qru
 extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
                                           const sfx_space* sp, const double* x, double* y, int nrhs,
                                           int accumulate, sfx_precision prec, sfx_algo algo, void* stream) {
+  Range range("sfx_assemble_action");
   if (!ctx || !sp || !x || !y || nrhs < 1 || nrhs > 64 || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
   if (!form_ok(sp->family, form)) return SFX_ERR_ARG;
   if (x == y) return SFX_ERR_ARG;
@@ -648,6 +660,7 @@ extern "C" sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, con
                                                 const sfx_space* sp, const double* x, int nrhs,
                                                 const int64_t* cells, int64_t ncells, double* b,
                                                 sfx_precision prec, void* stream) {
+  Range range("sfx_assemble_cell_vectors");
   if (!ctx || !sp || !x || !b || nrhs < 1 || nrhs > 64 || ncells < 0 || ctx->device < 0 || !sp->d_map)
     return SFX_ERR_ARG;
   if (ncells > 0 && !cells) return SFX_ERR_ARG;
@@ -683,6 +696,7 @@ extern "C" sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, con
 extern "C" sfx_status sfx_assemble_weighted_action(sfx_ctx* ctx, const sfx_space* sp, const double* kappa,
                                                    const double* x, double* y, int nrhs, int accumulate,
                                                    sfx_precision prec, void* stream) {
+  Range range("sfx_assemble_weighted_action");
   if (!ctx || !sp || !kappa || !x || !y || nrhs < 1 || nrhs > 64 || ctx->device < 0 || !sp->d_map)
     return SFX_ERR_ARG;
   if (sp->family != SFX_Q && sp->family != SFX_DQ) return SFX_ERR_ARG;
@@ -720,6 +734,7 @@ extern "C" sfx_status sfx_assemble_weighted_action(sfx_ctx* ctx, const sfx_space
 extern "C" sfx_status sfx_assemble_weighted_cell_matrices(sfx_ctx* ctx, const sfx_space* sp, const double* kappa,
                                                           int64_t cell_begin, int64_t cell_end, double* A,
                                                           sfx_precision prec, void* stream) {
+  Range range("sfx_assemble_weighted_cell_matrices");
   if (!ctx || !sp || !kappa || !A || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
   if (sp->family != SFX_Q && sp->family != SFX_DQ) return SFX_ERR_ARG;
   if (cell_begin < 0 || cell_end > sp->mesh->ncell || cell_begin > cell_end) return SFX_ERR_ARG;
@@ -793,6 +808,7 @@ extern "C" sfx_status sfx_assemble_linearised_action(sfx_ctx* ctx, sfx_form form
                                                      const sfx_space* sp, const double* u, const double* du,
                                                      double* y, int nrhs, int accumulate, sfx_precision prec,
                                                      void* stream) {
+  Range range("sfx_assemble_linearised_action");
   return linearised(ctx, form, params, sp, u, du, y, nrhs, accumulate, nullptr, 0, prec, stream);
 }
 
@@ -801,6 +817,7 @@ extern "C" sfx_status sfx_assemble_linearised_cell_vectors(sfx_ctx* ctx, sfx_for
                                                            const double* u, const double* du, int nrhs,
                                                            const int64_t* cells, int64_t ncells, double* b,
                                                            sfx_precision prec, void* stream) {
+  Range range("sfx_assemble_linearised_cell_vectors");
   if (ncells > 0 && !cells) return SFX_ERR_ARG;
   if (ncells == 0) return (ctx && sp && u && du && b) ? SFX_OK : SFX_ERR_ARG;
   return linearised(ctx, form, params, sp, u, du, b, nrhs, 0, cells, ncells, prec, stream);
@@ -810,6 +827,7 @@ extern "C" sfx_status sfx_assemble_linearised_cell_matrices(sfx_ctx* ctx, sfx_fo
                                                             const sfx_form_params* params, const sfx_space* sp,
                                                             const double* u, int64_t cell_begin, int64_t cell_end,
                                                             double* A, sfx_precision prec, void* stream) {
+  Range range("sfx_assemble_linearised_cell_matrices");
   if (!ctx || !sp || !u || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
   if (sp->family != SFX_VQ || (form != SFX_NEOHOOKE && form != SFX_SVK)) return SFX_ERR_ARG;
   if (cell_begin < 0 || cell_end > sp->mesh->ncell || cell_begin > cell_end) return SFX_ERR_ARG;
@@ -849,6 +867,7 @@ extern "C" sfx_status sfx_assemble_linearised_cell_matrices(sfx_ctx* ctx, sfx_fo
 extern "C" sfx_status sfx_assemble_cell_matrices(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
                                                  const sfx_space* sp, int64_t cell_begin, int64_t cell_end,
                                                  double* A, sfx_precision prec, sfx_algo algo, void* stream) {
+  Range range("sfx_assemble_cell_matrices");
   if (!ctx || !sp || !A || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
   if (!form_ok(sp->family, form) || form == SFX_NEOHOOKE || form == SFX_SVK) return SFX_ERR_ARG;
   if (cell_begin < 0 || cell_end > sp->mesh->ncell || cell_begin > cell_end) return SFX_ERR_ARG;
@@ -1018,6 +1037,7 @@ extern "C" sfx_status sfx_csr_info(const sfx_csr* c, int64_t* nrows, int64_t* nn
 
 extern "C" sfx_status sfx_csr_assemble(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
                                        const sfx_csr* c, double* values, void* stream) {
+  Range range("sfx_csr_assemble");
   if (!ctx || !c || !values || ctx->device < 0 || !c->d_col) return SFX_ERR_ARG;
   const sfx_space* sp = c->space;
   if (form != SFX_MASS && form != SFX_LAPLACE && form != SFX_HELMHOLTZ) return SFX_ERR_ARG;
@@ -1041,6 +1061,7 @@ extern "C" sfx_status sfx_csr_assemble(sfx_ctx* ctx, sfx_form form, const sfx_fo
 
 extern "C" sfx_status sfx_csr_spmv(sfx_ctx* ctx, const sfx_csr* c, const double* values, const double* x,
                                    double* y, void* stream) {
+  Range range("sfx_csr_spmv");
   if (!ctx || !c || !values || !x || !y || x == y || ctx->device < 0 || !c->d_col) return SFX_ERR_ARG;
   return launch_csr_spmv(c->lanes, c->nrows, c->d_row_ptr, c->d_col, values, x, y, stream) ? SFX_ERR_CUDA : SFX_OK;
 }
@@ -1182,6 +1203,7 @@ static ActArgs plan_args(const sfx_plan* pl, const double* x) {
 
 extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* const* y, sfx_exec_mode mode,
                                        void* stream) {
+  Range range("sfx_plan_execute");
   if (!pl || !x || !y) return SFX_ERR_ARG;
   for (int f = 0; f < pl->nforms; ++f)
     if (!y[f] || y[f] == x) return SFX_ERR_ARG;
@@ -1253,6 +1275,7 @@ extern "C" void sfx_qdata_destroy(sfx_qdata* q) {
 }
 
 extern "C" sfx_status sfx_qdata_create(sfx_ctx* ctx, const sfx_space* sp, int formats, void* stream, sfx_qdata** out) {
+  Range range("sfx_qdata_create");
   if (!ctx || !sp || !out || ctx->device < 0 || !sp->d_map) return SFX_ERR_ARG;
   if ((formats & ~(SFX_QDATA_FP64 | SFX_QDATA_FP32)) || !formats) return SFX_ERR_ARG;
   *out = nullptr;
@@ -1281,6 +1304,7 @@ extern "C" sfx_status sfx_qdata_create(sfx_ctx* ctx, const sfx_space* sp, int fo
 extern "C" sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
                                                  const sfx_space* sp, const sfx_qdata* q, const double* x, double* y,
                                                  int nrhs, int accumulate, sfx_precision prec, void* stream) {
+  Range range("sfx_assemble_action_stored");
   if (!ctx || !sp || !q || !x || !y || x == y || nrhs < 1 || nrhs > 64 || ctx->device < 0 || !sp->d_map)
     return SFX_ERR_ARG;
   if (q->space != sp) return SFX_ERR_ARG;
