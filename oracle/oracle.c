@@ -589,7 +589,8 @@ static int dpiola(int form, const double* params, double Hu[3][3], double dF[3][
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
       dP[a][b] = 0.0;
-      for (int k = 0; k < 3; ++k) dP[a][b] += dF[a][k] * S2[k][b] + F[a][k] * dS[k][b];
+      for (int k = 0; k < 3; ++k)
+        dP[a][b] += (g_plant == 12 ? 0.0 : dF[a][k] * S2[k][b]) + F[a][k] * dS[k][b]; /* 12: planted */
     }
   return 0;
 }
@@ -619,7 +620,7 @@ static int cell_vector(const elem_t* E, const tab_t* T, int form, const double* 
         scalar_weights(form, params, &a_lap, &b_mass);
         if (kap) { /* kappa(xi_q) = sum_l kappa_l psi_l(xi_q) */
           a_lap = 0.0;
-          for (int l = 0; l < nloc; ++l) a_lap += kap[l] * val[l];
+          for (int l = 0; l < nloc; ++l) a_lap += kap[l] * val[g_plant == 11 ? (l + 1) % nloc : l]; /* 11: planted */
           b_mass = 0.0;
         }
         /* coefficient evaluation, Eq. coeff_eval: u and reference gradient */

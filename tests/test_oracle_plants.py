@@ -121,6 +121,28 @@ def vector_delta_ok(orc):
     return True
 
 
+def weighted_energy_ok(orc):
+    p, d = 2, (3, 2, 3)
+    X = inputs.box_coords(*d, perturb=0.1, seed=0)
+    xn = orc.q_node_coords(p, d, X)
+    a, b, c = np.array([0.4, -0.9, 1.3]), 1.7, np.array([0.3, -0.5, 0.8])
+    u = xn @ a
+    y = orc.weighted_action("Q", p, d, X, b + xn @ c, u)
+    return abs(u @ y - (a @ a) * (b + c @ np.array([0.5, 0.5, 0.5]))) <= 1e-12
+
+
+def svk_linearisation_ok(orc):
+    p, d = 1, (2, 1, 2)
+    X = inputs.box_coords(*d, perturb=0.1, seed=4)
+    ndof, _ = orc.space_size("VQ", p, d)
+    u = 0.05 * inputs.random_vector(ndof, 1, seed=9)
+    du = inputs.random_vector(ndof, 1, seed=13)
+    k = orc.linearised_action("svk", p, d, X, u, du)
+    e = 1e-5
+    fd = (orc.action("VQ", "svk", p, d, X, u + e * du) - orc.action("VQ", "svk", p, d, X, u - e * du)) / (2 * e)
+    return np.abs(k - fd).max() <= 1e-7 * np.abs(k).max()
+
+
 PLANTS = {
     1: ("G used where G^T belongs", patch_ok),
     2: ("|J| dropped from the scalar forms", moments_ok),
@@ -132,6 +154,8 @@ PLANTS = {
     8: ("lambda ln J dropped from the neo-Hookean linearisation", linearisation_ok),
     9: ("trial direction transposed in the tangent matrix", tangent_ok),
     10: ("test component used for the trial in the vector mass matrix", vector_delta_ok),
+    11: ("coefficient kappa interpolated with the neighbouring basis function", weighted_energy_ok),
+    12: ("geometric term dF S dropped from the SVK linearisation", svk_linearisation_ok),
 }
 
 
