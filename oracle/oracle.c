@@ -74,7 +74,7 @@ int orc_gauss_legendre(int n, double* x, double* w) {
   if (n < 1 || n > 64) return -1;
   double e[64] = {0}, t[64], P[65];
   /* Jacobi matrix of the monic Legendre recurrence: beta_k = k^2/(4k^2-1). */
-  for (int k = 1; k < n; ++k) e[k - 1] = k / sqrt(4.0 * k * k - 1.0);
+  for (int k = 1; k < n; ++k) e[k - 1] = k / sqrt(4.0 * k * k + (g_plant == 13 ? 1.0 : -1.0)); /* 13: planted */
   tridiag_eigs(n, e, t);
   for (int i = 0; i < n; ++i) {
     /* Christoffel number 1 / sum_k p~_k(t)^2, p~_k = sqrt((2k+1)/2) P_k. */
@@ -245,7 +245,7 @@ static void elem_cell_dofs(const elem_t* E, int ny, int nz, int64_t cell, int64_
           for (int d = 0; d < 3; ++d) {
             /* continuous factor: p nodes advance per cell (shared endpoint);
              * discontinuous factor: cnt nodes per cell. */
-            int64_t step = (B->kind[d] == ORC_GLL) ? (B->cnt[d] - 1) : B->cnt[d];
+            int64_t step = (B->kind[d] == ORC_GLL && g_plant != 14) ? (B->cnt[d] - 1) : B->cnt[d]; /* 14: planted */
             g[d] = step * ci[d] + ii[d];
           }
           dofs[l++] = B->goff + (g[0] * B->gext[1] + g[1]) * B->gext[2] + g[2];

@@ -143,6 +143,21 @@ def svk_linearisation_ok(orc):
     return np.abs(k - fd).max() <= 1e-7 * np.abs(k).max()
 
 
+def gauss_rule_ok(orc):
+    x2, w2 = orc.gauss_legendre(2)
+    x3, w3 = orc.gauss_legendre(3)
+    r = np.sqrt(3.0) / 6.0
+    return (np.abs(np.sort(x2) - [0.5 - r, 0.5 + r]).max() < 1e-15
+            and np.abs(np.sort(w3) - [5 / 18, 5 / 18, 4 / 9]).max() < 1e-15)
+
+
+def q_map_ok(orc):
+    p, d = 2, (3, 2, 3)
+    ndof, _ = orc.space_size("Q", p, d)
+    m = orc.cell_map("Q", p, d)  # integer map only: no value is written through it
+    return int(m.max()) < ndof and len(np.unique(m)) == ndof
+
+
 PLANTS = {
     1: ("G used where G^T belongs", patch_ok),
     2: ("|J| dropped from the scalar forms", moments_ok),
@@ -156,6 +171,8 @@ PLANTS = {
     10: ("test component used for the trial in the vector mass matrix", vector_delta_ok),
     11: ("coefficient kappa interpolated with the neighbouring basis function", weighted_energy_ok),
     12: ("geometric term dF S dropped from the SVK linearisation", svk_linearisation_ok),
+    13: ("wrong off-diagonal of the Gauss-Legendre Jacobi matrix", gauss_rule_ok),
+    14: ("continuous factor advanced by p+1 nodes per cell (no shared dofs)", q_map_ok),
 }
 
 
