@@ -6,8 +6,11 @@ points, input vectors uniform[-1, 1) (seed 1), mesh interior vertices
 perturbed by uniform(+-0.1 h) (seed 0).  Metric: DoFs/s = sum of global DoFs
 of all actions in a step / step time (the paper's N/t, Sec. 4).
 
-Prints ONE JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
-reference arm) on a bounded sample of cells of the same workload instead.
+Output: detail lines first (one JSON object per section, tagged "detail":
+per-case times, the other arms, the sampled error against the oracle, the
+other workloads), then ONE compact headline JSON line, the last line of
+stdout.  ``--impl reference`` times the FP64 CPU oracle (the reference arm)
+on a bounded sample of cells of the same workload instead.
 """
 import argparse
 import json
@@ -65,6 +68,13 @@ def parse():
     ap.add_argument("--extras-only", default="",
                     help="comma list of extra workloads (names of the 'extras' keys) to measure alone, without "
                          "the sweep; prints their JSON")
+    ap.add_argument("--no-oracle-err", action="store_true",
+                    help="skip the sampled per-cell comparison of each arm against the oracle")
+    ap.add_argument("--detail-file", default="",
+                    help="also write the full result (every section) to this JSON file")
+    ap.add_argument("--small-extras", action="store_true",
+                    help="run the other workloads on meshes 1/8 the size per axis, first two degrees each "
+                         "(exercises the full output path quickly)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the measurements of the other configurations (structured elements, "
                          "p-adaptive batching, naive kernels, element matrices)")
@@ -96,8 +106,31 @@ def fp64_ops_per_cell(fam, p, form):
     return ncontr * n ** 4 + 78 * n ** 2 + pt * n ** 3
 
 
+def arm_dtype(arm):
+    """The arithmetic an arm computes in."""
+    prec = arm.split(":")[0]
+    if prec == "fp64":
+        return "f64"
+    return ("%s contractions (split operands, fp32 accumulate); f64 geometry, quadrature scaling and scatter"
+            % prec)
+
+
 def launches_per_action(fam):
     return 1 if fam == "DQ" else 8
+
+
+# --small-extras: the other workloads on meshes 1/8 the size per axis and their
+# first two degrees (a quick run of the full output path; not a measurement)
+SMALL_EXTRAS = False
+
+
+def _d(*dims):
+    return tuple(max(2, v // 8) for v in dims) if SMALL_EXTRAS else tuple(dims)
+
+
+def _ps(seq):
+    seq = list(seq)
+    return seq[:2] if SMALL_EXTRAS else seq
 
 
 class ClockSampler:
@@ -260,6 +293,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     ws, rank, local = dist_setup(args)
+    global SMALL_EXTRAS
+    SMALL_EXTRAS = args.small_extras
     import torch
     import paper_1711_02473_gb300 as sfx
     from paper_1711_02473_gb300 import inputs
@@ -343,7 +378,7 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": "DoF/s",
            "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": arm_dtype(prec),
            "data": "synthetic",
            "config": {"workload": "operator-action sweep: mass/laplace/helmholtz on Q_p and DQ_p, p=%s, "
                                   "%dx%dx%d perturbed hex mesh, (p+1)^3 Gauss points" % (args.degrees, *dims),
@@ -367,6 +402,9 @@ def main():
 
     if not args.no_e2e:
         out["e2e"] = e2e(args, sfx, torch, ctx, spaces, wl, prec, stream)
+    if rank == 0 and not args.no_oracle_err:
+        X = mesh.coords()
+        out["err_vs_oracle"] = oracle_err_sample(sfx, torch, ctx, spaces, xs, wl, precs, dims, X)
     if not args.no_extras and ws == 1:
         del spaces, xs, ys
         torch.cuda.empty_cache()
@@ -377,9 +415,91 @@ def main():
         v, desc, thr = cpu_sample(orc, inputs, wl, dims, X, args.cpu_seconds)
         out["cpu_baseline"] = {"value": v, "unit": "DoF/s", "cores": thr, "kind": "oracle", "sample": desc}
     if rank == 0:
-        print(json.dumps(out), flush=True)
+        emit(out, args.detail_file)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def headline(out):
+    """The compact JSON line printed last (under 2,000 characters): the
+    contract's keys, the headline arm's roofline, the FP64 arm beside it with
+    the speed-up, the measured error against the oracle, the end-to-end rate
+    and the CPU oracle's rate.  Everything else goes on the detail lines."""
+    keep = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "gpu_launches", "clocks")
+    h = {k: out[k] for k in keep if k in out}
+    rf = dict(out["roofline"])
+    rf.pop("note", None)
+    h["roofline"] = rf
+    arms = out.get("arms", {})
+    if "fp64" in arms and out["config"]["precision"] != "fp64":
+        h["fp64_value"] = arms["fp64"]["value"]
+        h["speedup_vs_fp64"] = round(out.get("speedup_vs_fp64", 0.0), 4)
+    ev = out.get("err_vs_oracle")
+    if ev:
+        h["max_rel_err_vs_oracle"] = {arm: ev["max"][arm] for arm in ev["max"]}
+        h["err_sample"] = ev["sample"]
+    if "e2e" in out:
+        h["e2e"] = {k: out["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
+    if "cpu_baseline" in out:
+        cb = dict(out["cpu_baseline"])
+        cb["sample"] = cb["sample"].split(";")[0]
+        h["cpu_baseline"] = cb
+    h["detail"] = "per-case times, the other arms and the other workloads are on the preceding stdout lines"
+    return h
+
+
+def emit(out, detail_file=None):
+    """Detail lines first (one JSON object per section, each tagged
+    "detail"), then the compact headline as the last line of stdout."""
+    sections = {"per_case": out.get("per_case"), "arms": out.get("arms"), "autotune": out.get("autotune"),
+                "err_vs_oracle": out.get("err_vs_oracle"), "roofline_note": out.get("roofline", {}).get("note")}
+    for name, fn in (out.get("extras") or {}).items():
+        sections["extras." + name] = fn
+    for name, val in sections.items():
+        if val is not None:
+            print(json.dumps({"detail": name, "data": val}), flush=True)
+    if detail_file:
+        with open(detail_file, "w") as f:
+            json.dump(out, f)
+    line = json.dumps(headline(out))
+    print(line, flush=True)
+
+
+def oracle_err_sample(sfx, torch, ctx, spaces, xs, wl, precs, dims, X, nsample=8, seed=11):
+    """Normwise relative error of each arm's per-cell vectors b^K against the
+    oracle's, on a seeded sample of cells per case (the first and the last cell
+    of the mesh plus nsample - 2 drawn ones): max |b - b_ref| / max |b_ref|
+    over the sample.  The stored-factor arms apply the same contractions as
+    their plain arm and are not sampled separately."""
+    import oracle as orc
+    ncell = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(seed)
+    arms = [a for a in precs if ":" not in a]
+    rows, mx = [], {a: 0.0 for a in arms}
+    xh = {}
+    for fam, p, form in wl:
+        key = (fam, p)
+        if key not in xh:
+            xh[key] = xs[key].cpu().numpy()
+        cells = np.unique(np.concatenate([[0, ncell - 1], rng.choice(ncell, nsample - 2, replace=False)]))
+        prm = HELM if form == "helmholtz" else None
+        ref = orc.cell_vectors(fam, form, p, dims, X, xh[key], cells, params=prm)
+        cd = torch.from_numpy(cells.astype(np.int64)).cuda()
+        sp = spaces[key]
+        row = {"family": fam, "p": p, "form": form}
+        for a in arms:
+            b = torch.empty(len(cells) * sp.nloc, dtype=torch.float64, device="cuda")
+            sfx.sfx_assemble_cell_vectors(ctx, form, sp, xs[key], cd, b, precision=a, params=prm)
+            e = float(np.abs(b.cpu().numpy().reshape(ref.shape) - ref).max() / np.abs(ref).max())
+            row[a] = e
+            mx[a] = max(mx[a], e)
+        rows.append(row)
+    if ctx.sync_status() != 0:
+        raise RuntimeError("device status flagged while sampling cell vectors")
+    return {"per_case": rows, "max": mx,
+            "sample": "%d cells per case (first, last, %d seeded), per-cell vectors vs the FP64 oracle, "
+                      "max|b-b_ref|/max|b_ref|" % (nsample, nsample - 2)}
 
 
 def mixed_fp64_ops_per_cell(fam, p, form):
@@ -533,9 +653,9 @@ def extra_structured(sfx, torch, ctx, inputs, flush, stream):
     """NCF mass + div-div and NCE curl-curl on 32^3 (p = 1..6), neo-Hookean
     residual on 48^3 (p = 2..6), FP64."""
     rows = []
-    for fam, form, dims, ps in [("NCF", "ncf_mass_divdiv", (32, 32, 32), range(1, 7)),
-                                ("NCE", "nce_curlcurl", (32, 32, 32), range(1, 7)),
-                                ("VQ", "neohooke", (48, 48, 48), range(2, 7))]:
+    for fam, form, dims, ps in [("NCF", "ncf_mass_divdiv", _d(32, 32, 32), _ps(range(1, 7))),
+                                ("NCE", "nce_curlcurl", _d(32, 32, 32), _ps(range(1, 7))),
+                                ("VQ", "neohooke", _d(48, 48, 48), _ps(range(2, 7)))]:
         mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
         for p in ps:
             sp = sfx.Space(mesh, fam, p)
@@ -556,10 +676,10 @@ def extra_linearised(sfx, torch, ctx, inputs, flush, stream):
     the operator whose action Sec. 4.1 times), vector Q_p on 48^3, p = 2..6,
     state = the residual's displacement, FP64."""
     rows = []
-    dims = (48, 48, 48)
+    dims = _d(48, 48, 48)
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     for form in ("svk", "neohooke"):
-        for p in range(2, 7):
+        for p in _ps(range(2, 7)):
             sp = sfx.Space(mesh, "VQ", p)
             ud = torch.from_numpy(inputs.displacement(sp.ndof, p, dims[0], seed=1)).cuda()
             dd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2)).cuda()
@@ -577,7 +697,7 @@ def extra_padaptive(sfx, torch, ctx, inputs, flush, stream):
     """p-adaptive batching: 200,000 cells (40x50x100), p in 1..8 with
     P(p) ~ 1/p, DQ_p per cell, Laplace + mass on 16 RHS (seeds 0..15): one
     graph-captured persistent launch vs one launch per (form, degree, RHS)."""
-    dims = (40, 50, 100)
+    dims = _d(40, 50, 100)
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     deg = inputs.padaptive_degrees(int(np.prod(dims)), 8, seed=2)
     forms, R = ["laplace", "mass"], 16
@@ -604,9 +724,9 @@ def extra_padaptive(sfx, torch, ctx, inputs, flush, stream):
 
 def extra_naive(sfx, torch, ctx, inputs, flush, stream):
     """Naive (un-factorised) vs sum-factorised action, Q_p Laplace, 32^3."""
-    mesh = sfx.Mesh.box(ctx, 32, 32, 32, perturb=0.1, seed=0)
+    mesh = sfx.Mesh.box(ctx, *_d(32, 32, 32), perturb=0.1, seed=0)
     rows = []
-    for p in range(1, 9):
+    for p in _ps(range(1, 9)):
         sp = sfx.Space(mesh, "Q", p)
         xd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
         yd = torch.empty_like(xd)
@@ -622,9 +742,9 @@ def extra_naive(sfx, torch, ctx, inputs, flush, stream):
 def extra_weighted(sfx, torch, ctx, inputs, flush, stream):
     """Weighted Laplace int kappa grad u . grad v (Sec. 1.1, Eq.
     weighted_laplace), FP64, Q_p on 64^3, beside the plain Laplace action."""
-    mesh = sfx.Mesh.box(ctx, 64, 64, 64, perturb=0.1, seed=0)
+    mesh = sfx.Mesh.box(ctx, *_d(64, 64, 64), perturb=0.1, seed=0)
     rows = []
-    for p in range(1, 9):
+    for p in _ps(range(1, 9)):
         sp = sfx.Space(mesh, "Q", p)
         xd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
         kd = 1.0 + 0.5 * torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=7)).cuda()
@@ -641,10 +761,10 @@ def extra_matrices(sfx, torch, ctx, inputs, flush, stream):
     """Element matrices (FP64): Q_p Laplace p = 1..8 and NCF/NCE p = 1..5 on
     32^3, on a chunk of cells sized to ~1 GB of output; sum-factorised and,
     p <= 4, naive."""
-    mesh = sfx.Mesh.box(ctx, 32, 32, 32, perturb=0.1, seed=0)
+    mesh = sfx.Mesh.box(ctx, *_d(32, 32, 32), perturb=0.1, seed=0)
     rows = []
-    for fam, form, ps in [("Q", "laplace", range(1, 9)), ("NCF", "ncf_mass_divdiv", range(1, 6)),
-                          ("NCE", "nce_curlcurl", range(1, 6))]:
+    for fam, form, ps in [("Q", "laplace", _ps(range(1, 9))), ("NCF", "ncf_mass_divdiv", _ps(range(1, 6))),
+                          ("NCE", "nce_curlcurl", _ps(range(1, 6)))]:
         for p in ps:
             sp = sfx.Space(mesh, fam, p)
             nc = int(min(sp.ncell, max(8, (1 << 30) // (sp.nloc * sp.nloc * 8))))
@@ -673,11 +793,11 @@ def extra_tangent(sfx, torch, ctx, inputs, flush, stream):
     """Tangent (element) matrices of the hyperelastic residual, vector Q_p on
     the 48^3 hyperelastic mesh, p = 1..6, both laws, state = the residual's
     displacement, FP64, on a chunk of cells sized to ~1 GB of output."""
-    dims = (48, 48, 48)
+    dims = _d(48, 48, 48)
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     rows = []
     for form in ("svk", "neohooke"):
-        for p in range(1, 7):
+        for p in _ps(range(1, 7)):
             sp = sfx.Space(mesh, "VQ", p)
             ud = torch.from_numpy(inputs.displacement(sp.ndof, p, dims[0], seed=1)).cuda()
             nc = int(min(sp.ncell, max(8, (1 << 30) // (sp.nloc * sp.nloc * 8))))
@@ -729,8 +849,8 @@ def matvec_block(sfx, torch, ctx, inputs, flush, stream):
     12 per nonzero (value + column) + 24 per row (x, y, row pointer); the
     achieved rate is against the measured HBM bandwidth."""
     rows = []
-    for p, n in [(1, 64), (2, 48), (3, 32), (4, 24), (5, 20), (6, 16)]:
-        mesh = sfx.Mesh.box(ctx, n, n, n, perturb=0.1, seed=0)
+    for p, n in _ps([(1, 64), (2, 48), (3, 32), (4, 24), (5, 20), (6, 16)]):
+        mesh = sfx.Mesh.box(ctx, *_d(n, n, n), perturb=0.1, seed=0)
         sp = sfx.Space(mesh, "Q", p)
         csr = sfx.Csr(sp)
         vals = torch.empty(csr.nnz, dtype=torch.float64, device="cuda")
@@ -762,9 +882,9 @@ def underint_block(sfx, torch, ctx, inputs, flush, stream):
     FP64 and TF32x3; Laplace element matrices on the first cells of a 32^3
     mesh (about 1 GB of output), delta-cancelled vs sum-factorised, with the
     bytes written per second (the collocated kernel's dense n^6 output)."""
-    mesh = sfx.Mesh.box(ctx, 64, 64, 64, perturb=0.1, seed=0)
+    mesh = sfx.Mesh.box(ctx, *_d(64, 64, 64), perturb=0.1, seed=0)
     acts = []
-    for p in range(1, 9):
+    for p in _ps(range(1, 9)):
         sp = sfx.Space(mesh, "Q", p)
         xd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
         yd = torch.empty_like(xd)
@@ -781,9 +901,9 @@ def underint_block(sfx, torch, ctx, inputs, flush, stream):
         del xd, yd, sp
     del mesh
     torch.cuda.empty_cache()
-    mesh = sfx.Mesh.box(ctx, 32, 32, 32, perturb=0.1, seed=0)
+    mesh = sfx.Mesh.box(ctx, *_d(32, 32, 32), perturb=0.1, seed=0)
     mats = []
-    for p in range(1, 9):
+    for p in _ps(range(1, 9)):
         sp = sfx.Space(mesh, "Q", p)
         nc = int(min(sp.ncell, max(8, (1 << 30) // (sp.nloc * sp.nloc * 8))))
         A = torch.empty(nc * sp.nloc * sp.nloc, dtype=torch.float64, device="cuda")
@@ -803,7 +923,7 @@ def underint_block(sfx, torch, ctx, inputs, flush, stream):
                     "and a different (under-integrated) operator; matrices: dense n^3 x n^3 output per cell"}
 
 
-def precision_block(sfx, torch, ctx, inputs, flush, stream, dims=(64, 64, 64), degrees=range(3, 9),
+def precision_block(sfx, torch, ctx, inputs, flush, stream, dims=None, degrees=None,
                     precs=("fp64", "tf32x3", "bf16x3")):
     """Per (form, p): event time of each precision, DoF/s, speedup over FP64
     and the normwise (inf) relative error against the FP64 GPU action (which
@@ -811,6 +931,8 @@ def precision_block(sfx, torch, ctx, inputs, flush, stream, dims=(64, 64, 64), d
     is the first ndof draws of stream 1 scaled by 0.05 h / p, exactly what
     inputs.displacement returns; it is generated once at the largest size and
     sliced, since the stream is counter-based."""
+    dims = dims or _d(64, 64, 64)
+    degrees = degrees or _ps(range(3, 9))
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     rows = []
     for fam, form in [("Q", "laplace"), ("VQ", "neohooke")]:
