@@ -142,6 +142,25 @@ sfx_status sfx_mesh_create_box(sfx_ctx* ctx, int nx, int ny, int nz, double pert
  * copied).  Errors as above. */
 sfx_status sfx_mesh_create_structured(sfx_ctx* ctx, int nx, int ny, int nz, const double* xyz_host,
                                       sfx_mesh** out);
+/* General hexahedral mesh: any connectivity (Sec. 1.1: the domain is a union
+ * of cells K, each the image F_K of the reference cell under its trilinear
+ * map, and global assembly sums the cells' contributions through the
+ * cell-node map).
+ *   nvert, xyz      host, nvert x 3 vertex coordinates (copied)
+ *   ncell, cell_vertices
+ *                   host, ncell x 8 int32 vertex ids per cell in VTK
+ *                   hexahedron order: the bottom face (reference z = 0)
+ *                   counter-clockwise from the origin corner, then the top
+ *                   face likewise; corners (0,0,0) (1,0,0) (1,1,0) (0,1,0)
+ *                   (0,0,1) (1,0,1) (1,1,1) (0,1,1) of the reference cell.
+ * Each cell must be positively oriented (det J > 0; the kernels flag
+ * SFX_DEV_INVERTED otherwise).  Spaces on such a mesh: Q_p, DQ_p and vector
+ * Q_p (NCF_p and NCE_p need face and edge orientation signs:
+ * SFX_ERR_UNSUPPORTED).  The assembled CSR matrix needs a box mesh.
+ * Errors: SFX_ERR_ARG (null, nvert < 8, ncell < 1, a vertex id out of range
+ * or repeated within a cell), SFX_ERR_RANGE, SFX_ERR_ALLOC, SFX_ERR_CUDA. */
+sfx_status sfx_mesh_create(sfx_ctx* ctx, int64_t nvert, const double* xyz_host, int64_t ncell,
+                           const int32_t* cell_vertices_host, sfx_mesh** out);
 /* Host view of the vertex coordinates (owned by the mesh). */
 sfx_status sfx_mesh_info(const sfx_mesh* mesh, int64_t* nvert, int64_t* ncell, const double** xyz_host);
 void sfx_mesh_destroy(sfx_mesh* mesh);
@@ -150,16 +169,34 @@ void sfx_mesh_destroy(sfx_mesh* mesh);
 
 /* Function space of `family` and degree p (1 <= p <= 8) on `mesh`; builds the
  * int32 cell-node map (ncell x nloc, host and device) and, for the continuous
- * families, the 8-colour cell lists used by the conflict-free scatter.
- * Numbering: Q_p/vector-Q_p global node (I,J,K) on the (pN+1)^3 GLL grid,
- * vector-Q_p component-major; DQ_p cell-major (cell*n^3 + l); NCF_p/NCE_p one
- * lexicographic grid per block, block-major.  The mesh must outlive the space.
+ * families, the colour lists used by the conflict-free scatter.
+ * Numbering on a box mesh: Q_p/vector-Q_p global node (I,J,K) on the
+ * (pN+1)^3 GLL grid, vector-Q_p component-major; DQ_p cell-major
+ * (cell*n^3 + l); NCF_p/NCE_p one lexicographic grid per block, block-major.
+ * Colours on a box mesh: the 8 parity classes (i&1, j&1, k&1) of the cell
+ * indices, colour 4(i&1) + 2(j&1) + (k&1), cells ascending within a colour.
+ * On a general mesh (sfx_mesh_create), Q_p: vertex dofs first (the vertex
+ * ids), then p-1 dofs per edge, (p-1)^2 per face and (p-1)^3 per cell, edges
+ * and faces numbered in order of first appearance (cells in order); an
+ * edge's nodes run from its smaller vertex id to its larger one, a face's
+ * nodes first along the edge from its smallest-id corner to that corner's
+ * neighbour of smaller id.  Colours: greedy first fit over the cells in order
+ * (the smallest colour unused by earlier cells sharing a vertex).  DQ_p is
+ * cell-major with one colour on either kind of mesh.
+ * The mesh must outlive the space.
  * Errors: SFX_ERR_ARG, SFX_ERR_UNSUPPORTED (p out of range), SFX_ERR_RANGE,
  * SFX_ERR_ALLOC, SFX_ERR_CUDA. */
 sfx_status sfx_space_create(const sfx_mesh* mesh, sfx_family family, int degree, sfx_space** out);
 /* Sizes and a host view of the cell-node map (owned by the space). */
 sfx_status sfx_space_info(const sfx_space* space, int64_t* ndof, int* nloc, int64_t* ncell,
                           const int32_t** host_map);
+/* Host view of the colour lists (owned by the space): *ncolour colours;
+ * cells[colour_off[k] .. colour_off[k+1]) are the cells of colour k.  Cells of
+ * one colour share no dof, so one scatter launch per colour never adds twice
+ * into one entry (Sec. 1.1, global assembly).  Any output may be NULL.
+ * Errors: SFX_ERR_ARG. */
+sfx_status sfx_space_colours(const sfx_space* space, int* ncolour, const int64_t** colour_off,
+                             const int32_t** cells);
 void sfx_space_destroy(sfx_space* space);
 
 /* ------------------------------------------------------------ tabulation */
@@ -390,11 +427,14 @@ void sfx_plan_destroy(sfx_plan* plan);
  * degree-sorted cell list and tile list on the device, in a fixed scratch
  * array inside the library, and calls no cudaMalloc, cudaFree or allocating
  * routine.  The paper has no counterpart: this is an interface for callers.
- *   degree       device, ncell int32, each in 1..8 (others are skipped and
- *                flagged SFX_DEV_BADCELL)
+ *   degree       device, ncell int32, each in 1..8
  *   cell_offset  device, ncell+1 int64: cell c owns dofs [off[c], off[c+1]),
- *                off[c+1] - off[c] = (degree[c]+1)^3
- *   x, y         device, ndof x nrhs (y overwritten); 1 <= nrhs <= 64
+ *                off[0] = 0, off[c+1] - off[c] = (degree[c]+1)^3
+ *   x, y         device, ndof x nrhs with ndof = off[ncell] (y overwritten);
+ *                1 <= nrhs <= 64
+ * A cell whose degree or offsets break these rules is checked on the device,
+ * flagged SFX_DEV_BADCELL (read it with sfx_sync_status) and skipped: its
+ * block of y is left as it was, and no access goes through its offsets.
  * Limit: ncell <= 262144 (SFX_ERR_RANGE beyond).  The scratch (about 5 MB) is
  * a static device array that every GPU loading the library holds until exit;
  * it keeps the last call's contents, and the call clears what must start at
@@ -402,8 +442,9 @@ void sfx_plan_destroy(sfx_plan* plan);
  * streams, or threads) race: serialise them.  The first call on a device, with
  * that device current, looks up the scratch address and uploads the 1D
  * tables; make that first call before any stream capture.
- * Errors: SFX_ERR_ARG (also: ctx's device not current on the first call),
- * SFX_ERR_UNSUPPORTED (form), SFX_ERR_RANGE, SFX_ERR_CUDA. */
+ * Errors: SFX_ERR_ARG (also: ctx's device is not the current device; this is
+ * checked on every call), SFX_ERR_UNSUPPORTED (form), SFX_ERR_RANGE,
+ * SFX_ERR_CUDA. */
 sfx_status sfx_padaptive_action_noalloc(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree,
                                         const int64_t* cell_offset, sfx_form form, const sfx_form_params* params,
                                         const double* x, double* y, int nrhs, void* stream);

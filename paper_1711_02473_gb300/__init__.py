@@ -28,8 +28,9 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported combination", -3: "C
 
 # every symbol include/sfx.h declares
 EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_string",
-           "sfx_mesh_create_box", "sfx_mesh_create_structured", "sfx_mesh_info", "sfx_mesh_destroy",
-           "sfx_space_create", "sfx_space_info", "sfx_space_destroy", "sfx_tabulate_1d",
+           "sfx_mesh_create_box", "sfx_mesh_create_structured", "sfx_mesh_create", "sfx_mesh_info",
+           "sfx_mesh_destroy", "sfx_space_create", "sfx_space_info", "sfx_space_colours", "sfx_space_destroy",
+           "sfx_tabulate_1d",
            "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices",
            "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy",
            "sfx_padaptive_action_noalloc", "sfx_qdata_create", "sfx_qdata_destroy",
@@ -77,7 +78,9 @@ def lib():
         L.sfx_status_string.restype = C.c_char_p
         L.sfx_mesh_create_box.argtypes = [P, i, i, i, d, u64, C.POINTER(P)]
         L.sfx_mesh_create_structured.argtypes = [P, i, i, i, P, C.POINTER(P)]
+        L.sfx_mesh_create.argtypes = [P, i64, P, i64, P, C.POINTER(P)]
         L.sfx_mesh_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(P)]
+        L.sfx_space_colours.argtypes = [P, C.POINTER(i), C.POINTER(P), C.POINTER(P)]
         L.sfx_mesh_destroy.argtypes = [P]
         L.sfx_mesh_destroy.restype = None
         L.sfx_space_create.argtypes = [P, i, i, C.POINTER(P)]
@@ -175,7 +178,10 @@ class Context:
 
 class Mesh:
     def __init__(self, ctx, h, dims):
-        self.ctx, self.h, self.dims = ctx, h, tuple(dims)
+        self.ctx, self.h, self.dims = ctx, h, (tuple(dims) if dims is not None else None)
+        nv, nc, p = C.c_int64(), C.c_int64(), C.c_void_p()
+        _check(lib().sfx_mesh_info(self.h, C.byref(nv), C.byref(nc), C.byref(p)), "sfx_mesh_info")
+        self.nvert, self.ncell = nv.value, nc.value
 
     @classmethod
     def box(cls, ctx, nx, ny, nz, perturb=0.1, seed=0):
@@ -192,6 +198,19 @@ class Mesh:
         _check(lib().sfx_mesh_create_structured(ctx.h, nx, ny, nz, xyz.ctypes.data_as(C.c_void_p), C.byref(h)),
                "sfx_mesh_create_structured")
         return cls(ctx, h, (nx, ny, nz))
+
+    @classmethod
+    def general(cls, ctx, xyz, cell_vertices):
+        """Any hexahedral connectivity: xyz (nvert, 3), cell_vertices (ncell,
+        8) in VTK hexahedron order."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        cv = np.ascontiguousarray(cell_vertices, dtype=np.int32)
+        if xyz.ndim != 2 or xyz.shape[1] != 3 or cv.ndim != 2 or cv.shape[1] != 8:
+            raise ValueError("xyz must be (nvert, 3) and cell_vertices (ncell, 8)")
+        h = C.c_void_p()
+        _check(lib().sfx_mesh_create(ctx.h, xyz.shape[0], xyz.ctypes.data_as(C.c_void_p), cv.shape[0],
+                                     cv.ctypes.data_as(C.c_void_p), C.byref(h)), "sfx_mesh_create")
+        return cls(ctx, h, None)
 
     def coords(self):
         nv, nc, p = C.c_int64(), C.c_int64(), C.c_void_p()
@@ -222,6 +241,14 @@ class Space:
 
     def cell_map(self):
         return np.ctypeslib.as_array(C.cast(self._map, C.POINTER(C.c_int32)), shape=(self.ncell, self.nloc)).copy()
+
+    def colours(self):
+        """(colour_off int64 (ncolour+1,), cells int32 (ncell,)): host copies."""
+        nc, off, cl = C.c_int(), C.c_void_p(), C.c_void_p()
+        _check(lib().sfx_space_colours(self.h, C.byref(nc), C.byref(off), C.byref(cl)), "sfx_space_colours")
+        o = np.ctypeslib.as_array(C.cast(off, C.POINTER(C.c_int64)), shape=(nc.value + 1,)).copy()
+        c = np.ctypeslib.as_array(C.cast(cl, C.POINTER(C.c_int32)), shape=(self.ncell,)).copy()
+        return o, c
 
     def close(self):
         if self.h:
@@ -423,7 +450,15 @@ def sfx_assemble_action_stored(ctx, form, space, qdata, x, y, nrhs=None, accumul
 def sfx_padaptive_action_noalloc(ctx, mesh, degree, cell_offset, form, x, y, nrhs=1, params=None, stream=None):
     """p-adaptive DQ action that allocates nothing (see include/sfx.h): for
     callers that cannot allocate device memory at the point of the call.
-    degree: int32 CUDA tensor (ncell); cell_offset: int64 CUDA tensor (ncell+1)."""
+    degree: int32 CUDA tensor (ncell); cell_offset: int64 CUDA tensor (ncell+1).
+    The lengths are checked here; reading ndof = cell_offset[-1] waits for the
+    stream."""
+    ncell = mesh.ncell
+    if degree.numel() != ncell or cell_offset.numel() != ncell + 1:
+        raise ValueError("degree must hold ncell int32, cell_offset ncell + 1 int64")
+    ndof = int(cell_offset[-1].item())
+    if x.numel() != ndof * nrhs or y.numel() != ndof * nrhs:
+        raise ValueError("x and y must hold cell_offset[-1] * nrhs doubles")
     _check(lib().sfx_padaptive_action_noalloc(ctx.h, mesh.h, _dptr(degree, "int32"), _dptr(cell_offset, "int64"),
                                               FORM[form], _params(params), _dptr(x, "float64"),
                                               _dptr(y, "float64"), nrhs, _stream(stream)),

@@ -14,8 +14,12 @@
 // library holds it (about 5 MB) until the process exits.  Host code may not
 // use its name as a device address (the host symbol is only a stand-in), so
 // the first call on each device, with that device current, looks the device
-// address up with cudaGetSymbolAddress and caches it.
+// address up with cudaGetSymbolAddress and caches it.  Every call checks that
+// the context's device is current, since the cached address and the mesh
+// belong to that device.
 #include <mutex>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "kern_common.cuh"
 
@@ -49,10 +53,26 @@ static __device__ __align__(256) int32_t g_noalloc_scratch[kScratchWords];
 
 namespace {
 
-__global__ void k_na_histogram(const int32_t* degree, int64_t ncell, int32_t* sc, uint32_t* status) {
+// A cell takes part only if its degree is in 1..kMaxDeg and its block of the
+// vectors is [off[c], off[c+1]) with off[c+1] - off[c] = (degree + 1)^3 and
+// off[0] = 0.  Cells that pass therefore have disjoint blocks inside
+// [0, off[ncell]); a cell that fails is flagged and skipped by every stage,
+// so the kernels never index x or y through it.
+__device__ __forceinline__ bool na_cell_ok(const int32_t* degree, const int64_t* off, int64_t c, int* d_out) {
+  const int d = degree[c];
+  if (d < 1 || d > kMaxDeg) return false;
+  const int64_t o0 = off[c], o1 = off[c + 1];
+  const int64_t n = (int64_t)(d + 1) * (d + 1) * (d + 1);
+  if (o0 < 0 || o1 - o0 != n || (c == 0 && o0 != 0)) return false;
+  *d_out = d;
+  return true;
+}
+
+__global__ void k_na_histogram(const int32_t* degree, const int64_t* off, int64_t ncell, int32_t* sc,
+                               uint32_t* status) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-    const int d = degree[c];
-    if (d < 1 || d > kMaxDeg) { atomicOr(status, SFX_DEV_BADCELL); continue; }
+    int d;
+    if (!na_cell_ok(degree, off, c, &d)) { atomicOr(status, SFX_DEV_BADCELL); continue; }
     atomicAdd(&sc[kCount + d], 1);
   }
 }
@@ -74,10 +94,10 @@ __global__ void k_na_layout(int32_t* sc, TileSizes ts) {
   sc[kCounter] = 0;
 }
 
-__global__ void k_na_scatter(const int32_t* degree, int64_t ncell, int32_t* sc) {
+__global__ void k_na_scatter(const int32_t* degree, const int64_t* off, int64_t ncell, int32_t* sc) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-    const int d = degree[c];
-    if (d < 1 || d > kMaxDeg) continue;
+    int d;
+    if (!na_cell_ok(degree, off, c, &d)) continue;
     const int pos = atomicAdd(&sc[kCursor + d], 1);
     sc[kSortedOff + pos] = (int32_t)c;
   }
@@ -102,10 +122,17 @@ __global__ void k_na_tiles(int32_t* sc, TileSizes ts, int64_t max_tiles) {
   }
 }
 
-__global__ void k_na_zero(const int64_t* off, int64_t ncell, int nrhs, double* y) {
-  const int64_t n = off[ncell] * nrhs;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = 0.0;
+// Zero the blocks of the cells that pass the check, one warp per cell (the
+// blocks are contiguous: off[c] * nrhs .. off[c+1] * nrhs).
+__global__ void k_na_zero(const int32_t* degree, const int64_t* off, int64_t ncell, int nrhs, double* y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncell; c += warps) {
+    int d;
+    if (!na_cell_ok(degree, off, c, &d)) continue;
+    const int64_t i0 = off[c] * nrhs, i1 = off[c + 1] * nrhs;
+    for (int64_t i = i0 + lane; i < i1; i += 32) y[i] = 0.0;
+  }
 }
 
 // device address of the scratch array, looked up once per device
@@ -116,6 +143,12 @@ void* g_addr[kMaxDevices] = {nullptr};
 }  // namespace
 
 int upload_all_tables();
+
+namespace {
+sfx_status noalloc_body(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree, const int64_t* cell_offset,
+                        sfx_form form, const sfx_form_params* params, const double* x, double* y, int nrhs,
+                        void* stream);
+}  // namespace
 
 }  // namespace sfx
 
@@ -129,12 +162,26 @@ extern "C" sfx_status sfx_padaptive_action_noalloc(sfx_ctx* ctx, const sfx_mesh*
   if (ctx->device < 0 || ctx->device >= kMaxDevices || mesh->ctx != ctx || !mesh->d_vmap) return SFX_ERR_ARG;
   if (form != SFX_MASS && form != SFX_LAPLACE && form != SFX_HELMHOLTZ) return SFX_ERR_UNSUPPORTED;
   if (mesh->ncell > kNoAllocMaxCells) return SFX_ERR_RANGE;
+  nvtxRangePushA("sfx_padaptive_action_noalloc");
+  const sfx_status st = noalloc_body(ctx, mesh, degree, cell_offset, form, params, x, y, nrhs, stream);
+  nvtxRangePop();
+  return st;
+}
+
+namespace sfx {
+namespace {
+
+sfx_status noalloc_body(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree, const int64_t* cell_offset,
+                        sfx_form form, const sfx_form_params* params, const double* x, double* y, int nrhs,
+                        void* stream) {
+  // the cached scratch address, the mesh and the status word belong to
+  // ctx->device: it must be the current device on every call
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != ctx->device) return SFX_ERR_ARG;
   int32_t* sc = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_addr[ctx->device]) {
-      int cur = -1;
-      if (cudaGetDevice(&cur) != cudaSuccess || cur != ctx->device) return SFX_ERR_ARG;  // device must be current
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return SFX_ERR_CUDA;
       if (upload_all_tables() != 0) return SFX_ERR_CUDA;
@@ -153,11 +200,11 @@ extern "C" sfx_status sfx_padaptive_action_noalloc(sfx_ctx* ctx, const sfx_mesh*
   const int nb = (int)((ncell + 255) / 256 < 1024 ? (ncell + 255) / 256 : 1024);
   // the scratch keeps the previous call's contents: clear the counters first
   if (cudaMemsetAsync(sc, 0, kMetaWords * sizeof(int32_t), s) != cudaSuccess) return SFX_ERR_CUDA;
-  k_na_histogram<<<nb, 256, 0, s>>>(degree, ncell, sc, ctx->d_status);
+  k_na_histogram<<<nb, 256, 0, s>>>(degree, cell_offset, ncell, sc, ctx->d_status);
   k_na_layout<<<1, 1, 0, s>>>(sc, ts);
-  k_na_scatter<<<nb, 256, 0, s>>>(degree, ncell, sc);
+  k_na_scatter<<<nb, 256, 0, s>>>(degree, cell_offset, ncell, sc);
   k_na_tiles<<<nb, 256, 0, s>>>(sc, ts, ncell);
-  k_na_zero<<<1024, 256, 0, s>>>(cell_offset, ncell, nrhs, y);
+  k_na_zero<<<nb * 8 < 4096 ? nb * 8 : 4096, 256, 0, s>>>(degree, cell_offset, ncell, nrhs, y);
   if (cudaGetLastError() != cudaSuccess) return SFX_ERR_CUDA;
   const sfx_form_params pr = params ? *params : sfx_form_params{1.0, -1.0, 0.0, 0.0};
   BatchArgs b{};
@@ -182,3 +229,6 @@ extern "C" sfx_status sfx_padaptive_action_noalloc(sfx_ctx* ctx, const sfx_mesh*
   b.form_id[0] = form;
   return batched_launch(b, grid, smem, stream) == 0 ? SFX_OK : SFX_ERR_CUDA;
 }
+
+}  // namespace
+}  // namespace sfx
