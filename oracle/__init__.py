@@ -71,6 +71,8 @@ def lib():
         L.orc_interp_grad_q_to_nce.argtypes = [i, i, i, i, P, P]
         L.orc_interp_curl_nce_to_ncf.argtypes = [i, i, i, i, P, P]
         L.orc_interp_linear_field.argtypes = [i, i, i, i, i, P, P, P, P]
+        L.orc_local_vectors.argtypes = [i, i, i, i, P, i64, P, P, i, P, i]
+        L.orc_local_matrices.argtypes = [i, i, i, i, P, i64, P, P, i]
         L.orc_set_plant.argtypes = [i]
         _lib = L
     return _lib
@@ -300,3 +302,106 @@ class planted:
     def __exit__(self, *exc):
         lib().orc_set_plant(0)
         return False
+
+
+# ---------------------------------------------------------------------------
+# Any hexahedral mesh.  The global numbering below is the oracle's own and is
+# built differently from the library's: a node of a cell is identified by its
+# position relative to the cell's corners, not by the mesh's edges and faces.
+
+# VTK hexahedron: the reference corner of each position in a cell's vertex list
+# (bottom face z = 0 counter-clockwise from the origin, then the top face).
+VTK_HEX_CORNERS = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+
+
+def vtk_to_corner_order(cell_vertices):
+    """(ncell, 8) VTK-ordered vertex ids -> (ncell, 8) with reference corner
+    (a, b, c) at column 4a + 2b + c (the oracle's corner convention)."""
+    cv = np.asarray(cell_vertices)
+    out = np.empty_like(cv)
+    for pos, (a, b, c) in enumerate(VTK_HEX_CORNERS):
+        out[:, 4 * a + 2 * b + c] = cv[:, pos]
+    return out
+
+
+def general_map(family, p, corner_vertices):
+    """Cell-node map of Q_p / vector Q_p / DQ_p on any conforming hexahedral
+    mesh, and the number of global dofs.
+
+    Q_p: the node with lattice index (i1, i2, i3) of a cell sits at the
+    trilinear combination of the cell's corners with weights
+    prod_d (i_d if a_d else p - i_d) / p^3 (the GLL nodes are symmetric, so the
+    lattice index fixes the node whatever the cell's local axes).  Two cells
+    share the node iff they give it the same set of (corner vertex id, integer
+    weight) pairs; the dofs are the distinct sets, numbered in sorted order.
+    Vector Q_p: three such blocks, component-major.  DQ_p: cell-major."""
+    V = np.asarray(corner_vertices, dtype=np.int64)
+    ncell, n = V.shape[0], p + 1
+    if family == "DQ":
+        return np.arange(ncell * n ** 3, dtype=np.int64).reshape(ncell, n ** 3), ncell * n ** 3
+    if family not in ("Q", "VQ"):
+        raise ValueError("general meshes: Q, VQ or DQ")
+    keys = np.full((ncell, n ** 3, 16), -1, dtype=np.int64)
+    l = 0
+    for i1 in range(n):
+        for i2 in range(n):
+            for i3 in range(n):
+                w = np.array([(i1 if a else p - i1) * (i2 if b else p - i2) * (i3 if c else p - i3)
+                              for a in (0, 1) for b in (0, 1) for c in (0, 1)], dtype=np.int64)
+                nz = np.flatnonzero(w)
+                vid = V[:, nz]
+                order = np.argsort(vid, axis=1)
+                keys[:, l, :len(nz)] = np.take_along_axis(vid, order, axis=1)
+                keys[:, l, 8:8 + len(nz)] = w[nz][order]
+                l += 1
+    _, inv = np.unique(keys.reshape(-1, 16), axis=0, return_inverse=True)
+    m = inv.reshape(ncell, n ** 3).astype(np.int64)
+    nd = int(m.max()) + 1
+    if family == "VQ":
+        return np.concatenate([m + c * nd for c in range(3)], axis=1), 3 * nd
+    return m, nd
+
+
+def _corners(xyz, corner_vertices):
+    return np.ascontiguousarray(np.asarray(xyz, dtype=np.float64)[np.asarray(corner_vertices)])
+
+
+def local_vectors(family, form, p, corners, xl, nq=None, params=None, nthreads=0):
+    """b^K (ncells, nloc, nrhs) from the cells' corner coordinates (ncells, 8, 3)
+    and local coefficients xl (ncells, nloc, nrhs)."""
+    corners = _f64(corners)
+    xl = _f64(xl)
+    nrhs = xl.shape[2]
+    b = np.zeros_like(xl)
+    pr = _params(form, params)
+    _check(lib().orc_local_vectors(FAMILIES[family], FORMS[form], p, nq or p + 1, _p(pr), corners.shape[0],
+                                   _p(corners), _p(xl), nrhs, _p(b), nthreads), "local_vectors")
+    return b
+
+
+def general_action(family, form, p, xyz, cell_vertices_vtk, x, nq=None, params=None, nthreads=0):
+    """y = sum_K P_K^T b^K on any hexahedral mesh, in the oracle's own
+    numbering (general_map).  Returns (y, map, ndof)."""
+    V = vtk_to_corner_order(cell_vertices_vtk)
+    m, nd = general_map(family, p, V)
+    x = _f64(x)
+    x2 = x.reshape(nd, -1)
+    xl = np.ascontiguousarray(x2[m])
+    b = local_vectors(family, form, p, _corners(xyz, V), xl, nq=nq, params=params, nthreads=nthreads)
+    y = np.zeros_like(x2)
+    for c in range(m.shape[0]):  # cells in order
+        y[m[c]] += b[c]
+    return y.reshape(x.shape), m, nd
+
+
+def general_cell_matrices(family, form, p, xyz, cell_vertices_vtk, nq=None, params=None, nthreads=0):
+    """A[c, j, i] (row = test) of every cell of a mesh given by connectivity."""
+    V = vtk_to_corner_order(cell_vertices_vtk)
+    corners = _corners(xyz, V)
+    ncell = corners.shape[0]
+    nloc = general_map(family, p, V[:1])[0].shape[1]
+    A = np.zeros((ncell, nloc, nloc))
+    pr = _params(form, params)
+    _check(lib().orc_local_matrices(FAMILIES[family], FORMS[form], p, nq or p + 1, _p(pr), ncell, _p(corners),
+                                    _p(A), nthreads), "local_matrices")
+    return A

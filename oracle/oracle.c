@@ -869,25 +869,29 @@ int orc_cell_matrices(int family, int form, int p, int nq, const double* params,
 
 static int cell_matrices_impl(int family, int form, int p, int nq, int qrule, const double* params,
                               int nx, int ny, int nz, const double* coords, const double* kappa,
-                              int64_t cell_begin, int64_t cell_end, double* A, int nthreads);
+                              const double* corners, int64_t cell_begin, int64_t cell_end, double* A,
+                              int nthreads);
 
 int orc_cell_matrices_rule(int family, int form, int p, int nq, int qrule, const double* params,
                            int nx, int ny, int nz, const double* coords,
                            int64_t cell_begin, int64_t cell_end, double* A, int nthreads) {
-  return cell_matrices_impl(family, form, p, nq, qrule, params, nx, ny, nz, coords, NULL, cell_begin, cell_end, A,
+  return cell_matrices_impl(family, form, p, nq, qrule, params, nx, ny, nz, coords, NULL, NULL, cell_begin, cell_end, A,
                             nthreads);
 }
 
 int orc_weighted_cell_matrices(int family, int p, int nq, int nx, int ny, int nz, const double* coords,
                                const double* kappa, int64_t cell_begin, int64_t cell_end, double* A, int nthreads) {
   if (!kappa || (family != ORC_Q && family != ORC_DQ)) return -1;
-  return cell_matrices_impl(family, ORC_LAPLACE, p, nq, ORC_GL, NULL, nx, ny, nz, coords, kappa, cell_begin,
+  return cell_matrices_impl(family, ORC_LAPLACE, p, nq, ORC_GL, NULL, nx, ny, nz, coords, kappa, NULL, cell_begin,
                             cell_end, A, nthreads);
 }
 
+/* corners != NULL: any mesh, cell c's corner coordinates at corners[c*24 ..]
+ * (corner (a,b,c) at 4a+2b+c), with nx = number of cells and ny = nz = 1. */
 static int cell_matrices_impl(int family, int form, int p, int nq, int qrule, const double* params,
                               int nx, int ny, int nz, const double* coords, const double* kappa,
-                              int64_t cell_begin, int64_t cell_end, double* A, int nthreads) {
+                              const double* corners, int64_t cell_begin, int64_t cell_end, double* A,
+                              int nthreads) {
   elem_t E;
   if (make_elem(family, p, nx, ny, nz, &E) || !form_ok(family, form)) return -1;
   if (form == ORC_NEOHOOKE || form == ORC_SVK) return -1;
@@ -911,7 +915,12 @@ static int cell_matrices_impl(int family, int form, int p, int nq, int qrule, co
       double* Ac = &A[(size_t)(c - cell_begin) * nloc * nloc];
       memset(Ac, 0, sizeof(double) * nloc * nloc);
       double X[8][3];
-      cell_vertices(nx, ny, nz, coords, c, X);
+      if (corners) {
+        for (int k = 0; k < 8; ++k)
+          for (int d = 0; d < 3; ++d) X[k][d] = corners[((size_t)c * 8 + k) * 3 + d];
+      } else {
+        cell_vertices(nx, ny, nz, coords, c, X);
+      }
       if (kappa) {
         elem_cell_dofs(&E, ny, nz, c, kd);
         for (int l = 0; l < nloc; ++l) kl[l] = kappa[kd[l]];
@@ -1389,4 +1398,37 @@ int orc_interp_linear_field(int family, int p, int nx, int ny, int nz, const dou
   }
   free(dofs);
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Any hexahedral mesh: the cells are given by their corner coordinates alone
+ * (corner (a,b,c) at 4a+2b+c, ncells x 8 x 3), so the per-cell integrals do
+ * not depend on any global numbering; the caller gathers and scatters through
+ * its own cell-node map (Sec. 1.1: y = sum_K P_K^T b^K). */
+int orc_local_vectors(int family, int form, int p, int nq, const double* params, int64_t ncells,
+                      const double* corners, const double* xl, int nrhs, double* b, int nthreads) {
+  elem_t E;
+  if (ncells < 1 || !corners || make_elem(family, p, 1, 1, 1, &E) || !form_ok(family, form) || nrhs < 1) return -1;
+  tab_t T;
+  if (tabulate(&E, nq, ORC_GL, &T)) return -1;
+  int err = 0;
+  int nt = nthreads_of(nthreads);
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
+  for (int64_t c = 0; c < ncells; ++c) {
+    double X[8][3];
+    for (int k = 0; k < 8; ++k)
+      for (int d = 0; d < 3; ++d) X[k][d] = corners[((size_t)c * 8 + k) * 3 + d];
+    int e = cell_vector(&E, &T, form, params, X, &xl[(size_t)c * E.nloc * nrhs], nrhs, NULL,
+                        &b[(size_t)c * E.nloc * nrhs]);
+    if (e) err = e;
+  }
+  tab_free(&T);
+  return err;
+}
+
+int orc_local_matrices(int family, int form, int p, int nq, const double* params, int64_t ncells,
+                       const double* corners, double* A, int nthreads) {
+  if (ncells < 1 || ncells > 2000000000LL || !corners) return -1;
+  return cell_matrices_impl(family, form, p, nq, ORC_GL, params, (int)ncells, 1, 1, NULL, NULL, corners, 0, ncells,
+                            A, nthreads);
 }

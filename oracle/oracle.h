@@ -129,6 +129,17 @@ int orc_interp_curl_nce_to_ncf(int p, int nx, int ny, int nz, const double* xnce
 int orc_interp_linear_field(int family, int p, int nx, int ny, int nz, const double* coords,
                             const double* A, const double* b, double* out);
 
+/* Any hexahedral mesh (no global numbering inside the oracle's C part): the
+ * cells are given by their corner coordinates, corners[c][k][d] with corner
+ * (a,b,c) at k = 4a+2b+c (ncells x 8 x 3).  Local vectors b (ncells x nloc x
+ * nrhs) from local coefficients xl (ncells x nloc x nrhs), and local element
+ * matrices A[c][j][i] (row = test); Gauss rule with nq points.  The caller
+ * gathers and scatters through its own cell-node map. */
+int orc_local_vectors(int family, int form, int p, int nq, const double* params, int64_t ncells,
+                      const double* corners, const double* xl, int nrhs, double* b, int nthreads);
+int orc_local_matrices(int family, int form, int p, int nq, const double* params, int64_t ncells,
+                       const double* corners, double* A, int nthreads);
+
 /* Deliberate-mistake switch used only by the tests that prove the pins catch
  * plausible errors.  0 = correct oracle. */
 void orc_set_plant(int which);
