@@ -3,7 +3,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <mutex>
+#include <unordered_map>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -321,19 +324,22 @@ extern "C" const char* sfx_status_string(sfx_status s) {
 
 // --------------------------------------------------------------------- mesh
 static sfx_status mesh_finish(sfx_mesh* m) {
-  const int ny = m->ny, nz = m->nz;
-  std::vector<int32_t> vmap((size_t)m->ncell * 8);
-  for (int64_t c = 0; c < m->ncell; ++c) {
-    int64_t k = c % nz, j = (c / nz) % ny, i = c / ((int64_t)ny * nz);
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b)
-        for (int cc = 0; cc < 2; ++cc)
-          vmap[c * 8 + 4 * a + 2 * b + cc] = (int32_t)(((i + a) * (ny + 1) + (j + b)) * (int64_t)(nz + 1) + (k + cc));
+  if (!m->general) {
+    const int ny = m->ny, nz = m->nz;
+    try { m->vmap.resize((size_t)m->ncell * 8); } catch (...) { return SFX_ERR_ALLOC; }
+    for (int64_t c = 0; c < m->ncell; ++c) {
+      int64_t k = c % nz, j = (c / nz) % ny, i = c / ((int64_t)ny * nz);
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+          for (int cc = 0; cc < 2; ++cc)
+            m->vmap[c * 8 + 4 * a + 2 * b + cc] =
+                (int32_t)(((i + a) * (ny + 1) + (j + b)) * (int64_t)(nz + 1) + (k + cc));
+    }
   }
   if (m->ctx->device < 0) return SFX_OK;
   sfx_status st = to_device(m->xyz.data(), m->xyz.size(), &m->d_xyz);
   if (st) return st;
-  return to_device(vmap.data(), vmap.size(), &m->d_vmap);
+  return to_device(m->vmap.data(), m->vmap.size(), &m->d_vmap);
 }
 
 static sfx_status mesh_alloc(sfx_ctx* ctx, int nx, int ny, int nz, sfx_mesh** out) {
@@ -389,6 +395,42 @@ extern "C" sfx_status sfx_mesh_create_structured(sfx_ctx* ctx, int nx, int ny, i
   if (st) return st;
   std::memcpy(m->xyz.data(), xyz, m->xyz.size() * sizeof(double));
   st = mesh_finish(m);
+  if (st) { sfx_mesh_destroy(m); return st; }
+  *out = m;
+  return SFX_OK;
+}
+
+// Local corner 4a+2b+c (reference corner (a,b,c)) -> position in the VTK
+// hexahedron's vertex list (bottom face z = 0 counter-clockwise from the
+// origin, then the top face likewise).
+static const int kVtkOfCorner[8] = {0, 4, 3, 7, 1, 5, 2, 6};
+
+extern "C" sfx_status sfx_mesh_create(sfx_ctx* ctx, int64_t nvert, const double* xyz, int64_t ncell,
+                                      const int32_t* cell_vertices, sfx_mesh** out) {
+  if (!ctx || !out || !xyz || !cell_vertices || nvert < 8 || ncell < 1) return SFX_ERR_ARG;
+  *out = nullptr;
+  if (nvert > 2000000000LL || ncell > 2000000000LL) return SFX_ERR_RANGE;
+  for (int64_t c = 0; c < ncell; ++c) {
+    const int32_t* v = cell_vertices + c * 8;
+    for (int k = 0; k < 8; ++k) {
+      if (v[k] < 0 || v[k] >= nvert) return SFX_ERR_ARG;
+      for (int l = 0; l < k; ++l)
+        if (v[l] == v[k]) return SFX_ERR_ARG;  // a degenerate hexahedron
+    }
+  }
+  sfx_mesh* m = new (std::nothrow) sfx_mesh;
+  if (!m) return SFX_ERR_ALLOC;
+  m->ctx = ctx;
+  m->general = true;
+  m->nvert = nvert;
+  m->ncell = ncell;
+  try {
+    m->xyz.assign(xyz, xyz + nvert * 3);
+    m->vmap.resize((size_t)ncell * 8);
+  } catch (...) { delete m; return SFX_ERR_ALLOC; }
+  for (int64_t c = 0; c < ncell; ++c)
+    for (int k = 0; k < 8; ++k) m->vmap[c * 8 + k] = cell_vertices[c * 8 + kVtkOfCorner[k]];
+  sfx_status st = mesh_finish(m);
   if (st) { sfx_mesh_destroy(m); return st; }
   *out = m;
   return SFX_OK;
@@ -467,15 +509,174 @@ int blocks_of(sfx_family fam, int p, const int64_t N[3], Block* B, int64_t* ndof
 
 }  // namespace
 
+namespace {
+
+// Corner index 4a+2b+c of the reference corner with bits b[0..2] = (a,b,c).
+inline int corner_of(const int b[3]) { return 4 * b[0] + 2 * b[1] + b[2]; }
+
+// Global numbering of Q_p (ncomp = 1) or vector Q_p (ncomp = 3, component-
+// major) on a general hexahedral mesh, from the mesh's topology alone:
+//   vertex dofs  = the vertex ids                          [0, nvert)
+//   edge dofs    = nvert + edge * (p-1) + k                 edges numbered in order of first appearance
+//   face dofs    = ... + face * (p-1)^2 + k                 faces likewise
+//   cell dofs    = ... + cell * (p-1)^3 + k                 interior nodes, local order
+// Two cells sharing an edge or a face must agree on the order of its interior
+// nodes, whatever their local axes.  The order is taken from the global vertex
+// ids: an edge runs from its smaller vertex id to its larger one; a face's
+// nodes run first along the face edge from its smallest-id corner to that
+// corner's neighbour with the smaller id, then along the other edge.  Since
+// the GLL nodes are symmetric (x_{p-i} = 1 - x_i), this identifies the same
+// physical points from either cell (Sec. 1.1: the global basis is the union
+// of the cells' bases, glued through shared entities).
+sfx_status general_q_map(const sfx_mesh* m, int p, int ncomp, std::vector<int32_t>& map, int64_t* ndof_out) {
+  const int n = p + 1, n3 = n * n * n, nloc = ncomp * n3;
+  const int64_t ncell = m->ncell, nvert = m->nvert;
+  const int32_t* V = m->vmap.data();
+  std::unordered_map<uint64_t, int64_t> edges;
+  std::map<std::array<int32_t, 4>, int64_t> faces;
+  if (p >= 2) {
+    for (int64_t c = 0; c < ncell; ++c) {
+      const int32_t* v = V + c * 8;
+      for (int d = 0; d < 3; ++d)      // 12 edges: along axis d, the other two bits free
+        for (int o = 0; o < 4; ++o) {
+          int b0[3], b1[3], k = 0;
+          for (int e = 0; e < 3; ++e) {
+            if (e == d) { b0[e] = 0; b1[e] = 1; continue; }
+            b0[e] = b1[e] = (o >> k++) & 1;
+          }
+          const uint32_t ga = (uint32_t)v[corner_of(b0)], gb = (uint32_t)v[corner_of(b1)];
+          const uint64_t key = ((uint64_t)std::min(ga, gb) << 32) | std::max(ga, gb);
+          edges.emplace(key, (int64_t)edges.size());
+        }
+      for (int f = 0; f < 3; ++f)      // 6 faces: axis f fixed at 0 or 1
+        for (int side = 0; side < 2; ++side) {
+          std::array<int32_t, 4> key;
+          int q = 0;
+          for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+              int bits[3], k = 0;
+              for (int e = 0; e < 3; ++e) bits[e] = e == f ? side : (k++ == 0 ? a : b);
+              key[q++] = v[corner_of(bits)];
+            }
+          std::sort(key.begin(), key.end());
+          faces.emplace(key, (int64_t)faces.size());
+        }
+    }
+  }
+  const int64_t pe = p - 1, pf = pe * pe, pc = pe * pe * pe;
+  const int64_t off_e = nvert, off_f = off_e + (int64_t)edges.size() * pe,
+                off_c = off_f + (int64_t)faces.size() * pf, per = off_c + ncell * pc;
+  if (ncomp * per >= (1LL << 31) - 1) return SFX_ERR_RANGE;
+  try { map.resize((size_t)ncell * nloc); } catch (...) { return SFX_ERR_ALLOC; }
+  for (int64_t c = 0; c < ncell; ++c) {
+    const int32_t* v = V + c * 8;
+    int32_t* row = &map[(size_t)c * nloc];
+    int l = 0;
+    for (int i1 = 0; i1 < n; ++i1)
+      for (int i2 = 0; i2 < n; ++i2)
+        for (int i3 = 0; i3 < n; ++i3, ++l) {
+          const int ii[3] = {i1, i2, i3};
+          int bnd[3], nb = 0;
+          for (int d = 0; d < 3; ++d) { bnd[d] = ii[d] == 0 || ii[d] == p; nb += bnd[d]; }
+          int64_t g;
+          if (nb == 3) {
+            const int bits[3] = {i1 / p, i2 / p, i3 / p};
+            g = v[corner_of(bits)];
+          } else if (nb == 2) {
+            int d = !bnd[0] ? 0 : (!bnd[1] ? 1 : 2);
+            int b0[3], b1[3];
+            for (int e = 0; e < 3; ++e) { b0[e] = e == d ? 0 : ii[e] / p; b1[e] = e == d ? 1 : ii[e] / p; }
+            const uint32_t ga = (uint32_t)v[corner_of(b0)], gb = (uint32_t)v[corner_of(b1)];
+            const uint64_t key = ((uint64_t)std::min(ga, gb) << 32) | std::max(ga, gb);
+            const int64_t t = ii[d], pos = ga < gb ? t - 1 : p - t - 1;
+            g = off_e + edges.at(key) * pe + pos;
+          } else if (nb == 1) {
+            const int f = bnd[0] ? 0 : (bnd[1] ? 1 : 2);
+            const int d1 = f == 0 ? 1 : 0, d2 = f == 2 ? 1 : 2;
+            int32_t cv[2][2];
+            for (int a = 0; a < 2; ++a)
+              for (int b = 0; b < 2; ++b) {
+                int bits[3];
+                bits[f] = ii[f] / p;
+                bits[d1] = a;
+                bits[d2] = b;
+                cv[a][b] = v[corner_of(bits)];
+              }
+            int a0 = 0, b0 = 0;
+            for (int a = 0; a < 2; ++a)
+              for (int b = 0; b < 2; ++b)
+                if (cv[a][b] < cv[a0][b0]) { a0 = a; b0 = b; }
+            const int64_t s1 = a0 ? p - ii[d1] : ii[d1], s2 = b0 ? p - ii[d2] : ii[d2];
+            const bool first_d1 = cv[1 - a0][b0] < cv[a0][1 - b0];
+            const int64_t u = first_d1 ? s1 : s2, w = first_d1 ? s2 : s1;
+            std::array<int32_t, 4> key = {cv[0][0], cv[0][1], cv[1][0], cv[1][1]};
+            std::sort(key.begin(), key.end());
+            g = off_f + faces.at(key) * pf + (u - 1) * pe + (w - 1);
+          } else {
+            g = off_c + c * pc + ((i1 - 1) * pe + (i2 - 1)) * pe + (i3 - 1);
+          }
+          for (int cmp = 0; cmp < ncomp; ++cmp) row[cmp * n3 + l] = (int32_t)(cmp * per + g);
+        }
+  }
+  *ndof_out = ncomp * per;
+  return SFX_OK;
+}
+
+// Greedy first-fit colouring: cells in order, each takes the smallest colour
+// that no earlier cell sharing one of its vertices has.  Cells of one colour
+// then share no vertex, hence no dof of Q_p or vector Q_p.
+void greedy_colour(const sfx_mesh* m, std::vector<int>& col, int* ncol) {
+  const int64_t ncell = m->ncell, nvert = m->nvert;
+  const int32_t* V = m->vmap.data();
+  std::vector<int64_t> start((size_t)nvert + 1, 0);
+  for (int64_t i = 0; i < ncell * 8; ++i) start[V[i] + 1]++;
+  for (int64_t v = 0; v < nvert; ++v) start[v + 1] += start[v];
+  std::vector<int64_t> fill(start.begin(), start.end() - 1);
+  std::vector<int32_t> cells_of((size_t)ncell * 8);
+  for (int64_t c = 0; c < ncell; ++c)
+    for (int k = 0; k < 8; ++k) cells_of[fill[V[c * 8 + k]]++] = (int32_t)c;
+  col.assign((size_t)ncell, -1);
+  std::vector<int64_t> seen;
+  *ncol = 0;
+  for (int64_t c = 0; c < ncell; ++c) {
+    for (int k = 0; k < 8; ++k) {
+      const int32_t v = V[c * 8 + k];
+      for (int64_t i = start[v]; i < start[v + 1]; ++i) {
+        const int32_t o = cells_of[i];
+        if (o < c) seen[col[o]] = c;
+      }
+    }
+    int k = 0;
+    while (k < *ncol && seen[k] == c) ++k;
+    if (k == *ncol) { seen.push_back(-1); ++*ncol; }
+    col[c] = k;
+  }
+}
+
+}  // namespace
+
 extern "C" sfx_status sfx_space_create(const sfx_mesh* mesh, sfx_family fam, int p, sfx_space** out) {
   if (!mesh || !out || !family_ok(fam)) return SFX_ERR_ARG;
   *out = nullptr;
   if (p < 1 || p > kMaxDeg) return SFX_ERR_UNSUPPORTED;
+  if (mesh->general && (fam == SFX_NCF || fam == SFX_NCE)) return SFX_ERR_UNSUPPORTED;
   const int64_t N[3] = {mesh->nx, mesh->ny, mesh->nz};
   Block B[3];
   int64_t ndof;
   int nloc;
-  int nb = blocks_of(fam, p, N, B, &ndof, &nloc);
+  int nb = 0;
+  const int64_t ncell = mesh->ncell;
+  std::vector<int32_t> gmap;
+  if (!mesh->general) {
+    nb = blocks_of(fam, p, N, B, &ndof, &nloc);
+  } else if (fam == SFX_DQ) {
+    nloc = (p + 1) * (p + 1) * (p + 1);
+    ndof = ncell * nloc;
+  } else {
+    sfx_status st = general_q_map(mesh, p, fam == SFX_VQ ? 3 : 1, gmap, &ndof);
+    if (st) return st;
+    nloc = (fam == SFX_VQ ? 3 : 1) * (p + 1) * (p + 1) * (p + 1);
+  }
   if (ndof >= (1LL << 31) - 1) return SFX_ERR_RANGE;
   sfx_space* s = new (std::nothrow) sfx_space;
   if (!s) return SFX_ERR_ALLOC;
@@ -484,9 +685,12 @@ extern "C" sfx_status sfx_space_create(const sfx_mesh* mesh, sfx_family fam, int
   s->p = p;
   s->nloc = nloc;
   s->ndof = ndof;
-  const int64_t ncell = mesh->ncell;
-  try { s->map.resize((size_t)ncell * nloc); } catch (...) { delete s; return SFX_ERR_ALLOC; }
-  for (int64_t c = 0; c < ncell; ++c) {
+  if (!gmap.empty()) {
+    s->map.swap(gmap);
+  } else {
+    try { s->map.resize((size_t)ncell * nloc); } catch (...) { delete s; return SFX_ERR_ALLOC; }
+  }
+  for (int64_t c = 0; c < ncell && (fam == SFX_DQ || !mesh->general); ++c) {
     int32_t* row = &s->map[(size_t)c * nloc];
     if (fam == SFX_DQ) {
       for (int l = 0; l < nloc; ++l) row[l] = (int32_t)(c * nloc + l);
@@ -506,11 +710,21 @@ extern "C" sfx_status sfx_space_create(const sfx_mesh* mesh, sfx_family fam, int
     }
   }
   // colouring: cells with the same parity in every axis share no vertex
-  std::vector<int32_t> cells((size_t)ncell);
+  // (structured box); greedy first-fit on a general mesh
+  std::vector<int32_t>& cells = s->cells;
+  try { cells.resize((size_t)ncell); } catch (...) { delete s; return SFX_ERR_ALLOC; }
   if (fam == SFX_DQ) {
     s->ncolour = 1;
     for (int64_t c = 0; c < ncell; ++c) cells[c] = (int32_t)c;
     s->colour_off = {0, ncell};
+  } else if (mesh->general) {
+    std::vector<int> col;
+    greedy_colour(mesh, col, &s->ncolour);
+    s->colour_off.assign((size_t)s->ncolour + 1, 0);
+    for (int64_t c = 0; c < ncell; ++c) s->colour_off[col[c] + 1]++;
+    for (int k = 0; k < s->ncolour; ++k) s->colour_off[k + 1] += s->colour_off[k];
+    std::vector<int64_t> pos(s->colour_off.begin(), s->colour_off.end() - 1);
+    for (int64_t c = 0; c < ncell; ++c) cells[pos[col[c]]++] = (int32_t)c;
   } else {
     s->ncolour = 8;
     s->colour_off.assign(9, 0);
@@ -545,6 +759,15 @@ extern "C" sfx_status sfx_space_info(const sfx_space* s, int64_t* ndof, int* nlo
   if (nloc) *nloc = s->nloc;
   if (ncell) *ncell = s->mesh->ncell;
   if (host_map) *host_map = s->map.data();
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_space_colours(const sfx_space* s, int* ncolour, const int64_t** colour_off,
+                                        const int32_t** cells) {
+  if (!s) return SFX_ERR_ARG;
+  if (ncolour) *ncolour = s->ncolour;
+  if (colour_off) *colour_off = s->colour_off.data();
+  if (cells) *cells = s->cells.data();
   return SFX_OK;
 }
 
@@ -944,6 +1167,7 @@ extern "C" sfx_status sfx_csr_create(const sfx_space* sp, sfx_csr** out) {
   if (!sp || !out) return SFX_ERR_ARG;
   *out = nullptr;
   if (sp->family != SFX_Q && sp->family != SFX_DQ) return SFX_ERR_UNSUPPORTED;
+  if (sp->mesh->general) return SFX_ERR_UNSUPPORTED;  // the pattern below uses the box's grid structure
   const sfx_mesh* m = sp->mesh;
   const int p = sp->p, n = p + 1, nloc = sp->nloc;
   sfx_csr* c = new (std::nothrow) sfx_csr;

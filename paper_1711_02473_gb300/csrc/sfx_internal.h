@@ -48,11 +48,13 @@ struct sfx_ctx {
 
 struct sfx_mesh {
   sfx_ctx* ctx = nullptr;
-  int nx = 0, ny = 0, nz = 0;
+  int nx = 0, ny = 0, nz = 0;      // structured box; all 0 for a general mesh
+  bool general = false;            // created by sfx_mesh_create (any hexahedral connectivity)
   int64_t nvert = 0, ncell = 0;
   std::vector<double> xyz;         // host, nvert x 3
+  std::vector<int32_t> vmap;       // host, ncell x 8 (cell -> vertices, corner (a,b,c) at 4a+2b+c)
   double* d_xyz = nullptr;         // device copy
-  int32_t* d_vmap = nullptr;       // device, ncell x 8 (cell -> vertices, corner (a,b,c) at 4a+2b+c)
+  int32_t* d_vmap = nullptr;       // device copy of vmap
 };
 
 struct sfx_space {
@@ -67,6 +69,7 @@ struct sfx_space {
   int ncolour = 1;
   double* d_naive = nullptr;       // dense 3D tabulation for the naive kernels (built on first use)
   std::vector<int64_t> colour_off; // ncolour + 1 offsets into d_cells
+  std::vector<int32_t> cells;      // host copy of the cell ids, colour by colour
   int32_t* d_cells = nullptr;
   sfx::Tab1D tab;                  // 1D tables of degree p
   // vector Q_p only: the scalar Q_p space of one component (component a's
