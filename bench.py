@@ -31,9 +31,6 @@ HELM = (1.0, -1.0, 0.0, 0.0)  # alpha * laplace + beta * mass, beta = -k^2, k = 
 # nominal GB300 FP64 pipe: 152 SMs x 2 FP64 operations (add, multiply or FMA) per
 # clock x 2.07 GHz; as flops (FMA = 2) this is the 1.26 TFLOP/s nominal figure
 FP64_PEAK_GOPS = 152 * 2 * 2.07
-# FP64 FMA throughput that a DFMA-only kernel (independent chains, 32 warps per
-# SM) sustained on GB300, G op/s: context for the nominal peak above
-FP64_DFMA_PROBE_GOPS = 500.6
 L2_FLUSH_BYTES = 256 << 20
 HBM_GBS = 6788.3             # GB300 HBM bandwidth, measured by a STREAM-style copy (GB/s)
 METRIC = "DoFs/s for sum-factorised action (mixed vs FP64, same GB300, stated error); % roofline"
@@ -104,6 +101,41 @@ def fp64_ops_per_cell(fam, p, form):
     ncontr = (0 if fam == "DQ" else 6) + (6 if lap else 0)
     pt = (47 + (1 if form == "helmholtz" else 0) if lap else 0) + ((3 if lap else 12) if mas else 0)
     return ncontr * n ** 4 + 78 * n ** 2 + pt * n ** 3
+
+
+def probe_rates(sfx, torch, target_ms=20.0):
+    """Throughput of the units the roofline divides by, measured in this run
+    with the library's probe kernels (independent chains, 4 CTAs of 256
+    threads per SM): DFMA and FFMA in G FMA/s (one FP64-pipe operation per
+    DFMA), the mma.sync forms in TFLOP/s.  Each probe is calibrated to about
+    target_ms and timed with CUDA events (median of 3)."""
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, threads = 4 * nsm, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    out = {}
+    for kind, scale, unit in (("dfma", 1e9, "G FMA/s"), ("ffma", 1e9, "G FMA/s"), ("mma_tf32", 1e12, "TFLOP/s"),
+                              ("mma_bf16", 1e12, "TFLOP/s"), ("dmma", 1e12, "TFLOP/s")):
+        iters = 16
+        for _ in range(12):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sfx.sfx_probe_launch(kind, blocks, threads, iters, sink)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            if t >= 0.5 * target_ms or iters >= 1 << 26:
+                break
+            iters = int(iters * min(64.0, max(2.0, target_ms / max(t, 1e-3))))
+        ts, ops = [], 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ops = sfx.sfx_probe_launch(kind, blocks, threads, iters, sink)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[kind] = {"rate": round(ops / (float(np.median(ts)) * 1e-3) / scale, 2), "unit": unit}
+    return out
 
 
 def arm_dtype(arm):
@@ -333,6 +365,7 @@ def main():
                         for pr in precs} - {"fp64"} | ({"fp64"} if any(pr.startswith("fp64") for pr in precs) else set()))
         degrees = sorted({p for _, p, _ in wl})
         tuning = autotune.ensure(ctx, torch.cuda.get_device_name(local), degrees=degrees, kinds=kinds)
+    probes = probe_rates(sfx, torch)
     arms = {pr: time_arm(args, sfx, torch, ctx, spaces, xs, ys, wl, pr, flush, stream, ws, local)
             for pr in precs}
     prec = precs[0]
@@ -355,8 +388,8 @@ def main():
         roofline = {"bound": "alu", "kernel": "k_action_scalar_fp64 %s p=%d %s" % (fam, p, form),
                     "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GOPS, 1), "unit": "G FP64 op/s",
                     "frac": round(achieved / FP64_PEAK_GOPS, 4),
-                    "dfma_probe_peak": FP64_DFMA_PROBE_GOPS,
-                    "frac_of_dfma_probe": round(achieved / FP64_DFMA_PROBE_GOPS, 4),
+                    "dfma_probe": probes["dfma"]["rate"],
+                    "frac_of_dfma_probe": round(achieved / probes["dfma"]["rate"], 4),
                     "traffic": round(tpc * mesh_cells / launches_per_action(fam)) if tpc else None,
                     "note": "algorithmic FP64 operations per action (all colour launches; add, multiply or FMA "
                             "= 1) / event time; peak = 152 SMs x 2 FP64 op/clk x 2.07 GHz, of nominal"}
@@ -367,8 +400,8 @@ def main():
         roofline = {"bound": "alu", "kernel": "k_action_scalar_mixed %s p=%d %s %s" % (fam, p, form, prec),
                     "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GOPS, 1), "unit": "G FP64 op/s",
                     "frac": round(achieved / FP64_PEAK_GOPS, 4),
-                    "dfma_probe_peak": FP64_DFMA_PROBE_GOPS,
-                    "frac_of_dfma_probe": round(achieved / FP64_DFMA_PROBE_GOPS, 4),
+                    "dfma_probe": probes["dfma"]["rate"],
+                    "frac_of_dfma_probe": round(achieved / probes["dfma"]["rate"], 4),
                     "traffic": round(tpc * mesh_cells / launches_per_action(fam)) if tpc else None,
                     "note": "binding resource = FP64 pipe (adjugate rows, det J, w/S and the factor scaling per "
                             "point, the FP64 scatter; the contractions run on the tensor cores); achieved = "
@@ -388,6 +421,7 @@ def main():
            # 1 per DQ_p action); the other arms are timed in their own regions
            "gpu_launches": sum(launches_per_action(f) for f, _, _ in wl) * args.steps,
            "clocks": head["clocks"], "roofline": roofline, "per_case": head["per_case"],
+           "probes": probes,
            "autotune": ({k: {str(p): v["best"] for p, v in per.items()} for k, per in tuning.items()}
                         if tuning else None),
            "arms": {pr: {"value": dofs_step * ws / (arms[pr]["ms_step"] * 1e-3), "ms_per_step": arms[pr]["ms_step"],
@@ -453,6 +487,7 @@ def emit(out, detail_file=None):
     """Detail lines first (one JSON object per section, each tagged
     "detail"), then the compact headline as the last line of stdout."""
     sections = {"per_case": out.get("per_case"), "arms": out.get("arms"), "autotune": out.get("autotune"),
+                "probes": out.get("probes"),
                 "err_vs_oracle": out.get("err_vs_oracle"), "roofline_note": out.get("roofline", {}).get("note")}
     for name, fn in (out.get("extras") or {}).items():
         sections["extras." + name] = fn

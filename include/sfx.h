@@ -50,6 +50,7 @@ typedef int32_t sfx_status;
 #define SFX_DEV_INVERTED 1u /* det J <= 0 at a quadrature point; the cell's output is zero */
 #define SFX_DEV_DETF 2u     /* det F <= 0 in a hyperelastic residual; that point contributes zero */
 #define SFX_DEV_BADCELL 4u  /* a caller-supplied cell id is out of range; that slot is skipped */
+#define SFX_DEV_TIMEOUT 8u  /* a kernel's bounded wait between its warp roles gave up; the output is not valid */
 
 typedef enum { SFX_Q = 0, SFX_DQ = 1, SFX_NCF = 2, SFX_NCE = 3, SFX_VQ = 4 } sfx_family;
 
@@ -264,9 +265,10 @@ sfx_status sfx_assemble_weighted_cell_matrices(sfx_ctx* ctx, const sfx_space* sp
  *   du   device, ndof x nrhs directions (read-only); y device, ndof x nrhs
  *        (must alias neither); accumulate as in sfx_assemble_action.
  * Deterministic colour-pass scatter.  A point with det F <= 0 (neo-Hookean)
- * contributes zero and sets SFX_DEV_DETF.  FP64 only.
- * Errors: SFX_ERR_ARG (null, aliasing, nrhs, family/form), SFX_ERR_UNSUPPORTED
- * (precision), SFX_ERR_CUDA. */
+ * contributes zero and sets SFX_DEV_DETF.  prec: FP64, or TF32X3 / BF16X3 for
+ * the 1D contractions of both fields (u and du) on the tensor cores with the
+ * geometry, F, dF, dP and the weight scaling in FP64.
+ * Errors: SFX_ERR_ARG (null, aliasing, nrhs, family/form), SFX_ERR_CUDA. */
 sfx_status sfx_assemble_linearised_action(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
                                           const sfx_space* space, const double* u, const double* du, double* y,
                                           int nrhs, int accumulate, sfx_precision prec, void* stream);
@@ -384,6 +386,47 @@ sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_for
  * Errors: SFX_ERR_ARG. */
 sfx_status sfx_tune_set_cells_per_cta(int kernel, int degree, int cells);
 sfx_status sfx_tune_get_cells_per_cta(int kernel, int degree, int* cells);
+
+/* Kind 4 of the table above: cells per batch of the warp-specialised
+ * split-precision action (0 = the launcher's choice: the most cells for
+ * which two CTAs fit in one SM's shared memory).  That kernel computes the
+ * Laplace and Helmholtz actions on Q_p / DQ_p, p >= 3, with geometry in the
+ * flux (stored factors off): a persistent CTA whose producer warps build the
+ * FP64 geometry factors of the next batch of cells while its consumer warps
+ * run the tensor-core contractions, gathers and scatters of the current one.
+ * Same arithmetic as the kernel kinds 1-2 use with staged factors.
+ * sfx_tune_set_warp_specialised switches it per degree (1 = on, the default
+ * for p >= 3; 0 = the kind-1 kernel).  Errors: SFX_ERR_ARG,
+ * SFX_ERR_UNSUPPORTED (enable at p < 3). */
+sfx_status sfx_tune_set_warp_specialised(int degree, int enable);
+sfx_status sfx_tune_get_warp_specialised(int degree, int* enable);
+
+/* ------------------------------------------------------------------ probes */
+
+/* Throughput probes of the units the roofline divides by (no counterpart in
+ * the paper: they measure this GPU).  One launch of `blocks` x `threads`
+ * threads (threads a multiple of 32, <= 1024), each running `iters` rounds of
+ * independent chains; `sink` (device, blocks*threads doubles, caller-owned)
+ * receives one folded value per thread.  *ops receives the work of the
+ * launch: FMAs for DFMA / FFMA (one FP64-pipe operation each for DFMA),
+ * flops (2 M N K per mma) for the mma.sync forms.  Time it with CUDA events on
+ * `stream`.  Errors: SFX_ERR_ARG, SFX_ERR_CUDA. */
+typedef enum {
+  SFX_PROBE_DFMA = 0,     /* FP64 FMA */
+  SFX_PROBE_FFMA = 1,     /* FP32 FMA */
+  SFX_PROBE_MMA_TF32 = 2, /* mma.sync m16n8k8 TF32, FP32 accumulate */
+  SFX_PROBE_MMA_BF16 = 3, /* mma.sync m16n8k16 BF16, FP32 accumulate */
+  SFX_PROBE_DMMA = 4      /* mma.sync m8n8k4 FP64 */
+} sfx_probe_kind;
+sfx_status sfx_probe_launch(int kind, int blocks, int threads, int iters, double* sink, void* stream, double* ops);
+
+/* Poll limit of every bounded wait between the warp roles of one kernel
+ * (mbarrier try_wait, each poll suspending for about 1 us; each wait also
+ * gives up after 2 s).  A wait that gives up sets SFX_DEV_TIMEOUT; the kernel
+ * still ends and its output is not valid.  Default 2^21; 0 makes every such
+ * wait give up at once (for testing the timeout path).  Process-wide.
+ * Errors: none. */
+sfx_status sfx_set_wait_limit(uint32_t polls);
 
 /* ------------------------------------------------------ batched execution */
 

@@ -22,7 +22,7 @@ FORM = {"mass": 0, "laplace": 1, "helmholtz": 2, "ncf_mass_divdiv": 3, "nce_curl
 NODES = {"GLL": 0, "GL": 1}
 PRECISION = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
 ALGO = {"sumfact": 0, "naive": 1, "collocated": 2}
-DEV_INVERTED, DEV_DETF, DEV_BADCELL = 1, 2, 4
+DEV_INVERTED, DEV_DETF, DEV_BADCELL, DEV_TIMEOUT = 1, 2, 4, 8
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported combination", -3: "CUDA runtime error",
           -4: "allocation failed", -5: "size exceeds 32-bit indexing"}
 
@@ -35,11 +35,13 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy",
            "sfx_padaptive_action_noalloc", "sfx_qdata_create", "sfx_qdata_destroy",
            "sfx_assemble_action_stored", "sfx_tune_set_cells_per_cta", "sfx_tune_get_cells_per_cta",
+           "sfx_tune_set_warp_specialised", "sfx_tune_get_warp_specialised", "sfx_set_wait_limit",
+           "sfx_probe_launch",
            "sfx_assemble_linearised_action", "sfx_assemble_linearised_cell_vectors",
            "sfx_assemble_linearised_cell_matrices",
            "sfx_csr_create", "sfx_csr_info", "sfx_csr_assemble", "sfx_csr_spmv", "sfx_csr_destroy",
            "sfx_assemble_weighted_action", "sfx_assemble_weighted_cell_matrices"]
-TUNE_KERNEL = {"fp64": 0, "mixed": 1, "mixed_stored": 2, "elastic_mixed": 3}
+TUNE_KERNEL = {"fp64": 0, "mixed": 1, "mixed_stored": 2, "elastic_mixed": 3, "mixed_ws": 4}
 QDATA = {"fp64": 1, "fp32": 2, "both": 3}
 EXEC = {"graph": 0, "per_launch": 1}
 
@@ -113,6 +115,10 @@ def lib():
         L.sfx_assemble_action_stored.argtypes = [P, i, C.POINTER(_Params), P, P, P, P, i, i, i, P]
         L.sfx_tune_set_cells_per_cta.argtypes = [i, i, i]
         L.sfx_tune_get_cells_per_cta.argtypes = [i, i, C.POINTER(i)]
+        L.sfx_tune_set_warp_specialised.argtypes = [i, i]
+        L.sfx_tune_get_warp_specialised.argtypes = [i, C.POINTER(i)]
+        L.sfx_set_wait_limit.argtypes = [C.c_uint32]
+        L.sfx_probe_launch.argtypes = [i, i, i, i, P, P, C.POINTER(d)]
         L.sfx_padaptive_action_noalloc.argtypes = [P, P, P, P, i, C.POINTER(_Params), P, P, i, P]
         for name in EXPORTS:
             f = getattr(L, name)
@@ -413,6 +419,33 @@ def sfx_tune_get_cells_per_cta(kernel, degree):
     v = C.c_int()
     _check(lib().sfx_tune_get_cells_per_cta(TUNE_KERNEL[kernel], degree, C.byref(v)), "sfx_tune_get_cells_per_cta")
     return v.value
+
+
+def sfx_tune_set_warp_specialised(degree, enable):
+    _check(lib().sfx_tune_set_warp_specialised(degree, int(bool(enable))), "sfx_tune_set_warp_specialised")
+
+
+def sfx_tune_get_warp_specialised(degree):
+    v = C.c_int()
+    _check(lib().sfx_tune_get_warp_specialised(degree, C.byref(v)), "sfx_tune_get_warp_specialised")
+    return bool(v.value)
+
+
+def sfx_set_wait_limit(polls):
+    _check(lib().sfx_set_wait_limit(int(polls)), "sfx_set_wait_limit")
+
+
+PROBE = {"dfma": 0, "ffma": 1, "mma_tf32": 2, "mma_bf16": 3, "dmma": 4}
+
+
+def sfx_probe_launch(kind, blocks, threads, iters, sink, stream=None):
+    """One probe launch (see include/sfx.h); returns the operations it does."""
+    if sink.numel() < blocks * threads:
+        raise ValueError("sink must hold blocks * threads doubles")
+    ops = C.c_double()
+    _check(lib().sfx_probe_launch(PROBE[kind], blocks, threads, iters, _dptr(sink, "float64"), _stream(stream),
+                                  C.byref(ops)), "sfx_probe_launch")
+    return ops.value
 
 
 class QData:

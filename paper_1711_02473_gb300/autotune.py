@@ -1,9 +1,12 @@
 """Autotuner for the cells-per-CTA of the scalar action kernels.
 
-For each kernel kind ("fp64", "mixed", "mixed_stored") and degree it times
+For each kernel kind ("fp64", "mixed", "mixed_stored", "mixed_ws") and degree it times
 the Q_p Laplace action on a tuning mesh for every candidate value (median of a
 few CUDA-event timings, L2 flushed between runs), keeps the fastest, and sets
-it in the library with sfx_tune_set_cells_per_cta.  The table can be saved per
+it in the library with sfx_tune_set_cells_per_cta.  For "mixed_ws" (the
+warp-specialised split-precision kernel, p >= 3) the candidates are cells per
+batch plus -1, which switches that kernel off for the degree in favour of the
+one-role kernel; "mixed" is timed with it off.  The table can be saved per
 GPU name and re-applied.  Only launch geometry changes: results are the same
 sums (the per-cell arithmetic does not depend on how many cells share a CTA).
 """
@@ -13,7 +16,7 @@ import os
 import numpy as np
 
 from . import (Context, Mesh, QData, Space, TUNE_KERNEL, sfx_assemble_action, sfx_assemble_action_stored,
-               sfx_tune_set_cells_per_cta)
+               sfx_tune_get_warp_specialised, sfx_tune_set_cells_per_cta, sfx_tune_set_warp_specialised)
 from . import inputs
 
 _BUILD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build")
@@ -24,6 +27,8 @@ def candidates(kind, p):
     if kind == "fp64":
         top = max(1, 256 // n2)
         return sorted({max(1, top // d) for d in (1, 2, 3, 4, 6)})
+    if kind == "mixed_ws":
+        return [-1, 1, 2, 3, 4, 6, 8] if p >= 3 else []
     return [2, 4, 6, 8, 12, 16, 24, 32] if p <= 2 else [1, 2, 3, 4, 6, 8, 12, 16]
 
 
@@ -41,6 +46,17 @@ def _time(torch, fn, reps, flush):
     return float(np.median(ts))
 
 
+def set_value(kind, p, cb):
+    """Apply one table entry (mixed_ws: -1 = off, else on with cb cells)."""
+    if kind == "mixed_ws":
+        if p < 3:
+            return
+        sfx_tune_set_warp_specialised(p, cb >= 0)
+        sfx_tune_set_cells_per_cta(kind, p, max(cb, 0))
+    else:
+        sfx_tune_set_cells_per_cta(kind, p, cb)
+
+
 def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims=(32, 32, 32), reps=3):
     """Returns {kind: {p: {"best": cb, "ms": {cb: t}}}} and applies the winners."""
     import torch
@@ -52,19 +68,26 @@ def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims
         x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
         y = torch.empty_like(x)
         qd = QData(ctx, sp, "fp32") if "mixed_stored" in kinds else None
-        for kind in kinds:
+        ws_was = sfx_tune_get_warp_specialised(p)
+        for kind in sorted(kinds, key=lambda k: k == "mixed_ws"):  # the one-role kernel first
+            if kind == "mixed_ws" and p < 3:
+                continue
             if kind == "fp64":
                 fn = lambda: sfx_assemble_action(ctx, "laplace", sp, x, y)
-            elif kind == "mixed":
+            elif kind in ("mixed", "mixed_ws"):
                 fn = lambda: sfx_assemble_action(ctx, "laplace", sp, x, y, precision="tf32x3")
             else:
                 fn = lambda: sfx_assemble_action_stored(ctx, "laplace", sp, qd, x, y, precision="tf32x3")
+            if kind == "mixed" and p >= 3:
+                sfx_tune_set_warp_specialised(p, False)
             res = {}
             for cb in candidates(kind, p):
-                sfx_tune_set_cells_per_cta(kind, p, cb)
+                set_value(kind, p, cb)
                 res[cb] = _time(torch, fn, reps, flush)
             best = min(res, key=res.get)
-            sfx_tune_set_cells_per_cta(kind, p, best)
+            set_value(kind, p, best)
+            if kind == "mixed" and p >= 3:
+                sfx_tune_set_warp_specialised(p, ws_was)
             table.setdefault(kind, {})[p] = {"best": best, "ms": {str(k): round(v, 4) for k, v in res.items()}}
         if qd is not None:
             qd.close()
@@ -75,7 +98,7 @@ def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims
 def apply(table):
     for kind, per in table.items():
         for p, rec in per.items():
-            sfx_tune_set_cells_per_cta(kind, int(p), int(rec["best"]))
+            set_value(kind, int(p), int(rec["best"]))
 
 
 def cache_dir():
@@ -110,7 +133,8 @@ def ensure(ctx, gpu_name, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_st
     table = load(gpu_name) or {}
     table = {k: {int(p): v for p, v in per.items()} for k, per in table.items()}
     apply(table)
-    missing = [(k, p) for k in kinds for p in degrees if p not in table.get(k, {})]
+    missing = [(k, p) for k in kinds for p in degrees
+               if p not in table.get(k, {}) and not (k == "mixed_ws" and p < 3)]
     if missing:
         new = tune(ctx, degrees=sorted({p for _, p in missing}), kinds=sorted({k for k, _ in missing}), **kw)
         for k, per in new.items():

@@ -56,8 +56,17 @@ int dispatch_family(bool dq, sfx_form form, const ActArgs& a, int64_t nc, cudaSt
 int launch_action_scalar_mixed_tf32(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
 int launch_action_scalar_mixed_bf16(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
 
+int launch_action_scalar_mixed_ws_tf32(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+int launch_action_scalar_mixed_ws_bf16(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+
 int launch_action_scalar_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
                                void* stream) {
+  // the warp-specialised kernel where it applies (Laplace part, p >= 3,
+  // geometry in the kernel), else the one-role kernel
+  int e = -1;
+  if (prec == SFX_PREC_TF32X3) e = launch_action_scalar_mixed_ws_tf32(sp, form, a, stream);
+  if (prec == SFX_PREC_BF16X3) e = launch_action_scalar_mixed_ws_bf16(sp, form, a, stream);
+  if (e != -1) return e;
   if (prec == SFX_PREC_TF32X3) return launch_action_scalar_mixed_tf32(sp, form, a, stream);
   if (prec == SFX_PREC_BF16X3) return launch_action_scalar_mixed_bf16(sp, form, a, stream);
   return -1;

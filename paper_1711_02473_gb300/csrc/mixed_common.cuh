@@ -64,11 +64,12 @@ __device__ __forceinline__ int faddr(int c, int f, int k) {
 // fiber of every cell in the CTA (TRANS: M[k][r]).  One warp owns 8 fibers at a
 // time (the n dimension of the mma); in-place use is safe because a warp reads
 // all of its fibers before writing them and no other warp touches them.
-template <int N, int AX, bool TRANS, bool ACC, int PREC, int NT = kThreads>
+// NT: threads taking part (whole warps, starting at warp WOFF of the CTA).
+template <int N, int AX, bool TRANS, bool ACC, int PREC, int NT = kThreads, int WOFF = 0>
 __device__ __forceinline__ void tc_contract(const float* in, float* out, const TabF& M, int ncell) {
   constexpr int NW = NT / 32;
   constexpr int N2 = N * N;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - WOFF;
   const int g = lane >> 2, tq = lane & 3;
   const int nfib = ncell * N2;
   const int ntiles = (nfib + 7) >> 3;

@@ -211,6 +211,8 @@ static int upload_tables(const Tab1D* t) {
   int e = upload_tab_scalar(t);
   if (!e) e = upload_tab_scalar_mixed_tf32(t);
   if (!e) e = upload_tab_scalar_mixed_bf16(t);
+  if (!e) e = upload_tab_scalar_mixed_ws_tf32(t);
+  if (!e) e = upload_tab_scalar_mixed_ws_bf16(t);
   if (!e) e = upload_tab_qdata(t);
   if (!e) e = upload_tab_hdivcurl(t);
   if (!e) e = upload_tab_elastic(t);
@@ -221,6 +223,7 @@ static int upload_tables(const Tab1D* t) {
   if (!e) e = upload_tab_scalar_coll(t);
   if (!e) e = upload_tab_scalar_mixed_coll(t);
   if (!e) e = upload_tab_elastic_lin(t);
+  if (!e) e = upload_tab_elastic_lin_mixed(t);
   if (!e) e = upload_tab_scalar_kappa(t);
   return e;
 }
@@ -249,9 +252,14 @@ constexpr int kBuiltinCells[SFX_TUNE_NKERNEL][kMaxDeg + 1] = {
     {0, 8, 6, 8, 4, 4, 2, 2, 2},    // split precision, geometry at the point
     {0, 8, 6, 6, 6, 3, 3, 3, 3},    // split precision, stored factors
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision hyperelastic residual
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},    // warp-specialised split precision (launcher default)
 };
+int g_ws[kMaxDeg + 1] = {0, 0, 0, 1, 1, 1, 1, 1, 1};  // by degree; needs n = p + 1 >= 4
+uint32_t g_wait_cap = 1u << 21;
 }
 namespace sfx {
+bool ws_enabled(int degree) { return degree >= 3 && degree <= kMaxDeg && g_ws[degree] != 0; }
+uint32_t ws_wait_cap() { return g_wait_cap; }
 int tuned_cells_per_cta(int kernel, int degree, int fallback) {
   if (kernel < 0 || kernel >= SFX_TUNE_NKERNEL || degree < 1 || degree > kMaxDeg) return fallback;
   if (g_tune[kernel][degree] > 0) return g_tune[kernel][degree];
@@ -264,6 +272,24 @@ extern "C" sfx_status sfx_tune_set_cells_per_cta(int kernel, int degree, int cel
   if (kernel < 0 || kernel >= SFX_TUNE_NKERNEL || degree < 1 || degree > kMaxDeg || cells < 0 || cells > 64)
     return SFX_ERR_ARG;
   g_tune[kernel][degree] = cells;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_tune_set_warp_specialised(int degree, int enable) {
+  if (degree < 1 || degree > kMaxDeg || (enable != 0 && enable != 1)) return SFX_ERR_ARG;
+  if (enable && degree < 3) return SFX_ERR_UNSUPPORTED;
+  g_ws[degree] = enable;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_tune_get_warp_specialised(int degree, int* enable) {
+  if (degree < 1 || degree > kMaxDeg || !enable) return SFX_ERR_ARG;
+  *enable = ws_enabled(degree) ? 1 : 0;
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_set_wait_limit(uint32_t polls) {
+  g_wait_cap = polls;
   return SFX_OK;
 }
 
@@ -988,8 +1014,11 @@ static sfx_status linearised(sfx_ctx* ctx, sfx_form form, const sfx_form_params*
   if (sp->family != SFX_VQ || (form != SFX_NEOHOOKE && form != SFX_SVK)) return SFX_ERR_ARG;
   if (y == du || y == u) return SFX_ERR_ARG;
   if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3) return SFX_ERR_ARG;
-  if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
   if (ncells < 0 || (ncells > 0 && !cells)) return SFX_ERR_ARG;
+  auto launch = [&](const ActArgs& aa) {
+    return prec == SFX_PREC_FP64 ? launch_linearised_elastic(sp, form, aa, stream)
+                                 : launch_linearised_elastic_mixed(sp, form, prec, aa, stream);
+  };
   sfx_form_params pr = params ? *params : default_params(form);
   cudaStream_t s = (cudaStream_t)stream;
   ActArgs a{};
@@ -1009,7 +1038,7 @@ static sfx_status linearised(sfx_ctx* ctx, sfx_form form, const sfx_form_params*
     a.cells64 = cells;
     a.ncells = ncells;
     a.cell_vectors = 1;
-    const int e = launch_linearised_elastic(sp, form, a, stream);
+    const int e = launch(a);
     if (e == -1) return SFX_ERR_UNSUPPORTED;
     return e ? SFX_ERR_CUDA : SFX_OK;
   }
@@ -1020,7 +1049,7 @@ static sfx_status linearised(sfx_ctx* ctx, sfx_form form, const sfx_form_params*
     a.cells = sp->d_cells + sp->colour_off[col];
     a.ncells = sp->colour_off[col + 1] - sp->colour_off[col];
     if (a.ncells == 0) continue;
-    const int e = launch_linearised_elastic(sp, form, a, stream);
+    const int e = launch(a);
     if (e == -1) return SFX_ERR_UNSUPPORTED;
     if (e) return SFX_ERR_CUDA;
   }

@@ -132,6 +132,8 @@ int launch_action_scalar_mixed(const sfx_space* sp, sfx_form form, sfx_precision
 int launch_action_scalar_naive(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
 // Linearised hyperelastic operator at the state a.xs on the directions a.x (FP64).
 int launch_linearised_elastic(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+int launch_linearised_elastic_mixed(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
+                                    void* stream);
 // Q_p actions with the collocated GLL rule (B = I): FP64 and TF32x3.
 int launch_action_scalar_coll(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
 int launch_action_scalar_mixed_coll(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
@@ -196,14 +198,21 @@ enum {
   SFX_TUNE_SCALAR_MIXED = 1,
   SFX_TUNE_SCALAR_MIXED_STORED = 2,
   SFX_TUNE_ELASTIC_MIXED = 3,
-  SFX_TUNE_NKERNEL = 4
+  SFX_TUNE_SCALAR_MIXED_WS = 4,
+  SFX_TUNE_NKERNEL = 5
 };
 int tuned_cells_per_cta(int kernel, int degree, int fallback);
+// Warp-specialised split-precision scalar action on (1) or off (0) by degree.
+bool ws_enabled(int degree);
+// Poll limit of the bounded waits between warp roles (sfx_set_wait_limit).
+uint32_t ws_wait_cap();
 
 // Each kernel file keeps its own constant-memory copy of the 1D tables.
 int upload_tab_scalar(const Tab1D* t);
 int upload_tab_scalar_mixed_tf32(const Tab1D* t);
 int upload_tab_scalar_mixed_bf16(const Tab1D* t);
+int upload_tab_scalar_mixed_ws_tf32(const Tab1D* t);
+int upload_tab_scalar_mixed_ws_bf16(const Tab1D* t);
 int upload_tab_hdivcurl(const Tab1D* t);
 int upload_tab_elastic(const Tab1D* t);
 int upload_tab_elastic_mixed(const Tab1D* t);
@@ -214,6 +223,7 @@ int upload_tab_qdata(const Tab1D* t);
 int upload_tab_scalar_coll(const Tab1D* t);
 int upload_tab_scalar_mixed_coll(const Tab1D* t);
 int upload_tab_elastic_lin(const Tab1D* t);
+int upload_tab_elastic_lin_mixed(const Tab1D* t);
 int upload_tab_scalar_kappa(const Tab1D* t);
 
 }  // namespace sfx

@@ -104,4 +104,4 @@ def test_headline_line_is_compact(capsys):
         assert k in h, k
     assert h["fp64_value"] == 1e10 and h["max_rel_err_vs_oracle"]["tf32x3"] == 4e-6
     assert all(json.loads(l)["detail"] for l in lines[:-1])
-    assert len(lines) == 1 + 4 + 10  # per_case, arms, err_vs_oracle, roofline_note; ten extras
+    assert len(lines) == 1 + 4 + 10  # per_case, arms, err_vs_oracle, roofline_note; ten extras (no probes here)

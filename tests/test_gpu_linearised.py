@@ -102,8 +102,9 @@ def test_linearised_errors(gpu):
     u = torch.zeros(sp.ndof, dtype=torch.float64, device="cuda")
     du = torch.zeros_like(u)
     y = torch.empty_like(u)
-    with pytest.raises(sfx.SfxError) as e:
-        sfx.sfx_assemble_linearised_action(ctx, "neohooke", sp, u, du, y, precision="tf32x3")
+    A = torch.empty(sp.nloc * sp.nloc, dtype=torch.float64, device="cuda")
+    with pytest.raises(sfx.SfxError) as e:  # tangent matrices: FP64 only
+        sfx.sfx_assemble_linearised_cell_matrices(ctx, "neohooke", sp, u, 0, 1, A, precision="tf32x3")
     assert e.value.code == -2
     with pytest.raises(sfx.SfxError) as e:
         sfx.sfx_assemble_linearised_action(ctx, "neohooke", sp, u, du, du)
