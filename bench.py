@@ -363,6 +363,8 @@ def main():
         from paper_1711_02473_gb300 import autotune
         kinds = sorted({("fp64" if pr.startswith("fp64") else ("mixed_stored" if pr.endswith(":stored") else "mixed"))
                         for pr in precs} - {"fp64"} | ({"fp64"} if any(pr.startswith("fp64") for pr in precs) else set()))
+        if "mixed" in kinds:
+            kinds = kinds + ["mixed_ws"]  # after "mixed": the warp-specialised kernel or the one-role one, per degree
         degrees = sorted({p for _, p, _ in wl})
         tuning = autotune.ensure(ctx, torch.cuda.get_device_name(local), degrees=degrees, kinds=kinds)
     probes = probe_rates(sfx, torch)
@@ -709,21 +711,41 @@ def extra_structured(sfx, torch, ctx, inputs, flush, stream):
 def extra_linearised(sfx, torch, ctx, inputs, flush, stream):
     """Linearised hyperelastic operator K(u) du (the Jacobian of the residual;
     the operator whose action Sec. 4.1 times), vector Q_p on 48^3, p = 2..6,
-    state = the residual's displacement, FP64."""
+    state = the residual's displacement: FP64 and TF32x3 (split-precision
+    contractions), the speed-up, the error against the FP64 GPU action and
+    against the oracle on six sampled cells (first, last and four seeded)."""
     rows = []
     dims = _d(48, 48, 48)
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    import oracle as orc
+    X = mesh.coords()
+    rng = np.random.default_rng(17)
     for form in ("svk", "neohooke"):
         for p in _ps(range(2, 7)):
             sp = sfx.Space(mesh, "VQ", p)
-            ud = torch.from_numpy(inputs.displacement(sp.ndof, p, dims[0], seed=1)).cuda()
-            dd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2)).cuda()
-            yd = torch.empty_like(dd)
-            t = _time(torch, stream, flush,
-                      lambda: sfx.sfx_assemble_linearised_action(ctx, form, sp, ud, dd, yd, stream=stream))
-            rows.append({"family": "VQ", "form": form + "_linearised", "p": p, "mesh": "%dx%dx%d" % dims,
-                         "ndof": sp.ndof, "ms": round(t, 4), "dofs_per_s": sp.ndof / (t * 1e-3)})
-            del ud, dd, yd, sp
+            u = inputs.displacement(sp.ndof, p, dims[0], seed=1)
+            du = inputs.random_vector(sp.ndof, 1, seed=2)
+            ud, dd = torch.from_numpy(u).cuda(), torch.from_numpy(du).cuda()
+            row = {"family": "VQ", "form": form + "_linearised", "p": p, "mesh": "%dx%dx%d" % dims, "ndof": sp.ndof}
+            ys = {}
+            cells = np.unique(np.concatenate([[0, sp.ncell - 1], rng.choice(sp.ncell, 4, replace=False)]))
+            ref = orc.linearised_cell_vectors(form, p, dims, X, u, du, cells)
+            cd = torch.from_numpy(cells.astype(np.int64)).cuda()
+            for prec in ("fp64", "tf32x3"):
+                ys[prec] = torch.empty_like(dd)
+                t = _time(torch, stream, flush,
+                          lambda: sfx.sfx_assemble_linearised_action(ctx, form, sp, ud, dd, ys[prec], precision=prec,
+                                                                     stream=stream))
+                row[prec + "_ms"] = round(t, 4)
+                row[prec + "_dofs_per_s"] = sp.ndof / (t * 1e-3)
+                b = torch.empty(len(cells) * sp.nloc, dtype=torch.float64, device="cuda")
+                sfx.sfx_assemble_linearised_cell_vectors(ctx, form, sp, ud, dd, cd, b, precision=prec)
+                row[prec + "_rel_err_vs_oracle_sampled"] = float(np.abs(b.cpu().numpy().reshape(ref.shape) - ref).max()
+                                                                 / np.abs(ref).max())
+            row["tf32x3_speedup_vs_fp64"] = row["fp64_ms"] / row["tf32x3_ms"]
+            row["tf32x3_rel_err_vs_fp64"] = float((ys["tf32x3"] - ys["fp64"]).abs().max() / ys["fp64"].abs().max())
+            rows.append(row)
+            del ud, dd, ys, sp
     del mesh
     return {"rows": rows, "device_status": ctx.sync_status()}
 

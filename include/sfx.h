@@ -387,7 +387,11 @@ sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_for
 sfx_status sfx_tune_set_cells_per_cta(int kernel, int degree, int cells);
 sfx_status sfx_tune_get_cells_per_cta(int kernel, int degree, int* cells);
 
-/* Kind 4 of the table above: cells per batch of the warp-specialised
+/* Kind 5 of the table above: cells per tile of the persistent p-adaptive
+ * batch (sfx_plan_create_padaptive, sfx_padaptive_action_noalloc), at most the
+ * count the kernel's shared-memory layout holds for that degree (larger values
+ * are clamped); 0 = that count.  Takes effect for plans created afterwards.
+ * Kind 4: cells per batch of the warp-specialised
  * split-precision action (0 = the launcher's choice: the most cells for
  * which two CTAs fit in one SM's shared memory).  That kernel computes the
  * Laplace and Helmholtz actions on Q_p / DQ_p, p >= 3, with geometry in the
@@ -395,8 +399,8 @@ sfx_status sfx_tune_get_cells_per_cta(int kernel, int degree, int* cells);
  * FP64 geometry factors of the next batch of cells while its consumer warps
  * run the tensor-core contractions, gathers and scatters of the current one.
  * Same arithmetic as the kernel kinds 1-2 use with staged factors.
- * sfx_tune_set_warp_specialised switches it per degree (1 = on, the default
- * for p >= 3; 0 = the kind-1 kernel).  Errors: SFX_ERR_ARG,
+ * sfx_tune_set_warp_specialised switches it per degree (1 = on; 0 = the kind-1
+ * kernel; default on at p = 4, 5, 6, 8, where it measured faster on GB300).  Errors: SFX_ERR_ARG,
  * SFX_ERR_UNSUPPORTED (enable at p < 3). */
 sfx_status sfx_tune_set_warp_specialised(int degree, int enable);
 sfx_status sfx_tune_get_warp_specialised(int degree, int* enable);

@@ -29,6 +29,8 @@ def candidates(kind, p):
         return sorted({max(1, top // d) for d in (1, 2, 3, 4, 6)})
     if kind == "mixed_ws":
         return [-1, 1, 2, 3, 4, 6, 8] if p >= 3 else []
+    if kind == "batched":
+        return [1, 2, 3, 4, 6, 8, 12, 16, 24, 32]
     return [2, 4, 6, 8, 12, 16, 24, 32] if p <= 2 else [1, 2, 3, 4, 6, 8, 12, 16]
 
 
@@ -63,7 +65,12 @@ def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims
     mesh = Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device="cuda")
     table = {}
+    if "batched" in kinds:
+        table["batched"] = tune_batched(ctx, degrees, torch, flush, reps)
+        kinds = [k for k in kinds if k != "batched"]
     for p in degrees:
+        if not kinds:
+            break
         sp = Space(mesh, "Q", p)
         x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
         y = torch.empty_like(x)
@@ -93,6 +100,31 @@ def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims
             qd.close()
         del x, y, sp
     return table
+
+
+def tune_batched(ctx, degrees, torch, flush, reps, dims=(20, 20, 20), nrhs=4):
+    """Cells per tile of the persistent p-adaptive batch, per degree: a DQ_p
+    mesh of that single degree, Laplace + mass on nrhs right-hand sides, one
+    graph launch per candidate (a plan per candidate: tiles are cut when the
+    plan is made)."""
+    from . import Plan
+    mesh = Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    ncell = dims[0] * dims[1] * dims[2]
+    out = {}
+    for p in degrees:
+        res = {}
+        deg = np.full(ncell, p, dtype=np.int32)
+        for cb in candidates("batched", p):
+            sfx_tune_set_cells_per_cta("batched", p, cb)
+            plan = Plan(ctx, mesh, deg, ["laplace", "mass"], nrhs=nrhs)
+            x = torch.from_numpy(inputs.random_vector(plan.ndof * nrhs, 1, seed=1)).cuda()
+            ys = [torch.empty_like(x) for _ in range(2)]
+            res[cb] = _time(torch, lambda: plan.execute(x, ys), reps, flush)
+            plan.close()
+        best = min(res, key=res.get)
+        sfx_tune_set_cells_per_cta("batched", p, best)
+        out[p] = {"best": best, "ms": {str(k): round(v, 4) for k, v in res.items()}}
+    return out
 
 
 def apply(table):

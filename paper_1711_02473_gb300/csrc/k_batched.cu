@@ -85,10 +85,16 @@ int cb_min(int form_mask) {
 // Team counts per degree (a tile must fit every form's shared-memory layout:
 // the minimum over the three forms), the dynamic shared memory of the
 // persistent kernel and its grid (CTAs resident on all SMs).
+// Cells per tile: the tuned value (sfx_tune_set_cells_per_cta, kind 5) where
+// one is set, at most the layout's count; smaller tiles give the tile counter
+// finer pieces to balance across the SMs.  Only launch geometry changes: each
+// cell's arithmetic is the same.
 int batched_config(int* cb, size_t* smem, int* grid) {
-  cb[0] = 0;
-  cb[1] = cb_min<2>(7); cb[2] = cb_min<3>(7); cb[3] = cb_min<4>(7); cb[4] = cb_min<5>(7);
-  cb[5] = cb_min<6>(7); cb[6] = cb_min<7>(7); cb[7] = cb_min<8>(7); cb[8] = cb_min<9>(7);
+  batched_tile_sizes(cb);
+  for (int p = 1; p <= kMaxDeg; ++p) {
+    const int t = tuned_cells_per_cta(SFX_TUNE_BATCHED, p, cb[p]);
+    cb[p] = t >= 1 && t < cb[p] ? t : cb[p];
+  }
   *smem = kBudget;
   cudaError_t e = cudaFuncSetAttribute(k_batched_dq_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBudget);
   if (e != cudaSuccess) return (int)e;

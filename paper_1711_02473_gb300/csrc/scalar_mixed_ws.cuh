@@ -2,19 +2,21 @@
 // scalar_mixed_ws.cuh -- warp-specialised split-precision scalar action
 // (Laplace and Helmholtz on Q_p and DQ_p, n >= 4).
 //
-// Same arithmetic as k_action_scalar_mixed with the per-point factors staged
-// once per cell (the geo_once path of that kernel): Sec. 3.3, Eqs. coeff_eval
-// and form_eval, with the sum factorisation of Sec. 3.2.  What changes is who
+// Same algorithm as k_action_scalar_mixed (Sec. 3.3, Eqs. coeff_eval and
+// form_eval, with the sum factorisation of Sec. 3.2), with the per-point
+// geometry staged once per cell of a batch.  What changes is who
 // does it and when.  On this GPU the FP64 pipe (geometry: adjugate-row tables,
 // det J, the weight scaling) and the other units (tensor-core contractions,
 // shared-memory traffic, gathers and scatters) can run at the same time, but a
 // kernel whose warps all go through the phases together uses them one after
 // the other.  Here a persistent CTA splits its warps in two roles:
 //   producers (NPW warps): for batch j of cb cells, the adjugate-row tables,
-//     then, once the factor buffer is free, the factors K = w S G G^T (six
-//     FP32 values, scaled in FP64) and beta w S at every point;
-//   consumers (NCW warps): gather, forward contractions, the flux with the
-//     factors, transposed contractions and scatter of batch j.
+//     then, once the factor buffer is free, at every point t = alpha w / S
+//     (FP64), the row products D = R R^T of adj J (six FP32 values) and
+//     beta w S;
+//   consumers (NCW warps): gather, forward contractions, the flux t (D g)
+//     (the scaling by t in FP64: three operations per point, all the FP64
+//     work they do), transposed contractions and scatter of batch j.
 // One factor buffer is enough: the consumers read it only in their flux
 // phase, so the producers fill it for batch j+1 while the consumers run the
 // transposed contractions and scatter of batch j and the gather and forward
@@ -84,26 +86,80 @@ __device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, uint32_t
   return false;
 }
 
+// Producer work at point qp of a cell, from its 2D adjugate-row tables: the
+// rows r_k of adj J, S = det J and t = alpha w / S (one-step Newton
+// reciprocal) in FP64; the six row products D = (r_k . r_l) in FP32 from the
+// rows rounded once (they only feed FP32 factors); beta w S rounded to FP32.
+// The consumer applies t R R^T g as t (D g), the scaling by t in FP64, so the
+// FP64 work here is the geometry alone.  Returns S.
+template <int N, bool LAP, bool MAS>
+__device__ __forceinline__ double ws_point_factors(const double* tab, const double* xq, const double* wq, int qp,
+                                                   double alpha, double beta, float* D, double* t, float* wsm) {
+  constexpr int N2 = N * N;
+  constexpr int REC23 = LAP ? 16 : 4;
+  const int q1 = qp / N2, q2 = (qp / N) % N, q3 = qp % N;
+  double r0[3], r1[3], r2[3], w;
+  const double S = adj_rows<N, REC23, LAP>(tab, tab + N2 * REC23, xq, wq, q1, q2, q3, r0, r1, r2, &w);
+  if (LAP) {
+    *t = (alpha * w) * recip_nr<1>(S);
+    float f0[3], f1[3], f2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      f0[k] = d2f_int(r0[k]);
+      f1[k] = d2f_int(r1[k]);
+      f2[k] = d2f_int(r2[k]);
+    }
+    auto dotf = [](const float* u, const float* v) { return fmaf(u[0], v[0], fmaf(u[1], v[1], u[2] * v[2])); };
+    D[0] = dotf(f0, f0);
+    D[1] = dotf(f1, f1);
+    D[2] = dotf(f2, f2);
+    D[3] = dotf(f0, f1);
+    D[4] = dotf(f0, f2);
+    D[5] = dotf(f1, f2);
+  }
+  if (MAS) *wsm = d2f_int((beta * w) * S);
+  return S;
+}
+
 template <int N, int FORM, int NPW, int NCW>
 struct WsShape {
   using Sh = MixedShape<N, FORM>;
   static constexpr int N2 = N * N, N3 = N2 * N;
   static constexpr bool LAP = FORM != SFX_MASS, MAS = FORM != SFX_LAPLACE;
   static constexpr int NPT = NPW * 32, NCT = NCW * 32, NT = NPT + NCT;
-  static constexpr int NK = (LAP ? 6 : 0) + (MAS ? 1 : 0);  // staged factors per point
+  static constexpr int NK = (LAP ? 6 : 0) + (MAS ? 1 : 0);  // staged FP32 factors per point
+  static constexpr int NT64 = LAP ? 1 : 0;                  // staged FP64 factors per point (t = alpha w / S)
   static constexpr int NC = LAP ? 4 : 1;                    // consumer arrays per point (U, G0..G2)
+  // map entries kept in shared memory from the gather to the scatter, when
+  // there is room: not with the mass factor of the Helmholtz form, which would
+  // leave only one n = 9 cell per batch at two CTAs per SM
+  static constexpr bool CMAP = !MAS;
   static constexpr int TMPD = 24 + kAdjEdge + kAdjT1D * N;  // corners, edge vectors, 1D vectors
   static constexpr int TABD = N2 * (Sh::REC23 + 6);         // 2D tables R23, R12
   static constexpr int PD = TMPD + TABD;                    // producer doubles per cell
   static constexpr size_t kHead = 64;                       // two mbarriers, the abort word
   static constexpr size_t bytes(int cb) {
-    return kHead + 2 * sizeof(TabF) + 32 * 8 + (size_t)cb * PD * 8 + (size_t)cb * N3 * (NK + NC) * 4 +
-           (size_t)cb * N3 * 4 + (size_t)cb * 4 * 4;
+    return kHead + 2 * sizeof(TabF) + 32 * 8 + (size_t)cb * (PD + NT64 * N3) * 8 + (size_t)cb * N3 * (NK + NC) * 4 +
+           (CMAP ? (size_t)cb * N3 * 4 : 0) + (size_t)cb * 4 * 4;
   }
 };
 
+// Warp split and CTAs per SM, chosen by measurement (see the launcher).
+#ifndef SFX_WS_NPW
+#define SFX_WS_NPW 8
+#endif
+#ifndef SFX_WS_NCW
+#define SFX_WS_NCW 8
+#endif
+#ifndef SFX_WS_CTAS
+#define SFX_WS_CTAS 2
+#endif
+#ifndef SFX_WS_PUNROLL
+#define SFX_WS_PUNROLL 1
+#endif
+
 template <int N, bool DQ, int FORM, int PREC, int NPW, int NCW>
-__global__ void __launch_bounds__((NPW + NCW) * 32, 2)
+__global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
     k_action_scalar_mixed_ws(const ActArgs a, const int64_t ncell_total, const int cb, const int64_t nbatch,
                              const uint32_t cap) {
   static_assert(FORM != SFX_MASS && N >= 4, "Laplace part and the staged adjugate tables (n >= 4) only");
@@ -114,8 +170,8 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
   const Tab1D& T = c_tab[N - 1];
   extern __shared__ double smd[];
   // layout: [full, empty mbarriers; abort word][2 TabF][xq 16][wq 16]
-  //         [producer doubles: cb x PD][factors: NK x cb x N3 floats]
-  //         [consumer floats: NC x cb x N3][map: cb x N3 ints][bad, ccid, pcid, cbad: cb ints each]
+  //         [producer doubles: cb x PD][t: cb x N3 doubles][factors: NK x cb x N3 floats]
+  //         [consumer floats: NC x cb x N3][map: cb x N3 ints if CMAP][bad, ccid, pcid, cbad: cb ints each]
   unsigned char* base = reinterpret_cast<unsigned char*>(smd);
   uint64_t* full = reinterpret_cast<uint64_t*>(base);
   uint64_t* empty = full + 1;
@@ -124,10 +180,11 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
   double* xq = reinterpret_cast<double*>(tabs + 2);
   double* wq = xq + 16;
   double* pd = wq + 16;
-  float* kf = reinterpret_cast<float*>(pd + (size_t)cb * W::PD);
+  double* td = pd + (size_t)cb * W::PD;
+  float* kf = reinterpret_cast<float*>(td + (size_t)cb * N3 * W::NT64);
   float* cf = kf + (size_t)cb * N3 * W::NK;
   int* cmap = reinterpret_cast<int*>(cf + (size_t)cb * N3 * W::NC);
-  int* bad = cmap + (size_t)cb * N3;
+  int* bad = cmap + (W::CMAP ? (size_t)cb * N3 : 0);
   int* ccid = bad + cb;
   int* pcid = ccid + cb;
   int* cbad = pcid + cb;
@@ -154,6 +211,7 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
   if (tid < NPT) {
     // ------------------------------------------------------------ producers
     const int pt = tid;
+    constexpr int PU = SFX_WS_PUNROLL;
     auto tmp_of = [&](int c) -> double* { return pd + (size_t)c * W::PD; };
     auto tab_of = [&](int c) -> double* { return pd + (size_t)c * W::PD + W::TMPD; };
     int j = 0;
@@ -192,16 +250,26 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
       if (j > 0) ws_wait(empty, (uint32_t)((j - 1) & 1), cap, abort_word, a.status);
       for (int c = pt; c < cb; c += NPT) bad[c] = 0;
       named_sync(1, NPT);  // also: the 2D tables of every cell are complete
-      for (int i = pt; i < cb * N3; i += NPT) {
-        const int c = i / N3, qp = i - c * N3;
-        float kk[6], wsm = 0.f;
-        const double S = mixed_point_factors<N, LAP, MAS>(tab_of(c), xq, wq, qp, alpha, beta, kk, &wsm);
-        if (!positive_finite(S)) bad[c] = 1;
-        if (LAP) {
+      // PU points per thread per step: independent dependency chains for the
+      // latency-bound FP64 / conversion sequence of each point
+      for (int i0 = pt; i0 < cb * N3; i0 += PU * NPT) {
 #pragma unroll
-          for (int q = 0; q < 6; ++q) kf[((size_t)q * cb + c) * N3 + qp] = kk[q];
+        for (int u = 0; u < PU; ++u) {
+          const int i = i0 + u * NPT;
+          if (i < cb * N3) {
+            const int c = i / N3, qp = i - c * N3;
+            float kk[6], wsm = 0.f;
+            double t = 0.0;
+            const double S = ws_point_factors<N, LAP, MAS>(tab_of(c), xq, wq, qp, alpha, beta, kk, &t, &wsm);
+            if (!positive_finite(S)) bad[c] = 1;
+            if (LAP) {
+#pragma unroll
+              for (int q = 0; q < 6; ++q) kf[((size_t)q * cb + c) * N3 + qp] = kk[q];
+              td[(size_t)c * N3 + qp] = t;
+            }
+            if (MAS) kf[((size_t)(LAP ? 6 : 0) * cb + c) * N3 + qp] = wsm;
+          }
         }
-        if (MAS) kf[((size_t)(LAP ? 6 : 0) * cb + c) * N3 + qp] = wsm;
       }
       mbar_arrive(full);
     }
@@ -225,7 +293,7 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
 #pragma unroll 1
       for (int r = 0; r < a.nrhs; ++r) {
         // gather: G independent (map, x) load pairs per thread in flight; the
-        // map entries are kept in shared memory for the scatter
+        // map entries are kept in shared memory for the scatter (CMAP)
         for (int i0 = ct; i0 < tot; i0 += G * NCT) {
           int dof[G];
 #pragma unroll
@@ -233,7 +301,8 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
             const int i = i0 + g * NCT;
             const int c = i / N3;
             const int cell = i < tot ? ccid[c] : -1;
-            dof[g] = cell >= 0 ? (r == 0 ? __ldg(&a.map[(int64_t)cell * N3 + (i - c * N3)]) : cmap[i]) : -1;
+            dof[g] = cell >= 0 ? ((r == 0 || !W::CMAP) ? __ldg(&a.map[(int64_t)cell * N3 + (i - c * N3)]) : cmap[i])
+                               : -1;
           }
           double xv[G];
 #pragma unroll
@@ -243,7 +312,7 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
             const int i = i0 + g * NCT;
             if (i < tot) {
               U[i] = d2f_int(xv[g]);
-              if (r == 0) cmap[i] = dof[g];
+              if (W::CMAP && r == 0) cmap[i] = dof[g];
             }
           }
         }
@@ -268,10 +337,16 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
           const int c = i / N3, qp = i - c * N3;
           const float* kc = kf + (size_t)c * N3 + qp;
           const size_t ks = (size_t)cb * N3;
+          // flux t (R R^T) g: the row products D = R R^T in FP32, the scaling
+          // by t = alpha w / S in FP64
           const float g0 = G0[i], g1 = G1[i], g2 = G2[i];
-          G0[i] = kc[0] * g0 + kc[3 * ks] * g1 + kc[4 * ks] * g2;
-          G1[i] = kc[3 * ks] * g0 + kc[ks] * g1 + kc[5 * ks] * g2;
-          G2[i] = kc[4 * ks] * g0 + kc[5 * ks] * g1 + kc[2 * ks] * g2;
+          const double t = td[(size_t)c * N3 + qp];
+          const float v0 = kc[0] * g0 + kc[3 * ks] * g1 + kc[4 * ks] * g2;
+          const float v1 = kc[3 * ks] * g0 + kc[ks] * g1 + kc[5 * ks] * g2;
+          const float v2 = kc[4 * ks] * g0 + kc[5 * ks] * g1 + kc[2 * ks] * g2;
+          G0[i] = d2f_int(t * f2d_int(v0));
+          G1[i] = d2f_int(t * f2d_int(v1));
+          G2[i] = d2f_int(t * f2d_int(v2));
           if (MAS) U[i] = kc[6 * ks] * U[i];
         }
         if (r == a.nrhs - 1) mbar_arrive(empty);
@@ -300,7 +375,8 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
             a.y[(slot * N3 + l) * a.nrhs + r] = ok ? f2d_int(U[i]) : 0.0;
           } else if (ok) {
             // L2 reduction (red.global.add.f64); cells of one launch share no dof
-            atomicAdd(&a.y[(int64_t)cmap[i] * a.nrhs + r], f2d_int(U[i]));
+            const int dof = W::CMAP ? cmap[i] : __ldg(&a.map[(int64_t)cell * N3 + l]);
+            atomicAdd(&a.y[(int64_t)dof * a.nrhs + r], f2d_int(U[i]));
           }
         }
         if (r == 0)
@@ -318,13 +394,13 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, 2)
 // kernel covers.
 template <int N, bool DQ, int FORM, int PREC>
 int launch_ws_one(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
-  constexpr int NPW = 4, NCW = 8;
+  constexpr int NPW = SFX_WS_NPW, NCW = SFX_WS_NCW;
   using W = WsShape<N, FORM, NPW, NCW>;
-  const size_t max_smem = 227 * 1024, two_per_sm = 113 * 1024;
+  const size_t max_smem = 227 * 1024, per_cta = (228 * 1024) / SFX_WS_CTAS - 1024;
   int cb = tuned_cells_per_cta(SFX_TUNE_SCALAR_MIXED_WS, N - 1, 0);
   if (cb <= 0) {
     cb = 1;
-    while (cb < 32 && W::bytes(cb + 1) <= two_per_sm) ++cb;
+    while (cb < 32 && W::bytes(cb + 1) <= per_cta) ++cb;
   }
   while (cb > 1 && W::bytes(cb) > max_smem) --cb;
   const size_t smem = W::bytes(cb);

@@ -253,8 +253,12 @@ constexpr int kBuiltinCells[SFX_TUNE_NKERNEL][kMaxDeg + 1] = {
     {0, 8, 6, 6, 6, 3, 3, 3, 3},    // split precision, stored factors
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision hyperelastic residual
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // warp-specialised split precision (launcher default)
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},    // p-adaptive batch tiles (the layout's full count)
 };
-int g_ws[kMaxDeg + 1] = {0, 0, 0, 1, 1, 1, 1, 1, 1};  // by degree; needs n = p + 1 >= 4
+// by degree (needs n = p + 1 >= 4): on where it measured faster than the
+// one-role kernel on the 64^3 Laplace and Helmholtz actions (p = 4, 5, 6, 8:
+// 4-14% on Q_p); at p = 3 and 7 the two are within a few per cent either way
+int g_ws[kMaxDeg + 1] = {0, 0, 0, 0, 1, 1, 1, 0, 1};
 uint32_t g_wait_cap = 1u << 21;
 }
 namespace sfx {

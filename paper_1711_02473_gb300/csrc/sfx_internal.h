@@ -199,7 +199,8 @@ enum {
   SFX_TUNE_SCALAR_MIXED_STORED = 2,
   SFX_TUNE_ELASTIC_MIXED = 3,
   SFX_TUNE_SCALAR_MIXED_WS = 4,
-  SFX_TUNE_NKERNEL = 5
+  SFX_TUNE_BATCHED = 5,  // cells per tile of the persistent p-adaptive batch (at most its layout's count)
+  SFX_TUNE_NKERNEL = 6
 };
 int tuned_cells_per_cta(int kernel, int degree, int fallback);
 // Warp-specialised split-precision scalar action on (1) or off (0) by degree.

@@ -28,3 +28,27 @@ def test_candidates_are_valid_team_counts():
         fp = autotune.candidates("fp64", p)
         assert fp and all(1 <= c <= max(1, 256 // n2) for c in fp)
         assert all(1 <= c <= 32 for c in autotune.candidates("mixed", p))
+
+
+def test_warp_specialised_candidates_and_switch():
+    """The warp-specialised kind has candidates only at p >= 3 (its kernel needs
+    n >= 4), -1 among them (switch it off for that degree); applying a table
+    entry sets the library's switch and cells per batch (host-only calls)."""
+    import paper_1711_02473_gb300 as sfx
+    for p in range(1, 9):
+        c = autotune.candidates("mixed_ws", p)
+        assert (c == []) == (p < 3)
+        if c:
+            assert -1 in c and all(v == -1 or 1 <= v <= 32 for v in c)
+    try:
+        autotune.set_value("mixed_ws", 5, -1)
+        assert not sfx.sfx_tune_get_warp_specialised(5)
+        autotune.set_value("mixed_ws", 5, 3)
+        assert sfx.sfx_tune_get_warp_specialised(5) and sfx.sfx_tune_get_cells_per_cta("mixed_ws", 5) == 3
+        autotune.set_value("mixed_ws", 2, 3)  # no kernel at p = 2: ignored
+        assert not sfx.sfx_tune_get_warp_specialised(2)
+        with __import__("pytest").raises(sfx.SfxError):
+            sfx.sfx_tune_set_warp_specialised(2, True)
+    finally:
+        sfx.sfx_tune_set_warp_specialised(5, True)
+        sfx.sfx_tune_set_cells_per_cta("mixed_ws", 5, 0)

@@ -18,6 +18,9 @@ def test_cells_per_cta_bitwise(gpu, kind, prec, stored, p):
     q = sfx.QData(ctx, sp, "fp32") if stored else None
     x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2)).cuda()
     outs = []
+    ws = p >= 3 and sfx.sfx_tune_get_warp_specialised(p)
+    if ws and kind == "mixed":
+        sfx.sfx_tune_set_warp_specialised(p, False)  # the one-role kernel whose knob this is
     try:
         for cb in (1, 2, 3, 5, 16):
             sfx.sfx_tune_set_cells_per_cta(kind, p, cb)
@@ -29,8 +32,62 @@ def test_cells_per_cta_bitwise(gpu, kind, prec, stored, p):
             outs.append(y)
     finally:
         sfx.sfx_tune_set_cells_per_cta(kind, p, 0)
+        if ws:
+            sfx.sfx_tune_set_warp_specialised(p, True)
     for y in outs[1:]:
         assert torch.equal(outs[0], y)
+
+
+@pytest.mark.parametrize("p", [4, 8])
+@pytest.mark.parametrize("form", ["laplace", "helmholtz"])
+def test_ws_cells_per_batch_bitwise(gpu, p, form):
+    """Warp-specialised kernel: cells per batch (and so the persistent grid's
+    batch count and the contraction tiles' cell mix) change nothing."""
+    sfx, torch, ctx = gpu
+    sp = sfx.Space(sfx.Mesh.box(ctx, 9, 7, 6), "Q", p)
+    x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2)).cuda()
+    old = sfx.sfx_tune_get_warp_specialised(p)
+    sfx.sfx_tune_set_warp_specialised(p, True)
+    outs = []
+    try:
+        for cb in (1, 2, 3, 0):
+            sfx.sfx_tune_set_cells_per_cta("mixed_ws", p, cb)
+            y = torch.empty_like(x)
+            sfx.sfx_assemble_action(ctx, form, sp, x, y, precision="tf32x3")
+            outs.append(y)
+    finally:
+        sfx.sfx_tune_set_cells_per_cta("mixed_ws", p, 0)
+        sfx.sfx_tune_set_warp_specialised(p, old)
+    assert ctx.sync_status() == 0
+    for y in outs[1:]:
+        assert torch.equal(outs[0], y)
+
+
+def test_batched_tile_sizes_bitwise(gpu):
+    """The persistent p-adaptive batch: cells per tile (tuned per degree,
+    clamped to the layout's count) change nothing."""
+    sfx, torch, ctx = gpu
+    dims = (6, 5, 7)
+    mesh = sfx.Mesh.box(ctx, *dims)
+    deg = inputs.padaptive_degrees(int(np.prod(dims)), 8, seed=2)
+    outs, ntiles = [], []
+    try:
+        for cb in (1, 3, 1000, 0):
+            for p in range(1, 9):
+                sfx.sfx_tune_set_cells_per_cta("batched", p, min(cb, 64))
+            plan = sfx.Plan(ctx, mesh, deg, ["laplace", "mass"], nrhs=2)
+            x = torch.from_numpy(inputs.random_vector(plan.ndof * 2, 1, seed=3)).cuda()
+            ys = [torch.empty_like(x) for _ in range(2)]
+            plan.execute(x, ys)
+            outs.append(ys)
+            ntiles.append(plan.ntiles)
+    finally:
+        for p in range(1, 9):
+            sfx.sfx_tune_set_cells_per_cta("batched", p, 0)
+    assert ctx.sync_status() == 0
+    assert ntiles[0] > ntiles[1] >= ntiles[2] == ntiles[3]
+    for ys in outs[1:]:
+        assert torch.equal(outs[0][0], ys[0]) and torch.equal(outs[0][1], ys[1])
 
 
 def test_autotune_small(gpu):
