@@ -398,8 +398,12 @@ def main():
     else:
         ops = mixed_fp64_ops_per_cell(fam, p, form) * mesh_cells
         achieved = ops / (dom["ms"] * 1e-3) / 1e9
-        tpc = NCU_DRAM_BYTES_PER_CELL.get(("k_action_scalar_mixed", fam, p, form)) if ":" not in prec else None
-        roofline = {"bound": "alu", "kernel": "k_action_scalar_mixed %s p=%d %s %s" % (fam, p, form, prec),
+        # which kernel ran the dominant case: the warp-specialised one (Laplace part, geometry in the
+        # kernel, switched on for this degree) or the one-role one
+        kname = ("k_action_scalar_mixed_ws" if ":" not in prec and form != "mass" and p >= 3
+                 and sfx.sfx_tune_get_warp_specialised(p) else "k_action_scalar_mixed")
+        tpc = NCU_DRAM_BYTES_PER_CELL.get((kname, fam, p, form)) if ":" not in prec else None
+        roofline = {"bound": "alu", "kernel": "%s %s p=%d %s %s" % (kname, fam, p, form, prec),
                     "achieved": round(achieved, 2), "peak": round(FP64_PEAK_GOPS, 1), "unit": "G FP64 op/s",
                     "frac": round(achieved / FP64_PEAK_GOPS, 4),
                     "dfma_probe": probes["dfma"]["rate"],
