@@ -1,5 +1,6 @@
 // k_scalar_mixed_bf16.cu -- BF16x3 instantiation of the split-precision scalar
-// actions (body in scalar_mixed_body.cuh).
+// actions (body in scalar_mixed_body.cuh).  The two formats are separate
+// translation units so that the build compiles them in parallel.
 #include "scalar_mixed_body.cuh"
 
 namespace sfx {

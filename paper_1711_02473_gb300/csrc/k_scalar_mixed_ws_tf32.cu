@@ -1,5 +1,6 @@
 // k_scalar_mixed_ws_tf32.cu -- TF32x3 instantiation of the warp-specialised
-// split-precision scalar action (body in scalar_mixed_ws.cuh).
+// split-precision scalar action (body in scalar_mixed_ws.cuh); one translation
+// unit per format so that the build compiles them in parallel.
 #include "scalar_mixed_ws.cuh"
 
 namespace sfx {
