@@ -41,7 +41,8 @@ METRIC = "DoFs/s for sum-factorised action (mixed vs FP64, same GB300, stated er
 # coordinates are per cell).
 NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_mixed", "Q", 8, "laplace"): (94.201856e6 + 4.166144e6) / 4096,
                            ("k_action_scalar_mixed", "Q", 8, "helmholtz"): (94.149376e6 + 3.642880e6) / 4096,
-                           ("k_action_scalar_fp64", "Q", 8, "laplace"): (94.203392e6 + 5.303552e6) / 4096}
+                           ("k_action_scalar_fp64", "Q", 8, "laplace"): (94.203392e6 + 5.303552e6) / 4096,
+                           ("k_action_scalar_mixed_ws", "Q", 8, "helmholtz"): (93.751040e6 + 4.130816e6) / 4096}
 
 
 def parse():
@@ -365,6 +366,8 @@ def main():
                         for pr in precs} - {"fp64"} | ({"fp64"} if any(pr.startswith("fp64") for pr in precs) else set()))
         if "mixed" in kinds:
             kinds = kinds + ["mixed_ws"]  # after "mixed": the warp-specialised kernel or the one-role one, per degree
+        if not args.no_extras:
+            kinds = kinds + ["batched"]  # tiles per degree of the p-adaptive batch (config-5 workload)
         degrees = sorted({p for _, p, _ in wl})
         tuning = autotune.ensure(ctx, torch.cuda.get_device_name(local), degrees=degrees, kinds=kinds)
     probes = probe_rates(sfx, torch)
@@ -778,7 +781,8 @@ def extra_padaptive(sfx, torch, ctx, inputs, flush, stream):
         "graph_dofs_per_s": work / (tg * 1e-3), "per_launch_dofs_per_s": work / (tl * 1e-3),
         "speedup_graph_vs_per_launch": tl / tg, "launches_graph": 1, "launches_per_launch": ndeg * R * len(forms),
         "roofline": {"bound": "alu", "achieved": round(fl / (tg * 1e-3) / 1e9, 2), "peak": round(FP64_PEAK_GOPS, 1),
-                     "unit": "G FP64 op/s", "frac": round(fl / (tg * 1e-3) / 1e9 / FP64_PEAK_GOPS, 4)}}
+                     "unit": "G FP64 op/s", "frac": round(fl / (tg * 1e-3) / 1e9 / FP64_PEAK_GOPS, 4)},
+        "tile_cells_tuned": {str(p): sfx.sfx_tune_get_cells_per_cta("batched", p) for p in range(1, 9)}}
     del xd, ys, plan, mesh
     return out
 

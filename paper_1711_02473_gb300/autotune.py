@@ -30,7 +30,7 @@ def candidates(kind, p):
     if kind == "mixed_ws":
         return [-1, 1, 2, 3, 4, 6, 8] if p >= 3 else []
     if kind == "batched":
-        return [1, 2, 3, 4, 6, 8, 12, 16, 24, 32]
+        return [1, 2, 4, 8, 16, 32]
     return [2, 4, 6, 8, 12, 16, 24, 32] if p <= 2 else [1, 2, 3, 4, 6, 8, 12, 16]
 
 
