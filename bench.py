@@ -367,7 +367,9 @@ def main():
         if "mixed" in kinds:
             kinds = kinds + ["mixed_ws"]  # after "mixed": the warp-specialised kernel or the one-role one, per degree
         if not args.no_extras:
-            kinds = kinds + ["batched"]  # tiles per degree of the p-adaptive batch (config-5 workload)
+            # the other workloads' kernels: tiles of the p-adaptive batch (config 5), cells per CTA of the
+            # H(div)/H(curl) and hyperelastic kernels (config 3 and the linearised operator)
+            kinds = kinds + ["batched", "hdivcurl", "elastic", "linearised", "linearised_mixed"]
         degrees = sorted({p for _, p, _ in wl})
         tuning = autotune.ensure(ctx, torch.cuda.get_device_name(local), degrees=degrees, kinds=kinds)
     probes = probe_rates(sfx, torch)

@@ -387,7 +387,13 @@ sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_for
 sfx_status sfx_tune_set_cells_per_cta(int kernel, int degree, int cells);
 sfx_status sfx_tune_get_cells_per_cta(int kernel, int degree, int* cells);
 
-/* Kind 5 of the table above: cells per tile of the persistent p-adaptive
+/* Kinds 6-9 of the table above: cells per CTA of the FP64 NCF / NCE actions
+ * (6), the FP64 hyperelastic residual (7), the FP64 linearised hyperelastic
+ * action (8) and its split-precision version (9); 0 = the launcher's rule
+ * (the most cells for which two CTAs share an SM, else one larger CTA), and a
+ * value that would not fit the kernel's team limit or shared memory is
+ * reduced until it does.
+ * Kind 5: cells per tile of the persistent p-adaptive
  * batch (sfx_plan_create_padaptive, sfx_padaptive_action_noalloc), at most the
  * count the kernel's shared-memory layout holds for that degree (larger values
  * are clamped); 0 = that count.  Takes effect for plans created afterwards.

@@ -1,6 +1,7 @@
 """Autotuner for the cells-per-CTA of the scalar action kernels.
 
-For each kernel kind ("fp64", "mixed", "mixed_stored", "mixed_ws") and degree it times
+For each kernel kind ("fp64", "mixed", "mixed_stored", "mixed_ws", "batched", and the
+structured-element kinds "hdivcurl", "elastic", "linearised", "linearised_mixed") and degree it times
 the Q_p Laplace action on a tuning mesh for every candidate value (median of a
 few CUDA-event timings, L2 flushed between runs), keeps the fastest, and sets
 it in the library with sfx_tune_set_cells_per_cta.  For "mixed_ws" (the
@@ -31,6 +32,11 @@ def candidates(kind, p):
         return [-1, 1, 2, 3, 4, 6, 8] if p >= 3 else []
     if kind == "batched":
         return [1, 2, 4, 8, 16, 32]
+    if kind in ("hdivcurl", "elastic", "linearised"):  # teams of (p+1)^2 threads, at most 256 threads
+        top = max(1, 256 // n2)
+        return sorted({c for c in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64) if c <= top})
+    if kind == "linearised_mixed":
+        return [1, 2, 4, 8, 16]
     return [2, 4, 6, 8, 12, 16, 24, 32] if p <= 2 else [1, 2, 3, 4, 6, 8, 12, 16]
 
 
@@ -68,6 +74,9 @@ def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims
     if "batched" in kinds:
         table["batched"] = tune_batched(ctx, degrees, torch, flush, reps)
         kinds = [k for k in kinds if k != "batched"]
+    for k in [k for k in kinds if k in STRUCTURED]:
+        table[k] = tune_structured(ctx, k, degrees, torch, flush, reps)
+    kinds = [k for k in kinds if k not in STRUCTURED]
     for p in degrees:
         if not kinds:
             break
@@ -100,6 +109,43 @@ def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims
             qd.close()
         del x, y, sp
     return table
+
+
+# kind -> (family, forms timed, precision, degrees it has, tuning mesh)
+STRUCTURED = {"hdivcurl": ("NCF", ("ncf_mass_divdiv",), "fp64", range(1, 9), (16, 16, 16)),
+              "elastic": ("VQ", ("neohooke",), "fp64", range(1, 9), (12, 12, 12)),
+              "linearised": ("VQ", ("svk",), "fp64", range(1, 9), (12, 12, 12)),
+              "linearised_mixed": ("VQ", ("svk",), "tf32x3", range(1, 9), (12, 12, 12))}
+
+
+def tune_structured(ctx, kind, degrees, torch, flush, reps):
+    """Cells per CTA of the NCF / NCE and hyperelastic kernels, per degree
+    (NCF and NCE share the H(div)/H(curl) kernel's table; the NCF action is
+    timed)."""
+    from . import sfx_assemble_linearised_action
+    fam, forms, prec, ps, dims = STRUCTURED[kind]
+    mesh = Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    out = {}
+    for p in degrees:
+        if p not in ps:
+            continue
+        sp = Space(mesh, fam, p)
+        x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1) * (0.01 if fam == "VQ" else 1.0)).cuda()
+        d = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2)).cuda()
+        y = torch.empty_like(x)
+        if kind.startswith("linearised"):
+            fn = lambda: sfx_assemble_linearised_action(ctx, forms[0], sp, x, d, y, precision=prec)
+        else:
+            fn = lambda: sfx_assemble_action(ctx, forms[0], sp, x, y, precision=prec)
+        res = {}
+        for cb in candidates(kind, p):
+            sfx_tune_set_cells_per_cta(kind, p, cb)
+            res[cb] = _time(torch, fn, reps, flush)
+        best = min(res, key=res.get)
+        sfx_tune_set_cells_per_cta(kind, p, best)
+        out[p] = {"best": best, "ms": {str(k): round(v, 4) for k, v in res.items()}}
+        del x, d, y, sp
+    return out
 
 
 def tune_batched(ctx, degrees, torch, flush, reps, dims=(20, 20, 20), nrhs=4):

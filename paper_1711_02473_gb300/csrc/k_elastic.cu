@@ -157,6 +157,7 @@ int launch_e(const ActArgs& a, int64_t nc, int64_t nds, cudaStream_t s) {
     cb = Sh::MAXCB;
     while (cb > 1 && fixed + cb * per_team > 200 * 1024) --cb;
   }
+  cb = tuned_team_cells(SFX_TUNE_ELASTIC, N - 1, cb, Sh::MAXCB, fixed, per_team, 200 * 1024);
   const size_t smem = fixed + cb * per_team;
   auto kern = k_residual_elastic_fp64<N, NEO>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

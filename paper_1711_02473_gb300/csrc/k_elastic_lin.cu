@@ -340,6 +340,7 @@ int launch_l(const ActArgs& a, int64_t nc, cudaStream_t s) {
   // two CTAs per SM (110 KB each), even at one cell per CTA (measured faster
   // at Q_6 than one CTA of two cells)
   while (cb > 1 && fixed + cb * per_team > 110 * 1024) --cb;
+  if (!mat) cb = tuned_team_cells(SFX_TUNE_LINEARISED, N - 1, cb, Sh::MAXCB, fixed, per_team, 200 * 1024);
   const size_t smem = fixed + cb * per_team;
   auto kern = k_linearised_elastic_fp64<N, NEO>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

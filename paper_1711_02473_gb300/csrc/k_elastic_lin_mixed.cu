@@ -204,6 +204,8 @@ int launch_lm(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   const size_t budget = 110 * 1024;  // two CTAs per SM
   int cb = (N <= 3) ? 16 : 8;
   while (cb > 1 && Sh::bytes(cb) > budget) --cb;
+  cb = tuned_team_cells(SFX_TUNE_LINEARISED_MIXED, N - 1, cb, 64, Sh::bytes(0), Sh::bytes(1) - Sh::bytes(0),
+                        200 * 1024);
   const size_t smem = Sh::bytes(cb);
   if (smem > 227 * 1024) return -1;
   auto kern = k_linearised_elastic_mixed<N, NEO, PREC>;

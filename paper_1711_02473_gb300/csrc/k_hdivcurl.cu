@@ -355,6 +355,7 @@ int launch_h(const ActArgs& a, int64_t nc, cudaStream_t s) {
     cb = Sh::MAXCB;
     while (cb > 1 && fixed + cb * per_team > 200 * 1024) --cb;
   }
+  cb = tuned_team_cells(SFX_TUNE_HDIVCURL, P, cb, Sh::MAXCB, fixed, per_team, 200 * 1024);
   const size_t smem = fixed + cb * per_team;
   auto kern = k_action_hdivcurl_fp64<P, NCF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

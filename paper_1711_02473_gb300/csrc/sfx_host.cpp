@@ -254,6 +254,10 @@ constexpr int kBuiltinCells[SFX_TUNE_NKERNEL][kMaxDeg + 1] = {
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision hyperelastic residual
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // warp-specialised split precision (launcher default)
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // p-adaptive batch tiles (the layout's full count)
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},    // FP64 NCF / NCE actions (launcher's shared-memory rule)
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},    // FP64 hyperelastic residual (same)
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},    // FP64 linearised hyperelastic action (same)
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision linearised hyperelastic action (same)
 };
 // by degree (needs n = p + 1 >= 4): on where it measured faster than the
 // one-role kernel on the 64^3 Laplace and Helmholtz actions (p = 4, 5, 6, 8:
@@ -264,6 +268,13 @@ uint32_t g_wait_cap = 1u << 21;
 namespace sfx {
 bool ws_enabled(int degree) { return degree >= 3 && degree <= kMaxDeg && g_ws[degree] != 0; }
 uint32_t ws_wait_cap() { return g_wait_cap; }
+int tuned_team_cells(int kernel, int degree, int fallback, int maxcb, size_t fixed, size_t per_cell, size_t limit) {
+  const int t = kernel >= 0 && kernel < SFX_TUNE_NKERNEL && degree >= 1 && degree <= kMaxDeg ? g_tune[kernel][degree] : 0;
+  if (t <= 0) return fallback;
+  int cb = t < maxcb ? t : maxcb;
+  while (cb > 1 && fixed + (size_t)cb * per_cell > limit) --cb;
+  return cb;
+}
 int tuned_cells_per_cta(int kernel, int degree, int fallback) {
   if (kernel < 0 || kernel >= SFX_TUNE_NKERNEL || degree < 1 || degree > kMaxDeg) return fallback;
   if (g_tune[kernel][degree] > 0) return g_tune[kernel][degree];

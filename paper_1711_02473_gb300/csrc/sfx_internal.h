@@ -200,8 +200,16 @@ enum {
   SFX_TUNE_ELASTIC_MIXED = 3,
   SFX_TUNE_SCALAR_MIXED_WS = 4,
   SFX_TUNE_BATCHED = 5,  // cells per tile of the persistent p-adaptive batch (at most its layout's count)
-  SFX_TUNE_NKERNEL = 6
+  SFX_TUNE_HDIVCURL = 6,         // FP64 NCF / NCE actions
+  SFX_TUNE_ELASTIC = 7,          // FP64 hyperelastic residual
+  SFX_TUNE_LINEARISED = 8,       // FP64 linearised hyperelastic action
+  SFX_TUNE_LINEARISED_MIXED = 9, // split-precision linearised hyperelastic action
+  SFX_TUNE_NKERNEL = 10
 };
+// Tuned cells per CTA for the team-per-cell kernels: the tuned value if one
+// is set (at most maxcb, and reduced until the shared memory fits `limit`),
+// else `fallback`.
+int tuned_team_cells(int kernel, int degree, int fallback, int maxcb, size_t fixed, size_t per_cell, size_t limit);
 int tuned_cells_per_cta(int kernel, int degree, int fallback);
 // Warp-specialised split-precision scalar action on (1) or off (0) by degree.
 bool ws_enabled(int degree);

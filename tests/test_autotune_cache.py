@@ -52,3 +52,12 @@ def test_warp_specialised_candidates_and_switch():
     finally:
         sfx.sfx_tune_set_warp_specialised(5, True)
         sfx.sfx_tune_set_cells_per_cta("mixed_ws", 5, 0)
+
+
+def test_structured_candidates_fit_the_team_limit():
+    for kind in ("hdivcurl", "elastic", "linearised"):
+        for p in range(1, 9):
+            c = autotune.candidates(kind, p)
+            assert c and all(1 <= v <= max(1, 256 // (p + 1) ** 2) for v in c)
+    assert all(1 <= v <= 64 for v in autotune.candidates("linearised_mixed", 4))
+    assert set(autotune.STRUCTURED) == {"hdivcurl", "elastic", "linearised", "linearised_mixed"}

@@ -102,3 +102,33 @@ def test_autotune_small(gpu):
     finally:
         for kind in ("fp64", "mixed"):
             sfx.sfx_tune_set_cells_per_cta(kind, 2, 0)
+
+
+@pytest.mark.parametrize("kind,fam,form,prec", [("hdivcurl", "NCF", "ncf_mass_divdiv", "fp64"),
+                                               ("hdivcurl", "NCE", "nce_curlcurl", "fp64"),
+                                               ("elastic", "VQ", "neohooke", "fp64"),
+                                               ("linearised", "VQ", "svk", "fp64"),
+                                               ("linearised_mixed", "VQ", "neohooke", "tf32x3")])
+@pytest.mark.parametrize("p", [1, 3])
+def test_structured_cells_per_cta_bitwise(gpu, kind, fam, form, prec, p):
+    """H(div)/H(curl) and hyperelastic kernels: cells per CTA (tuned, clamped
+    to the team limit and shared memory) change nothing."""
+    sfx, torch, ctx = gpu
+    sp = sfx.Space(sfx.Mesh.box(ctx, 5, 4, 3), fam, p)
+    x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2) * (0.01 if fam == "VQ" else 1.0)).cuda()
+    d = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=3)).cuda()
+    outs = []
+    try:
+        for cb in (1, 2, 3, 64, 0):
+            sfx.sfx_tune_set_cells_per_cta(kind, p, cb)
+            y = torch.empty_like(x)
+            if kind.startswith("linearised"):
+                sfx.sfx_assemble_linearised_action(ctx, form, sp, x, d, y, precision=prec)
+            else:
+                sfx.sfx_assemble_action(ctx, form, sp, x, y, precision=prec)
+            outs.append(y)
+    finally:
+        sfx.sfx_tune_set_cells_per_cta(kind, p, 0)
+    assert ctx.sync_status() == 0
+    for y in outs[1:]:
+        assert torch.equal(outs[0], y)
