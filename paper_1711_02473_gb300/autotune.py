@@ -130,7 +130,9 @@ def tune_structured(ctx, kind, degrees, torch, flush, reps):
         if p not in ps:
             continue
         sp = Space(mesh, fam, p)
-        x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1) * (0.01 if fam == "VQ" else 1.0)).cuda()
+        # a displacement small enough that det F > 0 everywhere (the residual's recipe)
+        x = torch.from_numpy(inputs.displacement(sp.ndof, p, dims[0], seed=1) if fam == "VQ"
+                             else inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
         d = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2)).cuda()
         y = torch.empty_like(x)
         if kind.startswith("linearised"):
@@ -145,6 +147,8 @@ def tune_structured(ctx, kind, degrees, torch, flush, reps):
         sfx_tune_set_cells_per_cta(kind, p, best)
         out[p] = {"best": best, "ms": {str(k): round(v, 4) for k, v in res.items()}}
         del x, d, y, sp
+    if ctx.sync_status() != 0:
+        raise RuntimeError("device status flagged while tuning " + kind)
     return out
 
 

@@ -104,6 +104,23 @@ def test_autotune_small(gpu):
             sfx.sfx_tune_set_cells_per_cta(kind, 2, 0)
 
 
+def test_autotune_other_kinds_small(gpu):
+    """Every other kind tunes without flagging the device status (the
+    hyperelastic states keep det F > 0) and sets one of its candidates."""
+    sfx, torch, ctx = gpu
+    from paper_1711_02473_gb300 import autotune
+    kinds = ("hdivcurl", "elastic", "linearised", "linearised_mixed", "batched", "mixed", "mixed_ws")
+    try:
+        table = autotune.tune(ctx, degrees=[3], kinds=kinds, dims=(8, 8, 8), reps=1)
+        assert ctx.sync_status() == 0
+        for kind in kinds:
+            assert table[kind][3]["best"] in autotune.candidates(kind, 3), kind
+    finally:
+        for kind in kinds:
+            autotune.set_value(kind, 3, 0)
+        sfx.sfx_tune_set_warp_specialised(3, False)
+
+
 @pytest.mark.parametrize("kind,fam,form,prec", [("hdivcurl", "NCF", "ncf_mass_divdiv", "fp64"),
                                                ("hdivcurl", "NCE", "nce_curlcurl", "fp64"),
                                                ("elastic", "VQ", "neohooke", "fp64"),
@@ -115,7 +132,8 @@ def test_structured_cells_per_cta_bitwise(gpu, kind, fam, form, prec, p):
     to the team limit and shared memory) change nothing."""
     sfx, torch, ctx = gpu
     sp = sfx.Space(sfx.Mesh.box(ctx, 5, 4, 3), fam, p)
-    x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2) * (0.01 if fam == "VQ" else 1.0)).cuda()
+    x = torch.from_numpy(inputs.displacement(sp.ndof, p, 5, seed=2) if fam == "VQ"
+                         else inputs.random_vector(sp.ndof, 1, seed=2)).cuda()
     d = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=3)).cuda()
     outs = []
     try:
