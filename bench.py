@@ -369,7 +369,7 @@ def main():
         if not args.no_extras:
             # the other workloads' kernels: tiles of the p-adaptive batch (config 5), cells per CTA of the
             # H(div)/H(curl) and hyperelastic kernels (config 3 and the linearised operator)
-            kinds = kinds + ["batched", "hdivcurl", "elastic", "linearised", "linearised_mixed"]
+            kinds = kinds + ["batched", "hdivcurl", "elastic", "linearised", "linearised_mixed", "hdivcurl_mixed"]
         degrees = sorted({p for _, p, _ in wl})
         tuning = autotune.ensure(ctx, torch.cuda.get_device_name(local), degrees=degrees, kinds=kinds)
     probes = probe_rates(sfx, torch)
@@ -717,6 +717,48 @@ def extra_structured(sfx, torch, ctx, inputs, flush, stream):
     return {"rows": rows, "device_status": ctx.sync_status()}
 
 
+def extra_hdivcurl_mixed(sfx, torch, ctx, inputs, flush, stream):
+    """NCF_p mass + div-div and NCE_p curl-curl on 32^3, p = 1..6 (the
+    structured-element configuration): FP64, TF32x3 and BF16x3 (split-precision
+    contractions on the tensor cores, FP64 geometry and scaling), each with its
+    speed-up over FP64 and its error against the oracle on six sampled cells
+    (first, last and four seeded) and against the FP64 GPU action."""
+    import oracle as orc
+    rows = []
+    dims = _d(32, 32, 32)
+    mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    X = mesh.coords()
+    rng = np.random.default_rng(19)
+    for fam, form in (("NCF", "ncf_mass_divdiv"), ("NCE", "nce_curlcurl")):
+        for p in _ps(range(1, 7)):
+            sp = sfx.Space(mesh, fam, p)
+            x = inputs.random_vector(sp.ndof, 1, seed=1)
+            xd = torch.from_numpy(x).cuda()
+            cells = np.unique(np.concatenate([[0, sp.ncell - 1], rng.choice(sp.ncell, 4, replace=False)]))
+            ref = orc.cell_vectors(fam, form, p, dims, X, x, cells)
+            cd = torch.from_numpy(cells.astype(np.int64)).cuda()
+            row = {"family": fam, "form": form, "p": p, "mesh": "%dx%dx%d" % dims, "ndof": sp.ndof}
+            ys = {}
+            for prec in ("fp64", "tf32x3", "bf16x3"):
+                ys[prec] = torch.empty_like(xd)
+                t = _time(torch, stream, flush,
+                          lambda: sfx.sfx_assemble_action(ctx, form, sp, xd, ys[prec], precision=prec, stream=stream))
+                row[prec + "_ms"] = round(t, 4)
+                row[prec + "_dofs_per_s"] = sp.ndof / (t * 1e-3)
+                b = torch.empty(len(cells) * sp.nloc, dtype=torch.float64, device="cuda")
+                sfx.sfx_assemble_cell_vectors(ctx, form, sp, xd, cd, b, precision=prec)
+                row[prec + "_rel_err_vs_oracle_sampled"] = float(np.abs(b.cpu().numpy().reshape(ref.shape) - ref).max()
+                                                                 / np.abs(ref).max())
+                if prec != "fp64":
+                    row[prec + "_speedup_vs_fp64"] = row["fp64_ms"] / row[prec + "_ms"]
+                    row[prec + "_rel_err_vs_fp64"] = float((ys[prec] - ys["fp64"]).abs().max()
+                                                           / ys["fp64"].abs().max())
+            rows.append(row)
+            del xd, ys, sp
+    del mesh
+    return {"rows": rows, "device_status": ctx.sync_status()}
+
+
 def extra_linearised(sfx, torch, ctx, inputs, flush, stream):
     """Linearised hyperelastic operator K(u) du (the Jacobian of the residual;
     the operator whose action Sec. 4.1 times), vector Q_p on 48^3, p = 2..6,
@@ -886,6 +928,7 @@ def extra_tangent(sfx, torch, ctx, inputs, flush, stream):
 EXTRAS = {
     "structured_fp64": extra_structured,
     "linearised_hyperelastic_fp64": extra_linearised,
+    "hdivcurl_mixed_32cube": extra_hdivcurl_mixed,
     "precision_64cube": lambda *a: precision_block(*a),
     "padaptive_batched_fp64": extra_padaptive,
     "naive_vs_sumfact_Q_laplace_32cube": extra_naive,

@@ -218,10 +218,18 @@ sfx_status sfx_tabulate_1d(sfx_nodes nodes, int ndof1d, sfx_nodes qrule, int nq,
  * Sec. 3.3, Eqs. coeff_def, coeff_eval, form_eval), u_K = sum_i x_{map(K,i)} psi_i.
  *   x, y   device, ndof x nrhs doubles (x read-only; must not alias y)
  *   nrhs   1 <= nrhs <= 64
- *   accumulate = 0: y is overwritten (zeroed on `stream` first); 1: y += action.
+ *   accumulate = 0: y is overwritten (every entry written, whatever it held:
+ *   for DQ_p and the FP64 Q_p kernels each dof's first contribution is stored,
+ *   otherwise y is zeroed on `stream` first); 1: y += action.
  *   params may be NULL (defaults: Helmholtz alpha=1, beta=-1; NCF alpha=beta=1;
  *   NCE alpha=0, beta=1; hyperelastic mu=1, lambda=10).
- * The scatter is deterministic (8 colour passes for shared-dof families).
+ *   prec: FP64 for every form; TF32X3 / BF16X3 (split-precision tensor-core
+ *   contractions, FP64 geometry, scaling and scatter) for the scalar forms on
+ *   Q_p / DQ_p / vector Q_p, NCF_MASS_DIVDIV on NCF_p, NCE_CURLCURL on NCE_p
+ *   and the hyperelastic residuals.
+ * The scatter is deterministic (8 colour passes for shared-dof families; the
+ * colour launches run in stream order, each one's scatter after the previous
+ * one's has completed).
  * Errors: SFX_ERR_ARG (null, nrhs, form/family mismatch), SFX_ERR_UNSUPPORTED
  * (precision or algorithm not available for this form), SFX_ERR_CUDA. */
 sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
@@ -387,9 +395,10 @@ sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, const sfx_for
 sfx_status sfx_tune_set_cells_per_cta(int kernel, int degree, int cells);
 sfx_status sfx_tune_get_cells_per_cta(int kernel, int degree, int* cells);
 
-/* Kinds 6-9 of the table above: cells per CTA of the FP64 NCF / NCE actions
+/* Kinds 6-10 of the table above: cells per CTA of the FP64 NCF / NCE actions
  * (6), the FP64 hyperelastic residual (7), the FP64 linearised hyperelastic
- * action (8) and its split-precision version (9); 0 = the launcher's rule
+ * action (8), its split-precision version (9) and the split-precision NCF /
+ * NCE actions (10); 0 = the launcher's rule
  * (the most cells for which two CTAs share an SM, else one larger CTA), and a
  * value that would not fit the kernel's team limit or shared memory is
  * reduced until it does.

@@ -42,7 +42,7 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_csr_create", "sfx_csr_info", "sfx_csr_assemble", "sfx_csr_spmv", "sfx_csr_destroy",
            "sfx_assemble_weighted_action", "sfx_assemble_weighted_cell_matrices"]
 TUNE_KERNEL = {"fp64": 0, "mixed": 1, "mixed_stored": 2, "elastic_mixed": 3, "mixed_ws": 4, "batched": 5,
-               "hdivcurl": 6, "elastic": 7, "linearised": 8, "linearised_mixed": 9}
+               "hdivcurl": 6, "elastic": 7, "linearised": 8, "linearised_mixed": 9, "hdivcurl_mixed": 10}
 QDATA = {"fp64": 1, "fp32": 2, "both": 3}
 EXEC = {"graph": 0, "per_launch": 1}
 

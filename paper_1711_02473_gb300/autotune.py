@@ -1,7 +1,8 @@
 """Autotuner for the cells-per-CTA of the scalar action kernels.
 
 For each kernel kind ("fp64", "mixed", "mixed_stored", "mixed_ws", "batched", and the
-structured-element kinds "hdivcurl", "elastic", "linearised", "linearised_mixed") and degree it times
+structured-element kinds "hdivcurl", "elastic", "linearised", "linearised_mixed", "hdivcurl_mixed") and
+degree it times
 the Q_p Laplace action on a tuning mesh for every candidate value (median of a
 few CUDA-event timings, L2 flushed between runs), keeps the fastest, and sets
 it in the library with sfx_tune_set_cells_per_cta.  For "mixed_ws" (the
@@ -35,7 +36,7 @@ def candidates(kind, p):
     if kind in ("hdivcurl", "elastic", "linearised"):  # teams of (p+1)^2 threads, at most 256 threads
         top = max(1, 256 // n2)
         return sorted({c for c in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64) if c <= top})
-    if kind == "linearised_mixed":
+    if kind in ("linearised_mixed", "hdivcurl_mixed"):
         return [1, 2, 4, 8, 16]
     return [2, 4, 6, 8, 12, 16, 24, 32] if p <= 2 else [1, 2, 3, 4, 6, 8, 12, 16]
 
@@ -115,7 +116,8 @@ def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims
 STRUCTURED = {"hdivcurl": ("NCF", ("ncf_mass_divdiv",), "fp64", range(1, 9), (16, 16, 16)),
               "elastic": ("VQ", ("neohooke",), "fp64", range(1, 9), (12, 12, 12)),
               "linearised": ("VQ", ("svk",), "fp64", range(1, 9), (12, 12, 12)),
-              "linearised_mixed": ("VQ", ("svk",), "tf32x3", range(1, 9), (12, 12, 12))}
+              "linearised_mixed": ("VQ", ("svk",), "tf32x3", range(1, 9), (12, 12, 12)),
+              "hdivcurl_mixed": ("NCE", ("nce_curlcurl",), "tf32x3", range(1, 9), (16, 16, 16))}
 
 
 def tune_structured(ctx, kind, degrees, torch, flush, reps):

@@ -381,8 +381,13 @@ int dispatch_p(int p, const ActArgs& a, int64_t nc, cudaStream_t s) {
 
 }  // namespace
 
+int launch_action_hdivcurl_mixed_tf32(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+int launch_action_hdivcurl_mixed_bf16(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream);
+
 int launch_action_hdivcurl(const sfx_space* sp, sfx_form form, sfx_precision prec, const ActArgs& a,
                            void* stream) {
+  if (prec == SFX_PREC_TF32X3) return launch_action_hdivcurl_mixed_tf32(sp, form, a, stream);
+  if (prec == SFX_PREC_BF16X3) return launch_action_hdivcurl_mixed_bf16(sp, form, a, stream);
   if (prec != SFX_PREC_FP64) return -1;
   cudaStream_t s = (cudaStream_t)stream;
   if (sp->family == SFX_NCF && form == SFX_NCF_MASS_DIVDIV) return dispatch_p<true>(sp->p, a, sp->mesh->ncell, s);

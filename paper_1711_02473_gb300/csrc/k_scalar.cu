@@ -32,7 +32,8 @@ int launch_fp64(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int64_t grid = (a.ncells + cb - 1) / cb;
-  kern<<<(unsigned)grid, cb * Sh::N2, smem, s>>>(a, ncell_total, geo_once);
+  e = launch_kernel(kern, (unsigned)grid, cb * Sh::N2, smem, s, a.overlap_prev != 0, a, ncell_total, geo_once);
+  if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();
 }
 

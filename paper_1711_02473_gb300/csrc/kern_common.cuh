@@ -19,6 +19,46 @@ static __constant__ Tab1D c_tab[kMaxDeg + 1];
 
 __device__ __forceinline__ void set_flag(uint32_t* st, uint32_t bit) { atomicOr(st, bit); }
 
+// Programmatic dependent launch between the colour launches of one action.
+// Launch k+1 may start while launch k drains (its CTAs take the SM slots that
+// launch k's CTAs leave): the work before the scatter (gather, geometry,
+// contractions) reads only inputs that no launch of the action writes.  Each
+// thread of launch k+1 waits for launch k to complete, with its writes to y
+// visible, before its first write to y, and every CTA passes that wait before
+// it exits, so launch k+1 also completes after launch k.  In a kernel launched
+// without the attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch `k` on `s`, as a programmatic dependent of the previous launch on the
+// stream when `overlap_prev` is set (the kernel must call pdl_wait_prev before
+// its first write to y).
+template <typename... P, typename... A>
+cudaError_t launch_kernel(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                          bool overlap_prev, const A&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = overlap_prev ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// Whether (cell, l) writes its dof first in an overwriting action (ActArgs
+// first / first_all): that pair stores its value (0 for a skipped cell), every
+// later pair of the dof, in a later colour launch, adds to it.
+__device__ __forceinline__ bool first_touch(const ActArgs& a, int64_t cell, int l, int nloc) {
+  if (a.first_all) return true;
+  if (!a.first) return false;
+  const int words = (nloc + 31) >> 5;
+  return (__ldg(&a.first[cell * words + (l >> 5)]) >> (l & 31)) & 1u;
+}
+
 // Resolve the cell handled by `slot`; false if the slot is idle or the
 // caller's id is out of range (flagged).
 __device__ __forceinline__ bool slot_cell(const ActArgs& a, int64_t slot, int64_t ncell_total, int* cell) {

@@ -160,5 +160,120 @@ __device__ __forceinline__ void tc_contract(const float* in, float* out, const T
   }
 }
 
+// The same contraction on a [cells][I0][I1][I2] array whose axis AX changes
+// length, K = I_AX -> R (the anisotropic blocks of NCF_p / NCE_p, Sec. 3.5:
+// tables of the P_p factor, q x (p+1), and of the dP_{p-1} factor, q x p).
+// The fibers are the other two axes; CSI / CSO are the cell strides of in and
+// out (floats).  NEG negates the product before it is stored or added.
+template <int I0, int I1, int I2, int AX, int R, int CSI, int CSO, bool TRANS, bool ACC, bool NEG, int PREC,
+          int NT = kThreads>
+__device__ __forceinline__ void tc_contract_g(const float* in, float* out, const TabF& M, int ncell) {
+  constexpr int NW = NT / 32;
+  constexpr int K = AX == 0 ? I0 : (AX == 1 ? I1 : I2);
+  constexpr int F = I0 * I1 * I2 / K;  // fibers per cell
+  constexpr int O1 = AX == 1 ? R : I1, O2 = AX == 2 ? R : I2;
+  static_assert(K <= 16 && R <= 16, "1D tables are at most 16 x 16");
+  auto ain = [](int c, int f, int k) -> int {
+    if (AX == 0) return c * CSI + k * (I1 * I2) + f;
+    if (AX == 1) {
+      const int f0 = f / I2, f1 = f - (f / I2) * I2;
+      return c * CSI + f0 * (I1 * I2) + k * I2 + f1;
+    }
+    return c * CSI + f * I2 + k;
+  };
+  auto aout = [](int c, int f, int r) -> int {
+    if (AX == 0) return c * CSO + r * (O1 * O2) + f;
+    if (AX == 1) {
+      const int f0 = f / O2, f1 = f - (f / O2) * O2;
+      return c * CSO + f0 * (O1 * O2) + r * O2 + f1;
+    }
+    return c * CSO + f * R + r;
+  };
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int nfib = ncell * F;
+  const int ntiles = (nfib + 7) >> 3;
+  auto A = [&](int r, int k) -> float { return TRANS ? M.v[k][r] : M.v[r][k]; };
+  auto store = [&](int tile, const float* c) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = g + ((e >> 1) << 3);
+      const int fc = tile * 8 + 2 * tq + (e & 1);
+      if (r < R && fc < nfib) {
+        const int cc = fc / F, lc = fc - cc * F;
+        const int ad = aout(cc, lc, r);
+        const float v = NEG ? -c[e] : c[e];
+        out[ad] = ACC ? out[ad] + v : v;
+      }
+    }
+  };
+  if (PREC == SFX_PREC_TF32X3) {
+    constexpr int KS = (K + 7) / 8;
+    uint32_t ah[KS][4], al[KS][4];
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      const int k0 = ks * 8 + tq;
+      split_tf32(A(g, k0), ah[ks][0], al[ks][0]);
+      split_tf32(A(g + 8, k0), ah[ks][1], al[ks][1]);
+      split_tf32(A(g, k0 + 4), ah[ks][2], al[ks][2]);
+      split_tf32(A(g + 8, k0 + 4), ah[ks][3], al[ks][3]);
+    }
+    for (int tile = warp; tile < ntiles; tile += NW) {
+      const int fb = tile * 8 + g;
+      const bool vb = fb < nfib;
+      const int cb = vb ? fb / F : 0, lb = vb ? fb - cb * F : 0;
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const int k0 = ks * 8 + tq, k1 = k0 + 4;
+        const float v0 = (vb && k0 < K) ? in[ain(cb, lb, k0)] : 0.f;
+        const float v1 = (vb && k1 < K) ? in[ain(cb, lb, k1)] : 0.f;
+        uint32_t h0, l0, h1, l1;
+        split_tf32(v0, h0, l0);
+        split_tf32(v1, h1, l1);
+        mma_tf32(c, ah[ks], h0, h1);
+        mma_tf32(c, ah[ks], l0, l1);
+        mma_tf32(c, al[ks], h0, h1);
+      }
+      __syncwarp();
+      store(tile, c);
+    }
+  } else {  // BF16x3, m16n8k16: one k-step covers K <= 16
+    uint32_t ah[4], al[4];
+    {
+      uint32_t h[8], l[8];
+      const int rr[8] = {g, g, g + 8, g + 8, g, g, g + 8, g + 8};
+      const int kk[8] = {2 * tq, 2 * tq + 1, 2 * tq, 2 * tq + 1, 2 * tq + 8, 2 * tq + 9, 2 * tq + 8, 2 * tq + 9};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) split_bf16(A(rr[e], kk[e]), h[e], l[e]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ah[q] = pack_bf16(h[2 * q], h[2 * q + 1]);
+        al[q] = pack_bf16(l[2 * q], l[2 * q + 1]);
+      }
+    }
+    for (int tile = warp; tile < ntiles; tile += NW) {
+      const int fb = tile * 8 + g;
+      const bool vb = fb < nfib;
+      const int cb = vb ? fb / F : 0, lb = vb ? fb - cb * F : 0;
+      float v[4];
+      const int kk[4] = {2 * tq, 2 * tq + 1, 2 * tq + 8, 2 * tq + 9};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = (vb && kk[e] < K) ? in[ain(cb, lb, kk[e])] : 0.f;
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split_bf16(v[e], h[e], l[e]);
+      const uint32_t bh0 = pack_bf16(h[0], h[1]), bh1 = pack_bf16(h[2], h[3]);
+      const uint32_t bl0 = pack_bf16(l[0], l[1]), bl1 = pack_bf16(l[2], l[3]);
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16(c, ah, bh0, bh1);
+      mma_bf16(c, ah, bl0, bl1);
+      mma_bf16(c, al, bh0, bh1);
+      __syncwarp();
+      store(tile, c);
+    }
+  }
+}
+
 }  // namespace
 }  // namespace sfx

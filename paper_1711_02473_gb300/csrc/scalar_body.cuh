@@ -127,6 +127,7 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
     }
   }
   __syncthreads();
+  pdl_allow_next();
   if (!STORED && member) jacobian_columns<N>(X, xq, Jc, t);
   __syncthreads();
   if (KAP) {
@@ -248,17 +249,25 @@ __device__ __forceinline__ void scalar_tile_fp64(const ActArgs& a, const int64_t
       __syncthreads();
     }
     // the inverted-cell flag is final here (set while forming the factors)
+    if (r == a.r0) pdl_wait_prev();
     const bool ok = active && !*bad;
     if (ok) {
       if (a.cell_vectors) {
         for (int l = t; l < N3; l += N2) a.y[(slot * N3 + l) * a.nrhs + r] = U[l];
       } else {
         // reduction in L2 (red.global.add.f64): cells of one launch share no
-        // dof, so each address is added to once per launch, in launch order
-        for (int l = t; l < N3; l += N2) atomicAdd(&a.y[dof(l) * a.nrhs + r], U[l]);
+        // dof, so each address is added to once per launch, in launch order;
+        // in an overwriting action the dof's first pair stores instead
+        for (int l = t; l < N3; l += N2) {
+          double* yp = &a.y[dof(l) * a.nrhs + r];
+          if (first_touch(a, cell, l, N3)) *yp = U[l]; else atomicAdd(yp, U[l]);
+        }
       }
     } else if (active && a.cell_vectors) {
       for (int l = t; l < N3; l += N2) a.y[(slot * N3 + l) * a.nrhs + r] = 0.0;
+    } else if (active) {
+      for (int l = t; l < N3; l += N2)
+        if (first_touch(a, cell, l, N3)) a.y[dof(l) * a.nrhs + r] = 0.0;
     }
     if (r == a.r0 && active && *bad && t == 0) set_flag(a.status, SFX_DEV_INVERTED);
     __syncthreads();

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
     flags[2 * c + 1] = 0;
   }
   __syncthreads();
+  pdl_allow_next();
   const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
   const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
   const float fa = (float)alpha, fb = (float)beta;
@@ -326,6 +327,7 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
       tc_contract<N, 2, true, false, PREC, NT>(U, U, tabs[0], cb);
       __syncthreads();
     }
+    if (r == 0) pdl_wait_prev();
     for (int i = tid; i < cb * N3; i += NT) {
       const int c = i / N3, l = i - c * N3;
       const int cell = flags[2 * c];
@@ -334,11 +336,14 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
       const bool ok = !flags[2 * c + 1];
       if (a.cell_vectors) {
         a.y[(slot * N3 + l) * a.nrhs + r] = ok ? f2d_int(U[i]) : 0.0;
-      } else if (ok) {
+      } else {
         // reduction in L2 (red.global.add.f64), not on the SM's FP64 pipe; cells
         // of one launch share no dof, so every address is added to once per
-        // launch and the order of the sums is that of the launches
-        atomicAdd(&a.y[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r], f2d_int(U[i]));
+        // launch and the order of the sums is that of the launches; in an
+        // overwriting action the dof's first pair stores instead (0 if skipped)
+        double* yp = &a.y[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r];
+        if (first_touch(a, cell, l, N3)) *yp = ok ? f2d_int(U[i]) : 0.0;
+        else if (ok) atomicAdd(yp, f2d_int(U[i]));
       }
     }
     if (r == 0)

@@ -205,6 +205,7 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
     *abort_word = 0;
   }
   __syncthreads();
+  pdl_allow_next();
   const double alpha = FORM == SFX_HELMHOLTZ ? a.alpha : 1.0;
   const double beta = FORM == SFX_HELMHOLTZ ? a.beta : 1.0;
 
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
     float* G0 = U + (size_t)cb * N3;
     float* G1 = G0 + (size_t)cb * N3;
     float* G2 = G1 + (size_t)cb * N3;
+    bool waited = false;  // pdl_wait_prev passed
     int j = 0;
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++j) {
       for (int c = ct; c < cb; c += NCT) {
@@ -365,6 +367,10 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
           tc_contract<N, 2, true, false, PREC, NCT, NPW>(U, U, tabs[0], cb);
           named_sync(2, NCT);
         }
+        if (!waited) {
+          pdl_wait_prev();
+          waited = true;
+        }
         for (int i = ct; i < tot; i += NCT) {
           const int c = i / N3, l = i - c * N3;
           const int cell = ccid[c];
@@ -373,10 +379,15 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
           if (a.cell_vectors) {
             const int64_t slot = b * cb + c;
             a.y[(slot * N3 + l) * a.nrhs + r] = ok ? f2d_int(U[i]) : 0.0;
-          } else if (ok) {
-            // L2 reduction (red.global.add.f64); cells of one launch share no dof
+          } else {
+            // L2 reduction (red.global.add.f64); cells of one launch share no
+            // dof; in an overwriting action the dof's first pair stores instead
+            const bool fst = first_touch(a, cell, l, N3);
+            if (!ok && !fst) continue;
             const int dof = W::CMAP ? cmap[i] : __ldg(&a.map[(int64_t)cell * N3 + l]);
-            atomicAdd(&a.y[(int64_t)dof * a.nrhs + r], f2d_int(U[i]));
+            double* yp = &a.y[(int64_t)dof * a.nrhs + r];
+            if (fst) *yp = ok ? f2d_int(U[i]) : 0.0;
+            else atomicAdd(yp, f2d_int(U[i]));
           }
         }
         if (r == 0)
@@ -385,6 +396,7 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
         named_sync(2, NCT);
       }
     }
+    if (!waited) pdl_wait_prev();
   }
 }
 
@@ -416,7 +428,9 @@ int launch_ws_one(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   const int64_t nbatch = (a.ncells + cb - 1) / cb;
   if (nbatch == 0) return 0;
   const int64_t grid = nbatch < (int64_t)nsm * per_sm ? nbatch : (int64_t)nsm * per_sm;
-  kern<<<(unsigned)grid, W::NT, smem, s>>>(a, ncell_total, cb, nbatch, ws_wait_cap());
+  const uint32_t cap = ws_wait_cap();
+  e = launch_kernel(kern, (unsigned)grid, W::NT, smem, s, a.overlap_prev != 0, a, ncell_total, cb, nbatch, cap);
+  if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();
 }
 

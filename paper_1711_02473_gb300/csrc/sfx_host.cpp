@@ -215,6 +215,8 @@ static int upload_tables(const Tab1D* t) {
   if (!e) e = upload_tab_scalar_mixed_ws_bf16(t);
   if (!e) e = upload_tab_qdata(t);
   if (!e) e = upload_tab_hdivcurl(t);
+  if (!e) e = upload_tab_hdivcurl_mixed_tf32(t);
+  if (!e) e = upload_tab_hdivcurl_mixed_bf16(t);
   if (!e) e = upload_tab_elastic(t);
   if (!e) e = upload_tab_elastic_mixed(t);
   if (!e) e = upload_tab_matrix(t);
@@ -258,6 +260,7 @@ constexpr int kBuiltinCells[SFX_TUNE_NKERNEL][kMaxDeg + 1] = {
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // FP64 hyperelastic residual (same)
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // FP64 linearised hyperelastic action (same)
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision linearised hyperelastic action (same)
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision NCF / NCE actions (same)
 };
 // by degree (needs n = p + 1 >= 4): on where it measured faster than the
 // one-role kernel on the 64^3 Laplace and Helmholtz actions (p = 4, 5, 6, 8:
@@ -788,6 +791,32 @@ extern "C" sfx_status sfx_space_create(const sfx_mesh* mesh, sfx_family fam, int
   if (upload_tables(&s->tab) != 0) { sfx_space_destroy(s); return SFX_ERR_CUDA; }
   sfx_status st = to_device(s->map.data(), s->map.size(), &s->d_map);
   if (!st) st = to_device(cells.data(), cells.size(), &s->d_cells);
+  if (!st && fam == SFX_Q) {
+    // first-touch bits: walk the cells colour by colour (the order of the
+    // launches) and mark each dof's first cell-node pair
+    const int words = (nloc + 31) / 32;
+    std::vector<uint32_t> first;
+    std::vector<uint8_t> seen;
+    try {
+      first.assign((size_t)ncell * words, 0u);
+      seen.assign((size_t)ndof, 0);
+    } catch (...) {
+      st = SFX_ERR_ALLOC;
+    }
+    if (!st) {
+      for (size_t k = 0; k < cells.size(); ++k) {
+        const int64_t c = cells[k];
+        const int32_t* row = &s->map[(size_t)c * nloc];
+        uint32_t* bits = &first[(size_t)c * words];
+        for (int l = 0; l < nloc; ++l)
+          if (!seen[(size_t)row[l]]) {
+            seen[(size_t)row[l]] = 1;
+            bits[l >> 5] |= 1u << (l & 31);
+          }
+      }
+      st = to_device(first.data(), first.size(), &s->d_first);
+    }
+  }
   if (st) { sfx_space_destroy(s); return st; }
   *out = s;
   return SFX_OK;
@@ -836,6 +865,7 @@ extern "C" void sfx_space_destroy(sfx_space* s) {
   if (s->scalar) sfx_space_destroy(s->scalar);
   if (s->d_map) cudaFree(s->d_map);
   if (s->d_cells) cudaFree(s->d_cells);
+  if (s->d_first) cudaFree(s->d_first);
   if (s->d_naive) cudaFree(s->d_naive);
   delete s;
 }
@@ -858,6 +888,18 @@ extern "C" sfx_status sfx_tabulate_1d(sfx_nodes nodes, int ndof1d, sfx_nodes qru
 }
 
 // ----------------------------------------------------------------- assembly
+// Overwriting scalar actions skip the memset of y where that measured faster
+// on GB300: DQ_p (every contribution is its dof's only one: plain stores, no
+// table) at every precision, and Q_p in the FP64 kernels (the first
+// contribution to each dof is stored, the later ones added; see d_first).
+// The split-precision Q_p kernels keep the memset: there the per-dof table
+// lookup and the split between stores and reductions within a warp cost more
+// than the memset saves (2-7% at p = 7, 8).
+static void set_first_touch(const sfx_space* sp, sfx_precision prec, ActArgs* a) {
+  if (sp->family == SFX_DQ) a->first_all = 1;
+  else if (sp->family == SFX_Q && prec == SFX_PREC_FP64) a->first = sp->d_first;
+}
+
 extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
                                           const sfx_space* sp, const double* x, double* y, int nrhs,
                                           int accumulate, sfx_precision prec, sfx_algo algo, void* stream) {
@@ -887,10 +929,13 @@ extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx
     return SFX_ERR_UNSUPPORTED;
   sfx_form_params pr = params ? *params : default_params(form);
   cudaStream_t s = (cudaStream_t)stream;
-  if (!accumulate) {
+  ActArgs a{};
+  // overwrite without a memset where the kernels store each dof's first
+  // contribution (the scalar sum-factorised and collocated kernels)
+  if (!accumulate && algo != SFX_ALGO_NAIVE) set_first_touch(sp, prec, &a);
+  if (!accumulate && !a.first && !a.first_all) {
     if (cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess) return SFX_ERR_CUDA;
   }
-  ActArgs a{};
   a.map = sp->d_map;
   a.vmap = sp->mesh->d_vmap;
   a.xyz = sp->mesh->d_xyz;
@@ -902,10 +947,14 @@ extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx
   a.cell_vectors = 0;
   a.alpha = pr.alpha; a.beta = pr.beta; a.mu = pr.mu; a.lambda = pr.lambda;
   a.status = ctx->d_status;
+  bool launched = false;
   for (int col = 0; col < sp->ncolour; ++col) {
     a.cells = sp->d_cells + sp->colour_off[col];
     a.ncells = sp->colour_off[col + 1] - sp->colour_off[col];
     if (a.ncells == 0) continue;
+    // later colours may start while the previous one drains (see pdl_wait_prev)
+    a.overlap_prev = launched ? 1 : 0;
+    launched = true;
     int e;
     if (algo == SFX_ALGO_COLLOCATED)
       e = prec == SFX_PREC_FP64 ? launch_action_scalar_coll(sp, form, a, stream)
@@ -968,10 +1017,11 @@ extern "C" sfx_status sfx_assemble_weighted_action(sfx_ctx* ctx, const sfx_space
   if (prec < SFX_PREC_FP64 || prec > SFX_PREC_BF16X3) return SFX_ERR_ARG;
   if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
-  if (!accumulate) {
+  ActArgs a{};
+  if (!accumulate) set_first_touch(sp, prec, &a);
+  if (!accumulate && !a.first && !a.first_all) {
     if (cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess) return SFX_ERR_CUDA;
   }
-  ActArgs a{};
   a.map = sp->d_map;
   a.vmap = sp->mesh->d_vmap;
   a.xyz = sp->mesh->d_xyz;
@@ -1466,6 +1516,9 @@ static ActArgs plan_args(const sfx_plan* pl, const double* x) {
   a.r0 = 0;
   a.r1 = pl->nrhs;
   a.status = pl->ctx->d_status;
+  // every (cell, l) of a p-adaptive DQ space is its dof's only pair: the
+  // kernels store b^K into y, which therefore needs no memset
+  a.first_all = 1;
   return a;
 }
 
@@ -1475,11 +1528,9 @@ extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* co
   if (!pl || !x || !y) return SFX_ERR_ARG;
   for (int f = 0; f < pl->nforms; ++f)
     if (!y[f] || y[f] == x) return SFX_ERR_ARG;
-  const size_t ybytes = (size_t)pl->ndof * pl->nrhs * sizeof(double);
   cudaStream_t s = (cudaStream_t)stream;
   if (mode == SFX_EXEC_PER_LAUNCH) {
     for (int f = 0; f < pl->nforms; ++f) {
-      if (cudaMemsetAsync(y[f], 0, ybytes, s) != cudaSuccess) return SFX_ERR_CUDA;
       for (int p = 1; p <= kMaxDeg; ++p) {
         const int64_t cnt = pl->deg_end[p] - pl->deg_begin[p];
         if (cnt == 0) continue;
@@ -1519,9 +1570,7 @@ extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* co
     }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SFX_ERR_CUDA;
-    int e = 0;
-    for (int f = 0; f < pl->nforms && !e; ++f) e = (int)cudaMemsetAsync(y[f], 0, ybytes, pl->cap);
-    if (!e) e = (int)cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
+    int e = (int)cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
     if (!e && b.ntiles > 0) e = batched_launch(b, pl->grid, pl->smem, pl->cap);
     cudaError_t ee = cudaStreamEndCapture(pl->cap, &g);
     if (e || ee != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); return SFX_ERR_CUDA; }
@@ -1581,9 +1630,11 @@ extern "C" sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, co
   if ((prec == SFX_PREC_FP64 && !q->d64) || (prec != SFX_PREC_FP64 && !q->d32)) return SFX_ERR_ARG;
   sfx_form_params pr = params ? *params : default_params(form);
   cudaStream_t s = (cudaStream_t)stream;
-  if (!accumulate && cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess)
-    return SFX_ERR_CUDA;
   ActArgs a{};
+  if (!accumulate) set_first_touch(sp, prec, &a);
+  if (!accumulate && !a.first && !a.first_all &&
+      cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess)
+    return SFX_ERR_CUDA;
   a.map = sp->d_map;
   a.vmap = sp->mesh->d_vmap;
   a.xyz = sp->mesh->d_xyz;
@@ -1596,10 +1647,13 @@ extern "C" sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, co
   a.beta = pr.beta;
   a.status = ctx->d_status;
   if (prec == SFX_PREC_FP64) a.qd64 = q->d64; else a.qd32 = q->d32;
+  bool launched = false;
   for (int col = 0; col < sp->ncolour; ++col) {
     a.cells = sp->d_cells + sp->colour_off[col];
     a.ncells = sp->colour_off[col + 1] - sp->colour_off[col];
     if (a.ncells == 0) continue;
+    a.overlap_prev = launched ? 1 : 0;
+    launched = true;
     const int e = launch_action_scalar(sp, form, prec, SFX_ALGO_SUMFACT, a, stream);
     if (e == -1) return SFX_ERR_UNSUPPORTED;
     if (e) return SFX_ERR_CUDA;

@@ -71,6 +71,11 @@ struct sfx_space {
   std::vector<int64_t> colour_off; // ncolour + 1 offsets into d_cells
   std::vector<int32_t> cells;      // host copy of the cell ids, colour by colour
   int32_t* d_cells = nullptr;
+  // scalar Q_p: bit l of cell c's row (nloc/32 words, rounded up) is set when
+  // (c, l) is the first of its dof's cell-node pairs in colour order, so an
+  // overwriting action stores that contribution and adds the later ones
+  // instead of zeroing y first (DQ_p: every pair is first; no table)
+  uint32_t* d_first = nullptr;
   sfx::Tab1D tab;                  // 1D tables of degree p
   // vector Q_p only: the scalar Q_p space of one component (component a's
   // global dofs are a * scalar->ndof + the scalar numbering), built on first
@@ -114,6 +119,12 @@ struct ActArgs {
   int64_t cell0;          // no cell list: cell = cell0 + slot
   int stage_factors;      // 1: stage the per-point factors once per cell even for one RHS (the
                           //    arithmetic of the persistent batched kernel, for bitwise comparison)
+  const uint32_t* first;  // overwrite mode, y not zeroed beforehand: the space's first-touch bits
+  int first_all;          //    (d_first), or 1 here when every (cell, l) is its dof's only pair (DQ);
+                          //    both unset: every contribution is added to y
+  int overlap_prev;       // 1: not the first launch of its action on the stream; a launcher whose
+                          //    kernel waits before writing y launches it as a programmatic
+                          //    dependent of the previous launch (pdl_wait_prev)
   double alpha, beta, mu, lambda;
   uint32_t* status;
 };
@@ -204,7 +215,8 @@ enum {
   SFX_TUNE_ELASTIC = 7,          // FP64 hyperelastic residual
   SFX_TUNE_LINEARISED = 8,       // FP64 linearised hyperelastic action
   SFX_TUNE_LINEARISED_MIXED = 9, // split-precision linearised hyperelastic action
-  SFX_TUNE_NKERNEL = 10
+  SFX_TUNE_HDIVCURL_MIXED = 10,  // split-precision NCF / NCE actions
+  SFX_TUNE_NKERNEL = 11
 };
 // Tuned cells per CTA for the team-per-cell kernels: the tuned value if one
 // is set (at most maxcb, and reduced until the shared memory fits `limit`),
@@ -223,6 +235,8 @@ int upload_tab_scalar_mixed_bf16(const Tab1D* t);
 int upload_tab_scalar_mixed_ws_tf32(const Tab1D* t);
 int upload_tab_scalar_mixed_ws_bf16(const Tab1D* t);
 int upload_tab_hdivcurl(const Tab1D* t);
+int upload_tab_hdivcurl_mixed_tf32(const Tab1D* t);
+int upload_tab_hdivcurl_mixed_bf16(const Tab1D* t);
 int upload_tab_elastic(const Tab1D* t);
 int upload_tab_elastic_mixed(const Tab1D* t);
 int upload_tab_matrix(const Tab1D* t);

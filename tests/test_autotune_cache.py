@@ -59,5 +59,6 @@ def test_structured_candidates_fit_the_team_limit():
         for p in range(1, 9):
             c = autotune.candidates(kind, p)
             assert c and all(1 <= v <= max(1, 256 // (p + 1) ** 2) for v in c)
-    assert all(1 <= v <= 64 for v in autotune.candidates("linearised_mixed", 4))
-    assert set(autotune.STRUCTURED) == {"hdivcurl", "elastic", "linearised", "linearised_mixed"}
+    for kind in ("linearised_mixed", "hdivcurl_mixed"):
+        assert all(1 <= v <= 32 for v in autotune.candidates(kind, 4))
+    assert set(autotune.STRUCTURED) == {"hdivcurl", "elastic", "linearised", "linearised_mixed", "hdivcurl_mixed"}
