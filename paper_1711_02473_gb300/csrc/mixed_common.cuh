@@ -65,8 +65,13 @@ __device__ __forceinline__ int faddr(int c, int f, int k) {
 // time (the n dimension of the mma); in-place use is safe because a warp reads
 // all of its fibers before writing them and no other warp touches them.
 // NT: threads taking part (whole warps, starting at warp WOFF of the CTA).
-template <int N, int AX, bool TRANS, bool ACC, int PREC, int NT = kThreads, int WOFF = 0>
-__device__ __forceinline__ void tc_contract(const float* in, float* out, const TabF& M, int ncell) {
+// NSUM > 1: the input is the sum of NSUM arrays `sstride` floats apart (in,
+// in + sstride, ...), plus the array sstride before `in` when PRE, summed in
+// FP32 as the values are loaded; in-place use (out = in or out = in - sstride)
+// stays safe for the same reason.
+template <int N, int AX, bool TRANS, bool ACC, int PREC, int NT = kThreads, int WOFF = 0, int NSUM = 1,
+          bool PRE = false>
+__device__ __forceinline__ void tc_contract(const float* in, float* out, const TabF& M, int ncell, int sstride = 0) {
   constexpr int NW = NT / 32;
   constexpr int N2 = N * N;
   const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - WOFF;
@@ -74,6 +79,13 @@ __device__ __forceinline__ void tc_contract(const float* in, float* out, const T
   const int nfib = ncell * N2;
   const int ntiles = (nfib + 7) >> 3;
   auto A = [&](int r, int k) -> float { return TRANS ? M.v[k][r] : M.v[r][k]; };
+  auto ld = [&](int a) -> float {
+    float v = in[a];
+#pragma unroll
+    for (int s = 1; s < NSUM; ++s) v += in[a + s * sstride];
+    if (PRE) v += in[a - sstride];
+    return v;
+  };
   if (PREC == SFX_PREC_TF32X3) {
     constexpr int KS = (N + 7) / 8;
     uint32_t ah[KS][4], al[KS][4];
@@ -93,8 +105,8 @@ __device__ __forceinline__ void tc_contract(const float* in, float* out, const T
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) {
         const int k0 = ks * 8 + tq, k1 = k0 + 4;
-        const float v0 = (vb && k0 < N) ? in[faddr<N, AX>(cb, lb, k0)] : 0.f;
-        const float v1 = (vb && k1 < N) ? in[faddr<N, AX>(cb, lb, k1)] : 0.f;
+        const float v0 = (vb && k0 < N) ? ld(faddr<N, AX>(cb, lb, k0)) : 0.f;
+        const float v1 = (vb && k1 < N) ? ld(faddr<N, AX>(cb, lb, k1)) : 0.f;
         uint32_t h0, l0, h1, l1;
         split_tf32(v0, h0, l0);
         split_tf32(v1, h1, l1);
@@ -135,7 +147,7 @@ __device__ __forceinline__ void tc_contract(const float* in, float* out, const T
       float v[4];
       const int kk[4] = {2 * tq, 2 * tq + 1, 2 * tq + 8, 2 * tq + 9};
 #pragma unroll
-      for (int e = 0; e < 4; ++e) v[e] = (vb && kk[e] < N) ? in[faddr<N, AX>(cb, lb, kk[e])] : 0.f;
+      for (int e = 0; e < 4; ++e) v[e] = (vb && kk[e] < N) ? ld(faddr<N, AX>(cb, lb, kk[e])) : 0.f;
       uint32_t h[4], l[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) split_bf16(v[e], h[e], l[e]);

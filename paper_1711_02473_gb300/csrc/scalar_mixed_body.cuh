@@ -328,22 +328,39 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
       __syncthreads();
     }
     if (r == 0) pdl_wait_prev();
-    for (int i = tid; i < cb * N3; i += NT) {
-      const int c = i / N3, l = i - c * N3;
-      const int cell = flags[2 * c];
-      if (cell < 0) continue;
-      const int64_t slot = (int64_t)blockIdx.x * cb + c;
-      const bool ok = !flags[2 * c + 1];
-      if (a.cell_vectors) {
-        a.y[(slot * N3 + l) * a.nrhs + r] = ok ? f2d_int(U[i]) : 0.0;
-      } else {
-        // reduction in L2 (red.global.add.f64), not on the SM's FP64 pipe; cells
-        // of one launch share no dof, so every address is added to once per
-        // launch and the order of the sums is that of the launches; in an
-        // overwriting action the dof's first pair stores instead (0 if skipped)
-        double* yp = &a.y[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r];
-        if (first_touch(a, cell, l, N3)) *yp = ok ? f2d_int(U[i]) : 0.0;
-        else if (ok) atomicAdd(yp, f2d_int(U[i]));
+    if (a.cell_vectors) {
+      for (int i = tid; i < cb * N3; i += NT) {
+        const int c = i / N3, l = i - c * N3;
+        if (flags[2 * c] < 0) continue;
+        const int64_t slot = (int64_t)blockIdx.x * cb + c;
+        a.y[(slot * N3 + l) * a.nrhs + r] = !flags[2 * c + 1] ? f2d_int(U[i]) : 0.0;
+      }
+    } else {
+      // reduction in L2 (red.global.add.f64), not on the SM's FP64 pipe; cells
+      // of one launch share no dof, so every address is added to once per
+      // launch and the order of the sums is that of the launches; in an
+      // overwriting action the dof's first pair stores instead (0 if skipped).
+      // GS map entries per thread are loaded before the first write.
+      constexpr int GS = 4;
+      for (int i0 = tid; i0 < cb * N3; i0 += GS * NT) {
+        int dof[GS];
+#pragma unroll
+        for (int g = 0; g < GS; ++g) {
+          const int i = i0 + g * NT;
+          const int c = i / N3;
+          const int cell = i < cb * N3 ? flags[2 * c] : -1;
+          dof[g] = cell >= 0 ? __ldg(&a.map[(int64_t)cell * N3 + (i - c * N3)]) : -1;
+        }
+#pragma unroll
+        for (int g = 0; g < GS; ++g) {
+          if (dof[g] < 0) continue;
+          const int i = i0 + g * NT;
+          const int c = i / N3;
+          const bool ok = !flags[2 * c + 1];
+          double* yp = &a.y[(int64_t)dof[g] * a.nrhs + r];
+          if (first_touch(a, flags[2 * c], i - c * N3, N3)) *yp = ok ? f2d_int(U[i]) : 0.0;
+          else if (ok) atomicAdd(yp, f2d_int(U[i]));
+        }
       }
     }
     if (r == 0)

@@ -140,16 +140,26 @@ struct WsShape {
   static constexpr size_t kHead = 64;                       // two mbarriers, the abort word
   static constexpr size_t bytes(int cb) {
     return kHead + 2 * sizeof(TabF) + 32 * 8 + (size_t)cb * (PD + NT64 * N3) * 8 + (size_t)cb * N3 * (NK + NC) * 4 +
-           (CMAP ? (size_t)cb * N3 * 4 : 0) + (size_t)cb * 4 * 4;
+           (CMAP ? (size_t)cb * N3 * 4 : 0) + (size_t)cb * 6 * 4;
   }
 };
 
-// Warp split and CTAs per SM, chosen by measurement (see the launcher).
-#ifndef SFX_WS_NPW
-#define SFX_WS_NPW 8
-#endif
-#ifndef SFX_WS_NCW
-#define SFX_WS_NCW 8
+// Producer / consumer warps of a 512-thread CTA by degree and family, from
+// measurement on the 64^3 Laplace and Helmholtz actions (TF32x3, ms, 8+8 ->
+// chosen): 8 + 8 where the two roles bind together (Q_8); more producers where
+// the FP64 geometry binds (DQ_8: 12.18 -> 12.02 Helmholtz; p = 5: 4.70 -> 4.63)
+// or where 7 consumer warps still take each contraction stage's fiber tiles in
+// as many rounds as 8 (p = 6: 7.10 -> 6.87; Q_4: 3.24 -> 3.21).  SFX_WS_NPW /
+// SFX_WS_NCW, when defined, override the table.
+constexpr int ws_npw_of(int N, bool DQ) {
+  return N == 5 ? (DQ ? 8 : 9) : N == 6 ? 10 : N == 7 ? 9 : N == 9 ? (DQ ? 10 : 8) : 8;
+}
+#ifdef SFX_WS_NPW
+constexpr int ws_npw(int, bool) { return SFX_WS_NPW; }
+constexpr int ws_ncw(int, bool) { return SFX_WS_NCW; }
+#else
+constexpr int ws_npw(int N, bool DQ) { return ws_npw_of(N, DQ); }
+constexpr int ws_ncw(int N, bool DQ) { return 16 - ws_npw_of(N, DQ); }
 #endif
 #ifndef SFX_WS_CTAS
 #define SFX_WS_CTAS 2
@@ -171,7 +181,8 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
   extern __shared__ double smd[];
   // layout: [full, empty mbarriers; abort word][2 TabF][xq 16][wq 16]
   //         [producer doubles: cb x PD][t: cb x N3 doubles][factors: NK x cb x N3 floats]
-  //         [consumer floats: NC x cb x N3][map: cb x N3 ints if CMAP][bad, ccid, pcid, cbad: cb ints each]
+  //         [consumer floats: NC x cb x N3][map: cb x N3 ints if CMAP][bad: cb, ccid: 2 cb, pcid: cb,
+  //         cbad: 2 cb ints (the consumers' cell ids and flags alternate between two slots by batch)]
   unsigned char* base = reinterpret_cast<unsigned char*>(smd);
   uint64_t* full = reinterpret_cast<uint64_t*>(base);
   uint64_t* empty = full + 1;
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
   int* cmap = reinterpret_cast<int*>(cf + (size_t)cb * N3 * W::NC);
   int* bad = cmap + (W::CMAP ? (size_t)cb * N3 : 0);
   int* ccid = bad + cb;
-  int* pcid = ccid + cb;
+  int* pcid = ccid + 2 * cb;
   int* cbad = pcid + cb;
 
   const int tid = threadIdx.x;
@@ -285,10 +296,15 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
     bool waited = false;  // pdl_wait_prev passed
     int j = 0;
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x, ++j) {
+      // this batch's slot of the cell ids and flags: threads still scattering
+      // the previous batch read the other slot, so no barrier is needed
+      // between that scatter and these writes
+      int* const cid = ccid + (j & 1) * cb;
+      int* const cfl = cbad + (j & 1) * cb;
       for (int c = ct; c < cb; c += NCT) {
         int cell = -1;
         if (!slot_cell(a, b * cb + c, ncell_total, &cell)) cell = -1;
-        ccid[c] = cell;
+        cid[c] = cell;
       }
       named_sync(2, NCT);
       const int tot = cb * N3;
@@ -296,13 +312,13 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
       for (int r = 0; r < a.nrhs; ++r) {
         // gather: G independent (map, x) load pairs per thread in flight; the
         // map entries are kept in shared memory for the scatter (CMAP)
-        for (int i0 = ct; i0 < tot; i0 += G * NCT) {
+        auto gather = [&](const int* idx) {
           int dof[G];
 #pragma unroll
           for (int g = 0; g < G; ++g) {
-            const int i = i0 + g * NCT;
+            const int i = idx[g];
             const int c = i / N3;
-            const int cell = i < tot ? ccid[c] : -1;
+            const int cell = i >= 0 ? cid[c] : -1;
             dof[g] = cell >= 0 ? ((r == 0 || !W::CMAP) ? __ldg(&a.map[(int64_t)cell * N3 + (i - c * N3)]) : cmap[i])
                                : -1;
           }
@@ -311,12 +327,18 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
           for (int g = 0; g < G; ++g) xv[g] = dof[g] >= 0 ? __ldg(&a.x[(int64_t)dof[g] * a.nrhs + r]) : 0.0;
 #pragma unroll
           for (int g = 0; g < G; ++g) {
-            const int i = i0 + g * NCT;
-            if (i < tot) {
+            const int i = idx[g];
+            if (i >= 0) {
               U[i] = d2f_int(xv[g]);
               if (W::CMAP && r == 0) cmap[i] = dof[g];
             }
           }
+        };
+        for (int i0 = ct; i0 < tot; i0 += G * NCT) {
+          int idx[G];
+#pragma unroll
+          for (int g = 0; g < G; ++g) idx[g] = i0 + g * NCT < tot ? i0 + g * NCT : -1;
+          gather(idx);
         }
         named_sync(2, NCT);
         if (!DQ) {
@@ -332,7 +354,7 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
         tc_contract<N, 2, false, false, PREC, NCT, NPW>(U, G2, tabs[1], cb);
         if (r == 0) {
           ws_wait(full, (uint32_t)(j & 1), cap, abort_word, a.status);
-          for (int c = ct; c < cb; c += NCT) cbad[c] = bad[c];
+          for (int c = ct; c < cb; c += NCT) cfl[c] = bad[c];
         }
         named_sync(2, NCT);
         for (int i = ct; i < tot; i += NCT) {
@@ -353,47 +375,73 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
         }
         if (r == a.nrhs - 1) mbar_arrive(empty);
         named_sync(2, NCT);
-        tc_contract<N, 0, true, MAS, PREC, NCT, NPW>(G0, U, tabs[1], cb);
-        named_sync(2, NCT);
-        tc_contract<N, 1, true, true, PREC, NCT, NPW>(G1, U, tabs[1], cb);
-        named_sync(2, NCT);
-        tc_contract<N, 2, true, true, PREC, NCT, NPW>(G2, U, tabs[1], cb);
+        // transposed derivative stages in place, one per array (no barrier
+        // between them: they touch different arrays); their sum, plus the
+        // mass term in U, is formed where it is read next -- in the first
+        // transposed B stage (Q_p) or in the scatter (DQ_p)
+        tc_contract<N, 0, true, false, PREC, NCT, NPW>(G0, G0, tabs[1], cb);
+        tc_contract<N, 1, true, false, PREC, NCT, NPW>(G1, G1, tabs[1], cb);
+        tc_contract<N, 2, true, false, PREC, NCT, NPW>(G2, G2, tabs[1], cb);
         named_sync(2, NCT);
         if (!DQ) {
-          tc_contract<N, 0, true, false, PREC, NCT, NPW>(U, U, tabs[0], cb);
+          tc_contract<N, 0, true, false, PREC, NCT, NPW, 3, MAS>(G0, U, tabs[0], cb, cb * N3);
           named_sync(2, NCT);
           tc_contract<N, 1, true, false, PREC, NCT, NPW>(U, U, tabs[0], cb);
           named_sync(2, NCT);
           tc_contract<N, 2, true, false, PREC, NCT, NPW>(U, U, tabs[0], cb);
           named_sync(2, NCT);
         }
+        // b^K at local index i: U (Q_p), or the sum of the stages (DQ_p)
+        auto bk = [&](int i) -> float {
+          if (!DQ) return U[i];
+          const float v = G0[i] + G1[i] + G2[i];
+          return MAS ? v + U[i] : v;
+        };
         if (!waited) {
           pdl_wait_prev();
           waited = true;
         }
-        for (int i = ct; i < tot; i += NCT) {
-          const int c = i / N3, l = i - c * N3;
-          const int cell = ccid[c];
-          if (cell < 0) continue;
-          const bool ok = !cbad[c];
-          if (a.cell_vectors) {
+        if (a.cell_vectors) {
+          for (int i = ct; i < tot; i += NCT) {
+            const int c = i / N3, l = i - c * N3;
+            if (cid[c] < 0) continue;
             const int64_t slot = b * cb + c;
-            a.y[(slot * N3 + l) * a.nrhs + r] = ok ? f2d_int(U[i]) : 0.0;
-          } else {
-            // L2 reduction (red.global.add.f64); cells of one launch share no
-            // dof; in an overwriting action the dof's first pair stores instead
-            const bool fst = first_touch(a, cell, l, N3);
-            if (!ok && !fst) continue;
-            const int dof = W::CMAP ? cmap[i] : __ldg(&a.map[(int64_t)cell * N3 + l]);
-            double* yp = &a.y[(int64_t)dof * a.nrhs + r];
-            if (fst) *yp = ok ? f2d_int(U[i]) : 0.0;
-            else atomicAdd(yp, f2d_int(U[i]));
+            a.y[(slot * N3 + l) * a.nrhs + r] = !cfl[c] ? f2d_int(bk(i)) : 0.0;
+          }
+        } else {
+          // L2 reduction (red.global.add.f64); cells of one launch share no
+          // dof; in an overwriting action the dof's first pair stores instead.
+          // G map entries per thread are loaded before the first write, so
+          // their latencies overlap (the map is re-read from L2 unless kept
+          // in shared memory)
+          for (int i0 = ct; i0 < tot; i0 += G * NCT) {
+            int dof[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+              const int i = i0 + g * NCT;
+              const int c = i / N3;
+              const int cell = i < tot ? cid[c] : -1;
+              dof[g] = cell >= 0 ? (W::CMAP ? cmap[i] : __ldg(&a.map[(int64_t)cell * N3 + (i - c * N3)])) : -1;
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+              if (dof[g] < 0) continue;
+              const int i = i0 + g * NCT;
+              const int c = i / N3;
+              const bool ok = !cfl[c];
+              const bool fst = first_touch(a, cid[c], i - c * N3, N3);
+              double* yp = &a.y[(int64_t)dof[g] * a.nrhs + r];
+              if (fst) *yp = ok ? f2d_int(bk(i)) : 0.0;
+              else if (ok) atomicAdd(yp, f2d_int(bk(i)));
+            }
           }
         }
         if (r == 0)
           for (int c = ct; c < cb; c += NCT)
-            if (ccid[c] >= 0 && cbad[c]) set_flag(a.status, SFX_DEV_INVERTED);
-        named_sync(2, NCT);
+            if (cid[c] >= 0 && cfl[c]) set_flag(a.status, SFX_DEV_INVERTED);
+        // no barrier here: a thread gathers the next right-hand side (or the
+        // next batch) into the same local indices i it has just scattered, and
+        // the next batch's cell ids go to the other slot
       }
     }
     if (!waited) pdl_wait_prev();
@@ -406,7 +454,7 @@ __global__ void __launch_bounds__((NPW + NCW) * 32, SFX_WS_CTAS)
 // kernel covers.
 template <int N, bool DQ, int FORM, int PREC>
 int launch_ws_one(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
-  constexpr int NPW = SFX_WS_NPW, NCW = SFX_WS_NCW;
+  constexpr int NPW = ws_npw(N, DQ), NCW = ws_ncw(N, DQ);
   using W = WsShape<N, FORM, NPW, NCW>;
   const size_t max_smem = 227 * 1024, per_cta = (228 * 1024) / SFX_WS_CTAS - 1024;
   int cb = tuned_cells_per_cta(SFX_TUNE_SCALAR_MIXED_WS, N - 1, 0);
