@@ -35,14 +35,14 @@ L2_FLUSH_BYTES = 256 << 20
 HBM_GBS = 6788.3             # GB300 HBM bandwidth, measured by a STREAM-style copy (GB/s)
 METRIC = "DoFs/s for sum-factorised action (mixed vs FP64, same GB300, stated error); % roofline"
 # DRAM bytes (read + write) per cell of one colour launch, from the ncu captures of
-# the 32^3, p = 8 cases (dram__bytes_read.sum + dram__bytes_write.sum of one launch /
-# 4096 cells), keyed by kernel, family, degree and form; the full-size launch processes
-# 8x the cells, and the traffic of these kernels grows in proportion (x, map, y and
-# coordinates are per cell).
-NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_mixed", "Q", 8, "laplace"): (94.201856e6 + 4.166144e6) / 4096,
-                           ("k_action_scalar_mixed", "Q", 8, "helmholtz"): (94.149376e6 + 3.642880e6) / 4096,
-                           ("k_action_scalar_fp64", "Q", 8, "laplace"): (94.203392e6 + 5.303552e6) / 4096,
-                           ("k_action_scalar_mixed_ws", "Q", 8, "helmholtz"): (93.751040e6 + 4.130816e6) / 4096}
+# the 32^3, p = 8 cases (dram__bytes_read.sum + dram__bytes_write.sum of the first
+# colour launch of the form / 4096 cells), keyed by kernel, family, degree and form;
+# the full-size launch processes 8x the cells, and the traffic of these kernels grows
+# in proportion (x, map, y and coordinates are per cell).  Only the kernels as they
+# are now: a kernel without an entry reports traffic null.  (The FP64 kernel's first
+# colour stores every dof it writes, so later colours read more of y.)
+NCU_DRAM_BYTES_PER_CELL = {("k_action_scalar_fp64", "Q", 8, "laplace"): (66.470400e6 + 11.927552e6) / 4096,
+                           ("k_action_scalar_mixed_ws", "Q", 8, "helmholtz"): (93.733120e6 + 3.786240e6) / 4096}
 
 
 def parse():

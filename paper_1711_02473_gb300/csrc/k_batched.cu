@@ -17,13 +17,20 @@ SFX_DEFINE_TAB_UPLOAD(upload_tab_batched)
 
 namespace {
 
-constexpr int kBT = 256;
-constexpr size_t kBudget = 200 * 1024;
+// threads per CTA and dynamic shared memory of the persistent kernel
+#ifndef SFX_BATCH_THREADS
+#define SFX_BATCH_THREADS 256
+#endif
+#ifndef SFX_BATCH_SMEM_KB
+#define SFX_BATCH_SMEM_KB 200
+#endif
+constexpr int kBT = SFX_BATCH_THREADS;
+constexpr size_t kBudget = (size_t)SFX_BATCH_SMEM_KB * 1024;
 
 template <int N, int FORM>
 constexpr int cb_of() {
   using Sh = ScalarShape<N, FORM>;
-  int cb = Sh::MAXCB;
+  int cb = kBT / Sh::N2 > 0 ? kBT / Sh::N2 : 1;  // one team of N^2 threads per cell
   while (cb > 1 && (Sh::N3 + 16) * 8 + (size_t)cb * Sh::TEAM * 8 > kBudget) --cb;
   return cb;
 }
