@@ -219,7 +219,8 @@ sfx_status sfx_tabulate_1d(sfx_nodes nodes, int ndof1d, sfx_nodes qrule, int nq,
  *   x, y   device, ndof x nrhs doubles (x read-only; must not alias y)
  *   nrhs   1 <= nrhs <= 64
  *   accumulate = 0: y is overwritten (every entry written, whatever it held:
- *   for DQ_p and the FP64 Q_p kernels each dof's first contribution is stored,
+ *   for DQ_p and the FP64 Q_p kernels with one right-hand side, and split-
+ *   precision DQ_p with up to four, each dof's first contribution is stored;
  *   otherwise y is zeroed on `stream` first); 1: y += action.
  *   params may be NULL (defaults: Helmholtz alpha=1, beta=-1; NCF alpha=beta=1;
  *   NCE alpha=0, beta=1; hyperelastic mu=1, lambda=10).

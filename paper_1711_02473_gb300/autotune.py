@@ -113,11 +113,13 @@ def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims
 
 
 # kind -> (family, forms timed, precision, degrees it has, tuning mesh)
-STRUCTURED = {"hdivcurl": ("NCF", ("ncf_mass_divdiv",), "fp64", range(1, 9), (16, 16, 16)),
-              "elastic": ("VQ", ("neohooke",), "fp64", range(1, 9), (12, 12, 12)),
-              "linearised": ("VQ", ("svk",), "fp64", range(1, 9), (12, 12, 12)),
-              "linearised_mixed": ("VQ", ("svk",), "tf32x3", range(1, 9), (12, 12, 12)),
-              "hdivcurl_mixed": ("NCE", ("nce_curlcurl",), "tf32x3", range(1, 9), (16, 16, 16))}
+# (meshes large enough that a colour launch fills the GPU at every candidate: on a
+# smaller one the fewest cells per CTA win only because they give more CTAs)
+STRUCTURED = {"hdivcurl": ("NCF", ("ncf_mass_divdiv",), "fp64", range(1, 9), (32, 32, 32)),
+              "elastic": ("VQ", ("neohooke",), "fp64", range(1, 9), (24, 24, 24)),
+              "linearised": ("VQ", ("svk",), "fp64", range(1, 9), (24, 24, 24)),
+              "linearised_mixed": ("VQ", ("svk",), "tf32x3", range(1, 9), (24, 24, 24)),
+              "hdivcurl_mixed": ("NCE", ("nce_curlcurl",), "tf32x3", range(1, 9), (32, 32, 32))}
 
 
 def tune_structured(ctx, kind, degrees, torch, flush, reps):

@@ -890,12 +890,20 @@ extern "C" sfx_status sfx_tabulate_1d(sfx_nodes nodes, int ndof1d, sfx_nodes qru
 // ----------------------------------------------------------------- assembly
 // Overwriting scalar actions skip the memset of y where that measured faster
 // on GB300: DQ_p (every contribution is its dof's only one: plain stores, no
-// table) at every precision, and Q_p in the FP64 kernels (the first
-// contribution to each dof is stored, the later ones added; see d_first).
-// The split-precision Q_p kernels keep the memset: there the per-dof table
-// lookup and the split between stores and reductions within a warp cost more
-// than the memset saves (2-7% at p = 7, 8).
-static void set_first_touch(const sfx_space* sp, sfx_precision prec, ActArgs* a) {
+// table), and Q_p in the FP64 kernels (the first contribution to each dof is
+// stored, the later ones added; see d_first).  The split-precision Q_p kernels
+// keep the memset: there the per-dof table lookup and the split between stores
+// and reductions within a warp cost more than the memset saves (2-7% at p = 7,
+// 8).  With several right-hand sides (y is dof-major, RHS fastest) each store
+// covers part of a DRAM sector, which costs more than the memset's full
+// sectors once y does not fit in L2: stores only for one RHS in FP64 (DQ_8,
+// 16 RHS: 58.5 ms against 57.9 with the memset) and up to four in split
+// precision (4 RHS: 4.06 against 4.18; 16 RHS: 20.35 against 20.17).
+static bool first_touch_pays(sfx_precision prec, int nrhs) {
+  return nrhs == 1 || (prec != SFX_PREC_FP64 && nrhs <= 4);
+}
+static void set_first_touch(const sfx_space* sp, sfx_precision prec, int nrhs, ActArgs* a) {
+  if (!first_touch_pays(prec, nrhs)) return;
   if (sp->family == SFX_DQ) a->first_all = 1;
   else if (sp->family == SFX_Q && prec == SFX_PREC_FP64) a->first = sp->d_first;
 }
@@ -932,7 +940,7 @@ extern "C" sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx
   ActArgs a{};
   // overwrite without a memset where the kernels store each dof's first
   // contribution (the scalar sum-factorised and collocated kernels)
-  if (!accumulate && algo != SFX_ALGO_NAIVE) set_first_touch(sp, prec, &a);
+  if (!accumulate && algo != SFX_ALGO_NAIVE) set_first_touch(sp, prec, nrhs, &a);
   if (!accumulate && !a.first && !a.first_all) {
     if (cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess) return SFX_ERR_CUDA;
   }
@@ -1018,7 +1026,7 @@ extern "C" sfx_status sfx_assemble_weighted_action(sfx_ctx* ctx, const sfx_space
   if (prec != SFX_PREC_FP64) return SFX_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   ActArgs a{};
-  if (!accumulate) set_first_touch(sp, prec, &a);
+  if (!accumulate) set_first_touch(sp, prec, nrhs, &a);
   if (!accumulate && !a.first && !a.first_all) {
     if (cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess) return SFX_ERR_CUDA;
   }
@@ -1516,9 +1524,10 @@ static ActArgs plan_args(const sfx_plan* pl, const double* x) {
   a.r0 = 0;
   a.r1 = pl->nrhs;
   a.status = pl->ctx->d_status;
-  // every (cell, l) of a p-adaptive DQ space is its dof's only pair: the
-  // kernels store b^K into y, which therefore needs no memset
-  a.first_all = 1;
+  // every (cell, l) of a p-adaptive DQ space is its dof's only pair: with one
+  // right-hand side the kernels store b^K into y, which then needs no memset
+  // (with several, y is zeroed and added to; see first_touch_pays)
+  a.first_all = first_touch_pays(SFX_PREC_FP64, pl->nrhs) ? 1 : 0;
   return a;
 }
 
@@ -1528,9 +1537,12 @@ extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* co
   if (!pl || !x || !y) return SFX_ERR_ARG;
   for (int f = 0; f < pl->nforms; ++f)
     if (!y[f] || y[f] == x) return SFX_ERR_ARG;
+  const size_t ybytes = (size_t)pl->ndof * pl->nrhs * sizeof(double);
+  const bool zero = !first_touch_pays(SFX_PREC_FP64, pl->nrhs);
   cudaStream_t s = (cudaStream_t)stream;
   if (mode == SFX_EXEC_PER_LAUNCH) {
     for (int f = 0; f < pl->nforms; ++f) {
+      if (zero && cudaMemsetAsync(y[f], 0, ybytes, s) != cudaSuccess) return SFX_ERR_CUDA;
       for (int p = 1; p <= kMaxDeg; ++p) {
         const int64_t cnt = pl->deg_end[p] - pl->deg_begin[p];
         if (cnt == 0) continue;
@@ -1570,7 +1582,9 @@ extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* co
     }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SFX_ERR_CUDA;
-    int e = (int)cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
+    int e = 0;
+    for (int f = 0; f < pl->nforms && zero && !e; ++f) e = (int)cudaMemsetAsync(y[f], 0, ybytes, pl->cap);
+    if (!e) e = (int)cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
     if (!e && b.ntiles > 0) e = batched_launch(b, pl->grid, pl->smem, pl->cap);
     cudaError_t ee = cudaStreamEndCapture(pl->cap, &g);
     if (e || ee != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); return SFX_ERR_CUDA; }
@@ -1631,7 +1645,7 @@ extern "C" sfx_status sfx_assemble_action_stored(sfx_ctx* ctx, sfx_form form, co
   sfx_form_params pr = params ? *params : default_params(form);
   cudaStream_t s = (cudaStream_t)stream;
   ActArgs a{};
-  if (!accumulate) set_first_touch(sp, prec, &a);
+  if (!accumulate) set_first_touch(sp, prec, nrhs, &a);
   if (!accumulate && !a.first && !a.first_all &&
       cudaMemsetAsync(y, 0, (size_t)sp->ndof * nrhs * sizeof(double), s) != cudaSuccess)
     return SFX_ERR_CUDA;

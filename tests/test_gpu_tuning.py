@@ -109,7 +109,7 @@ def test_autotune_other_kinds_small(gpu):
     hyperelastic states keep det F > 0) and sets one of its candidates."""
     sfx, torch, ctx = gpu
     from paper_1711_02473_gb300 import autotune
-    kinds = ("hdivcurl", "elastic", "linearised", "linearised_mixed", "batched", "mixed", "mixed_ws")
+    kinds = ("hdivcurl", "elastic", "linearised", "linearised_mixed", "hdivcurl_mixed", "batched", "mixed", "mixed_ws")
     try:
         table = autotune.tune(ctx, degrees=[3], kinds=kinds, dims=(8, 8, 8), reps=1)
         assert ctx.sync_status() == 0
@@ -125,7 +125,9 @@ def test_autotune_other_kinds_small(gpu):
                                                ("hdivcurl", "NCE", "nce_curlcurl", "fp64"),
                                                ("elastic", "VQ", "neohooke", "fp64"),
                                                ("linearised", "VQ", "svk", "fp64"),
-                                               ("linearised_mixed", "VQ", "neohooke", "tf32x3")])
+                                               ("linearised_mixed", "VQ", "neohooke", "tf32x3"),
+                                               ("hdivcurl_mixed", "NCF", "ncf_mass_divdiv", "tf32x3"),
+                                               ("hdivcurl_mixed", "NCE", "nce_curlcurl", "bf16x3")])
 @pytest.mark.parametrize("p", [1, 3])
 def test_structured_cells_per_cta_bitwise(gpu, kind, fam, form, prec, p):
     """H(div)/H(curl) and hyperelastic kernels: cells per CTA (tuned, clamped
