@@ -103,3 +103,36 @@ def test_overwrite_inverted_cell(gpu):
         assert torch.equal(y_over, y_acc)
         assert np.isfinite(y_over.cpu().numpy()).all()
         assert ctx.sync_status() & sfx.DEV_INVERTED
+
+
+@pytest.mark.parametrize("fam,p,prec", [("Q", 8, "tf32x3"), ("Q", 3, "fp64"), ("DQ", 5, "tf32x3")])
+def test_action_in_cuda_graph(gpu, fam, p, prec):
+    """An action captured in a CUDA graph (its colour launches, programmatic
+    dependents of one another, become graph nodes) replays to the same result
+    as the eager call, also after the input changes in place."""
+    sfx, torch, ctx = gpu
+    mesh = sfx.Mesh.box(ctx, 6, 5, 4, perturb=0.1, seed=0)
+    sp = sfx.Space(mesh, fam, p)
+    x = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
+    y_eager = torch.empty_like(x)
+    sfx.sfx_assemble_action(ctx, "helmholtz", sp, x, y_eager, precision=prec)
+    y = torch.full_like(x, float("nan"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up on the capture stream
+        sfx.sfx_assemble_action(ctx, "helmholtz", sp, x, y, precision=prec, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sfx.sfx_assemble_action(ctx, "helmholtz", sp, x, y, precision=prec, stream=s)
+    y.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, y_eager)
+    x2 = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=2)).cuda()
+    x.copy_(x2)
+    g.replay()
+    sfx.sfx_assemble_action(ctx, "helmholtz", sp, x2, y_eager, precision=prec)
+    torch.cuda.synchronize()
+    assert torch.equal(y, y_eager)
+    assert ctx.sync_status() == 0
