@@ -17,12 +17,17 @@ SFX_DEFINE_TAB_UPLOAD(upload_tab_batched)
 
 namespace {
 
-// threads per CTA and dynamic shared memory of the persistent kernel
+// threads per CTA and dynamic shared memory of the persistent kernel: the
+// kernel's registers (the bodies of every degree and form in one kernel) allow
+// one CTA per SM, so it takes nearly all the shared memory a CTA can have
+// (227 KB less 1 KB for the kernel's static variables; a tile of the Helmholtz
+// form then holds three DQ_8 cells instead of two; the other forms and
+// degrees already had their team limit)
 #ifndef SFX_BATCH_THREADS
 #define SFX_BATCH_THREADS 256
 #endif
 #ifndef SFX_BATCH_SMEM_KB
-#define SFX_BATCH_SMEM_KB 200
+#define SFX_BATCH_SMEM_KB 226
 #endif
 constexpr int kBT = SFX_BATCH_THREADS;
 constexpr size_t kBudget = (size_t)SFX_BATCH_SMEM_KB * 1024;
