@@ -319,15 +319,23 @@ template <int P, bool NCF, int PREC>
 int launch_hm(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
   using Sh = HMShape<P, NCF>;
   // cells per CTA: the most (up to 32) for which two CTAs fit in one SM's
-  // shared memory, else the most that fit 200 KB; the tuned value if set
+  // shared memory, else the most that fit 200 KB; when this launch's cells
+  // then fill less than one wave of two CTAs per SM, the fewest that still fit
+  // one wave (more CTAs, none in a second wave); the tuned value if set
   int cb = 32;
   while (cb > 1 && Sh::bytes(cb) > 110 * 1024) --cb;
   if (Sh::bytes(cb) > 110 * 1024) cb = 1;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return (int)e;
+  const int64_t slots = 2 * (int64_t)(nsm > 0 ? nsm : 1);
+  if (a.ncells <= slots * cb) cb = (int)((a.ncells + slots - 1) / slots);
   cb = tuned_team_cells(SFX_TUNE_HDIVCURL_MIXED, P, cb, 32, Sh::bytes(0), Sh::bytes(1) - Sh::bytes(0), 200 * 1024);
   const size_t smem = Sh::bytes(cb);
   if (smem > 227 * 1024) return -1;
   auto kern = k_action_hdivcurl_mixed<P, NCF, PREC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int64_t grid = (a.ncells + cb - 1) / cb;
   kern<<<(unsigned)grid, kThreads, smem, s>>>(a, ncell_total, cb);

@@ -370,5 +370,62 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
   }
 }
 
+// ------------------------------------------------------------------ launcher
+template <int N, bool DQ, int FORM, int PREC>
+int launch_mixed_one(const ActArgs& a, int64_t ncell_total, cudaStream_t s) {
+  using Sh = MixedShape<N, FORM>;
+  const bool stored = a.qd32 != nullptr;
+  const bool geo_once = a.nrhs > 1;
+  const size_t budget = 200 * 1024;
+  // cells per CTA: the autotuned value, else enough fibers for dense tiles
+  int cb = tuned_cells_per_cta(stored ? SFX_TUNE_SCALAR_MIXED_STORED : SFX_TUNE_SCALAR_MIXED, N - 1,
+                               (N <= 3) ? 32 : 16);
+  if (cb < 1) cb = 1;
+  while (cb > 1 && Sh::bytes(cb, geo_once, stored) > budget) --cb;
+  const size_t smem = Sh::bytes(cb, geo_once, stored);
+  auto kern = stored ? k_action_scalar_mixed<N, DQ, FORM, PREC, true> : k_action_scalar_mixed<N, DQ, FORM, PREC, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  const int64_t grid = (a.ncells + cb - 1) / cb;
+  e = launch_kernel(kern, (unsigned)grid, Sh::NT, smem, s, a.overlap_prev != 0, a, ncell_total, cb, geo_once);
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaGetLastError();
+}
+
+template <int N, bool DQ, int PREC>
+int mixed_dispatch_form(sfx_form form, const ActArgs& a, int64_t nc, cudaStream_t s) {
+  switch (form) {
+    case SFX_MASS: return launch_mixed_one<N, DQ, SFX_MASS, PREC>(a, nc, s);
+    case SFX_LAPLACE: return launch_mixed_one<N, DQ, SFX_LAPLACE, PREC>(a, nc, s);
+    case SFX_HELMHOLTZ: return launch_mixed_one<N, DQ, SFX_HELMHOLTZ, PREC>(a, nc, s);
+    default: return -1;
+  }
+}
+
+template <int N, int PREC>
+int mixed_dispatch(bool dq, sfx_form form, const ActArgs& a, int64_t nc, cudaStream_t s) {
+  return dq ? mixed_dispatch_form<N, true, PREC>(form, a, nc, s) : mixed_dispatch_form<N, false, PREC>(form, a, nc, s);
+}
+
+// Per-colour launch of the split-precision scalar action in format PREC (one
+// instantiation per translation unit).
+template <int PREC>
+int launch_scalar_mixed_prec(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream) {
+  const bool dq = sp->family == SFX_DQ;
+  const int64_t nc = sp->mesh->ncell;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (sp->p) {
+    case 1: return mixed_dispatch<2, PREC>(dq, form, a, nc, s);
+    case 2: return mixed_dispatch<3, PREC>(dq, form, a, nc, s);
+    case 3: return mixed_dispatch<4, PREC>(dq, form, a, nc, s);
+    case 4: return mixed_dispatch<5, PREC>(dq, form, a, nc, s);
+    case 5: return mixed_dispatch<6, PREC>(dq, form, a, nc, s);
+    case 6: return mixed_dispatch<7, PREC>(dq, form, a, nc, s);
+    case 7: return mixed_dispatch<8, PREC>(dq, form, a, nc, s);
+    case 8: return mixed_dispatch<9, PREC>(dq, form, a, nc, s);
+  }
+  return -1;
+}
+
 }  // namespace
 }  // namespace sfx
