@@ -369,7 +369,8 @@ def main():
         if not args.no_extras:
             # the other workloads' kernels: tiles of the p-adaptive batch (config 5), cells per CTA of the
             # H(div)/H(curl) and hyperelastic kernels (config 3 and the linearised operator)
-            kinds = kinds + ["batched", "hdivcurl", "elastic", "linearised", "linearised_mixed", "hdivcurl_mixed"]
+            kinds = kinds + ["batched", "batched_mixed", "hdivcurl", "elastic", "linearised", "linearised_mixed",
+                             "hdivcurl_mixed"]
         degrees = sorted({p for _, p, _ in wl})
         tuning = autotune.ensure(ctx, torch.cuda.get_device_name(local), degrees=degrees, kinds=kinds)
     probes = probe_rates(sfx, torch)
@@ -804,7 +805,8 @@ def extra_linearised(sfx, torch, ctx, inputs, flush, stream):
 def extra_padaptive(sfx, torch, ctx, inputs, flush, stream):
     """p-adaptive batching: 200,000 cells (40x50x100), p in 1..8 with
     P(p) ~ 1/p, DQ_p per cell, Laplace + mass on 16 RHS (seeds 0..15): one
-    graph-captured persistent launch vs one launch per (form, degree, RHS)."""
+    graph-captured persistent launch vs one launch per (form, degree, RHS), in
+    FP64 and with the TF32x3 tile body."""
     dims = _d(40, 50, 100)
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     deg = inputs.padaptive_degrees(int(np.prod(dims)), 8, seed=2)
@@ -827,7 +829,22 @@ def extra_padaptive(sfx, torch, ctx, inputs, flush, stream):
         "roofline": {"bound": "alu", "achieved": round(fl / (tg * 1e-3) / 1e9, 2), "peak": round(FP64_PEAK_GOPS, 1),
                      "unit": "G FP64 op/s", "frac": round(fl / (tg * 1e-3) / 1e9 / FP64_PEAK_GOPS, 4)},
         "tile_cells_tuned": {str(p): sfx.sfx_tune_get_cells_per_cta("batched", p) for p in range(1, 9)}}
-    del xd, ys, plan, mesh
+    # the same batch with the split-precision tile body (TF32x3): one graph
+    # launch, its speed-up over the FP64 batch and its error against it
+    ref = [y.clone() for y in ys]
+    plan.close()
+    planm = sfx.Plan(ctx, mesh, deg, forms, nrhs=R, precision="tf32x3")
+    tm = _time(torch, stream, flush, lambda: planm.execute(xd, ys, mode="graph", stream=stream))
+    tml = _time(torch, stream, flush, lambda: planm.execute(xd, ys, mode="per_launch", stream=stream), reps=2, warm=1)
+    planm.execute(xd, ys, mode="graph", stream=stream)
+    torch.cuda.synchronize()
+    out["tf32x3"] = {"graph_ms": round(tm, 3), "per_launch_ms": round(tml, 3), "graph_dofs_per_s": work / (tm * 1e-3),
+                     "speedup_vs_fp64_graph": tg / tm, "launches_per_launch": ndeg * len(forms),
+                     "rel_err_vs_fp64": max(float((y - r).abs().max() / r.abs().max()) for y, r in zip(ys, ref)),
+                     "tile_cells_tuned": {str(p): sfx.sfx_tune_get_cells_per_cta("batched_mixed", p)
+                                          for p in range(1, 9)}}
+    planm.close()
+    del xd, ys, ref, mesh
     return out
 
 

@@ -399,7 +399,9 @@ sfx_status sfx_tune_get_cells_per_cta(int kernel, int degree, int* cells);
 /* Kinds 6-10 of the table above: cells per CTA of the FP64 NCF / NCE actions
  * (6), the FP64 hyperelastic residual (7), the FP64 linearised hyperelastic
  * action (8), its split-precision version (9) and the split-precision NCF /
- * NCE actions (10); 0 = the launcher's rule
+ * NCE actions (10); kind 11: cells per tile of the split-precision p-adaptive
+ * batch (sfx_plan_create_padaptive_prec, at most its layout's count); 0 = the
+ * launcher's rule
  * (the most cells for which two CTAs share an SM, else one larger CTA), and a
  * value that would not fit the kernel's team limit or shared memory is
  * reduced until it does.
@@ -466,6 +468,18 @@ typedef struct sfx_plan sfx_plan;
 sfx_status sfx_plan_create_padaptive(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree, int nforms,
                                      const sfx_form* forms, const sfx_form_params* params, int nrhs,
                                      sfx_plan** out);
+/* The same plan with the tile body in `prec`: FP64 (as above), or TF32X3 /
+ * BF16X3, whose tiles run the split-precision scalar body (the 1D
+ * contractions as split tensor-core products with FP32 accumulation; the
+ * geometry, weight scaling and scatter in FP64; Sec. 3.3 with the
+ * precision choice of sfx_assemble_action).  Its tile sizes are those of that
+ * body's shared-memory layout for the plan's forms; kind 11 of
+ * sfx_tune_set_cells_per_cta sets smaller ones.  PER_LAUNCH mode then runs one
+ * launch per (form, degree) with all right-hand sides.  Errors as above, and
+ * SFX_ERR_ARG for another precision. */
+sfx_status sfx_plan_create_padaptive_prec(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree, int nforms,
+                                          const sfx_form* forms, const sfx_form_params* params, int nrhs,
+                                          sfx_precision prec, sfx_plan** out);
 /* Total dofs, number of tiles and a host view of the ncell+1 dof offsets. */
 sfx_status sfx_plan_info(const sfx_plan* plan, int64_t* ndof, int64_t* ntiles, const int64_t** cell_offset);
 

@@ -32,7 +32,8 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_mesh_destroy", "sfx_space_create", "sfx_space_info", "sfx_space_colours", "sfx_space_destroy",
            "sfx_tabulate_1d",
            "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices",
-           "sfx_plan_create_padaptive", "sfx_plan_info", "sfx_plan_execute", "sfx_plan_destroy",
+           "sfx_plan_create_padaptive", "sfx_plan_create_padaptive_prec", "sfx_plan_info", "sfx_plan_execute",
+           "sfx_plan_destroy",
            "sfx_padaptive_action_noalloc", "sfx_qdata_create", "sfx_qdata_destroy",
            "sfx_assemble_action_stored", "sfx_tune_set_cells_per_cta", "sfx_tune_get_cells_per_cta",
            "sfx_tune_set_warp_specialised", "sfx_tune_get_warp_specialised", "sfx_set_wait_limit",
@@ -42,7 +43,8 @@ EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_s
            "sfx_csr_create", "sfx_csr_info", "sfx_csr_assemble", "sfx_csr_spmv", "sfx_csr_destroy",
            "sfx_assemble_weighted_action", "sfx_assemble_weighted_cell_matrices"]
 TUNE_KERNEL = {"fp64": 0, "mixed": 1, "mixed_stored": 2, "elastic_mixed": 3, "mixed_ws": 4, "batched": 5,
-               "hdivcurl": 6, "elastic": 7, "linearised": 8, "linearised_mixed": 9, "hdivcurl_mixed": 10}
+               "hdivcurl": 6, "elastic": 7, "linearised": 8, "linearised_mixed": 9, "hdivcurl_mixed": 10,
+               "batched_mixed": 11}
 QDATA = {"fp64": 1, "fp32": 2, "both": 3}
 EXEC = {"graph": 0, "per_launch": 1}
 
@@ -106,6 +108,7 @@ def lib():
         L.sfx_assemble_cell_vectors.argtypes = [P, i, C.POINTER(_Params), P, P, i, P, i64, P, i, P]
         L.sfx_assemble_cell_matrices.argtypes = [P, i, C.POINTER(_Params), P, i64, i64, P, i, i, P]
         L.sfx_plan_create_padaptive.argtypes = [P, P, P, i, P, P, i, C.POINTER(P)]
+        L.sfx_plan_create_padaptive_prec.argtypes = [P, P, P, i, P, P, i, i, C.POINTER(P)]
         L.sfx_plan_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(P)]
         L.sfx_plan_execute.argtypes = [P, P, P, i, P]
         L.sfx_plan_destroy.argtypes = [P]
@@ -502,20 +505,23 @@ def sfx_padaptive_action_noalloc(ctx, mesh, degree, cell_offset, form, x, y, nrh
 
 class Plan:
     """Batched actions on a p-adaptive DQ mesh (sfx_plan_*): one persistent,
-    graph-captured launch for all forms and right-hand sides."""
+    graph-captured launch for all forms and right-hand sides; precision "fp64"
+    or a split precision ("tf32x3", "bf16x3") for the tile body."""
 
-    def __init__(self, ctx, mesh, degree, forms, nrhs=1, params=None):
+    def __init__(self, ctx, mesh, degree, forms, nrhs=1, params=None, precision="fp64"):
         degree = np.ascontiguousarray(degree, dtype=np.int32)
         self.ctx, self.mesh, self.forms, self.nrhs = ctx, mesh, list(forms), nrhs
+        self.precision = precision
         fa = (C.c_int * len(forms))(*[FORM[f] for f in forms])
         pa = None
         if params is not None:
             arr = (_Params * len(forms))(*[_Params(*(tuple(p) + (0.0,) * (4 - len(p)))) for p in params])
             pa = C.cast(arr, C.c_void_p)
         self.h = C.c_void_p()
-        _check(lib().sfx_plan_create_padaptive(ctx.h, mesh.h, degree.ctypes.data_as(C.c_void_p), len(forms),
-                                               C.cast(fa, C.c_void_p), pa, nrhs, C.byref(self.h)),
-               "sfx_plan_create_padaptive")
+        _check(lib().sfx_plan_create_padaptive_prec(ctx.h, mesh.h, degree.ctypes.data_as(C.c_void_p), len(forms),
+                                                    C.cast(fa, C.c_void_p), pa, nrhs, PRECISION[precision],
+                                                    C.byref(self.h)),
+               "sfx_plan_create_padaptive_prec")
         nd, nt, off = C.c_int64(), C.c_int64(), C.c_void_p()
         _check(lib().sfx_plan_info(self.h, C.byref(nd), C.byref(nt), C.byref(off)), "sfx_plan_info")
         self.ndof, self.ntiles = nd.value, nt.value

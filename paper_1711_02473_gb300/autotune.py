@@ -1,6 +1,6 @@
 """Autotuner for the cells-per-CTA of the scalar action kernels.
 
-For each kernel kind ("fp64", "mixed", "mixed_stored", "mixed_ws", "batched", and the
+For each kernel kind ("fp64", "mixed", "mixed_stored", "mixed_ws", "batched", "batched_mixed", and the
 structured-element kinds "hdivcurl", "elastic", "linearised", "linearised_mixed", "hdivcurl_mixed") and
 degree it times
 the Q_p Laplace action on a tuning mesh for every candidate value (median of a
@@ -31,7 +31,7 @@ def candidates(kind, p):
         return sorted({max(1, top // d) for d in (1, 2, 3, 4, 6)})
     if kind == "mixed_ws":
         return [-1, 1, 2, 3, 4, 6, 8] if p >= 3 else []
-    if kind == "batched":
+    if kind in ("batched", "batched_mixed"):
         return [1, 2, 4, 8, 16, 32]
     if kind in ("hdivcurl", "elastic", "linearised"):  # teams of (p+1)^2 threads, at most 256 threads
         top = max(1, 256 // n2)
@@ -72,9 +72,10 @@ def tune(ctx, degrees=range(1, 9), kinds=("fp64", "mixed", "mixed_stored"), dims
     mesh = Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device="cuda")
     table = {}
-    if "batched" in kinds:
-        table["batched"] = tune_batched(ctx, degrees, torch, flush, reps)
-        kinds = [k for k in kinds if k != "batched"]
+    for bk, prec in (("batched", "fp64"), ("batched_mixed", "tf32x3")):
+        if bk in kinds:
+            table[bk] = tune_batched(ctx, degrees, torch, flush, reps, kind=bk, precision=prec)
+            kinds = [k for k in kinds if k != bk]
     for k in [k for k in kinds if k in STRUCTURED]:
         table[k] = tune_structured(ctx, k, degrees, torch, flush, reps)
     kinds = [k for k in kinds if k not in STRUCTURED]
@@ -156,7 +157,7 @@ def tune_structured(ctx, kind, degrees, torch, flush, reps):
     return out
 
 
-def tune_batched(ctx, degrees, torch, flush, reps, dims=(20, 20, 20), nrhs=4):
+def tune_batched(ctx, degrees, torch, flush, reps, dims=(20, 20, 20), nrhs=4, kind="batched", precision="fp64"):
     """Cells per tile of the persistent p-adaptive batch, per degree: a DQ_p
     mesh of that single degree, Laplace + mass on nrhs right-hand sides, one
     graph launch per candidate (a plan per candidate: tiles are cut when the
@@ -168,15 +169,15 @@ def tune_batched(ctx, degrees, torch, flush, reps, dims=(20, 20, 20), nrhs=4):
     for p in degrees:
         res = {}
         deg = np.full(ncell, p, dtype=np.int32)
-        for cb in candidates("batched", p):
-            sfx_tune_set_cells_per_cta("batched", p, cb)
-            plan = Plan(ctx, mesh, deg, ["laplace", "mass"], nrhs=nrhs)
+        for cb in candidates(kind, p):
+            sfx_tune_set_cells_per_cta(kind, p, cb)
+            plan = Plan(ctx, mesh, deg, ["laplace", "mass"], nrhs=nrhs, precision=precision)
             x = torch.from_numpy(inputs.random_vector(plan.ndof * nrhs, 1, seed=1)).cuda()
             ys = [torch.empty_like(x) for _ in range(2)]
             res[cb] = _time(torch, lambda: plan.execute(x, ys), reps, flush)
             plan.close()
         best = min(res, key=res.get)
-        sfx_tune_set_cells_per_cta("batched", p, best)
+        sfx_tune_set_cells_per_cta(kind, p, best)
         out[p] = {"best": best, "ms": {str(k): round(v, 4) for k, v in res.items()}}
     return out
 

@@ -11,4 +11,9 @@ int launch_action_scalar_mixed_tf32(const sfx_space* sp, sfx_form form, const Ac
   return launch_scalar_mixed_prec<SFX_PREC_TF32X3>(sp, form, a, stream);
 }
 
+int launch_scalar_mixed_degree_tf32(int p, bool dq, sfx_form form, const ActArgs& a, int64_t ncell_total,
+                                   void* stream) {
+  return launch_scalar_mixed_degree<SFX_PREC_TF32X3>(p, dq, form, a, ncell_total, stream);
+}
+
 }  // namespace sfx

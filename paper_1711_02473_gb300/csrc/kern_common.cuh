@@ -49,6 +49,12 @@ cudaError_t launch_kernel(void (*k)(P...), unsigned grid, unsigned block, size_t
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
+// Global dof of local index l of a cell: the space's cell-node map, or, for a
+// p-adaptive DQ mesh (no map), the cell's dof offset + l.
+__device__ __forceinline__ int64_t cell_dof(const ActArgs& a, int64_t cell, int l, int nloc) {
+  return a.map ? (int64_t)__ldg(&a.map[cell * nloc + l]) : __ldg(&a.dq_off[cell]) + l;
+}
+
 // Whether (cell, l) writes its dof first in an overwriting action (ActArgs
 // first / first_all): that pair stores its value (0 for a skipped cell), every
 // later pair of the dof, in a later colour launch, adds to it.

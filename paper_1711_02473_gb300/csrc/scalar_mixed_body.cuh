@@ -144,14 +144,16 @@ __device__ __forceinline__ double mixed_point_flux(const double* tab, const doub
 // COLL: the collocated Gauss-Lobatto rule on the GLL nodes of Q_p (the points
 // are the nodes: B = I, derivative table = GLL collocation matrix, geometry at
 // the GLL points with the GLL weights; Sec. 2.5 and "underintegration" in 4.1).
-template <int N, bool DQ, int FORM, int PREC, bool STORED, bool COLL = false>
-__global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed(const ActArgs a, const int64_t ncell_total,
-                                                                  const int cb, const bool geo_once) {
+// One tile: the cb cells of slots slot0 .. slot0+cb-1, run by the NT threads
+// of the CTA (the per-colour kernel below, and the persistent p-adaptive batch
+// with NT = its block size).  smd: the tile's shared memory (MixedShape::bytes).
+template <int N, bool DQ, int FORM, int PREC, bool STORED, bool COLL, int NT>
+__device__ __forceinline__ void scalar_tile_mixed(const ActArgs& a, const int64_t ncell_total, const int64_t slot0,
+                                                  const int cb, const bool geo_once, double* smd) {
   using Sh = MixedShape<N, FORM>;
-  constexpr int N2 = Sh::N2, N3 = Sh::N3, NT = Sh::NT;
+  constexpr int N2 = Sh::N2, N3 = Sh::N3;
   constexpr bool LAP = Sh::LAP, MAS = Sh::MAS;
   const Tab1D& T = c_tab[N - 1];
-  extern __shared__ double smd[];
   // layout: [tables: 2 TabF][xq: 16 doubles][wq: 16 doubles][cells: doubles][cells: floats][flags]
   TabF* tabs = reinterpret_cast<TabF*>(smd);  // 0: B, 1: Dq
   double* xq = smd + (2 * sizeof(TabF)) / 8;
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
   }
   for (int c = tid; c < cb; c += NT) {
     int cell = -1;
-    if (!slot_cell(a, (int64_t)blockIdx.x * cb + c, ncell_total, &cell)) cell = -1;
+    if (!slot_cell(a, slot0 + c, ncell_total, &cell)) cell = -1;
     flags[2 * c] = cell;
     flags[2 * c + 1] = 0;
   }
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
     for (int i = tid; i < cb * N3; i += NT) {
       const int c = i / N3, l = i - c * N3;
       const int cell = flags[2 * c];
-      U[i] = cell >= 0 ? d2f_int(a.x[(int64_t)a.map[(int64_t)cell * N3 + l] * a.nrhs + r]) : 0.f;
+      U[i] = cell >= 0 ? d2f_int(a.x[cell_dof(a, cell, l, N3) * a.nrhs + r]) : 0.f;
     }
     __syncthreads();
     if (!DQ && !COLL) {
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
       for (int i = tid; i < cb * N3; i += NT) {
         const int c = i / N3, l = i - c * N3;
         if (flags[2 * c] < 0) continue;
-        const int64_t slot = (int64_t)blockIdx.x * cb + c;
+        const int64_t slot = slot0 + c;
         a.y[(slot * N3 + l) * a.nrhs + r] = !flags[2 * c + 1] ? f2d_int(U[i]) : 0.0;
       }
     } else {
@@ -343,13 +345,13 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
       // GS map entries per thread are loaded before the first write.
       constexpr int GS = 4;
       for (int i0 = tid; i0 < cb * N3; i0 += GS * NT) {
-        int dof[GS];
+        int64_t dof[GS];
 #pragma unroll
         for (int g = 0; g < GS; ++g) {
           const int i = i0 + g * NT;
           const int c = i / N3;
           const int cell = i < cb * N3 ? flags[2 * c] : -1;
-          dof[g] = cell >= 0 ? __ldg(&a.map[(int64_t)cell * N3 + (i - c * N3)]) : -1;
+          dof[g] = cell >= 0 ? cell_dof(a, cell, i - c * N3, N3) : -1;
         }
 #pragma unroll
         for (int g = 0; g < GS; ++g) {
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
           const int i = i0 + g * NT;
           const int c = i / N3;
           const bool ok = !flags[2 * c + 1];
-          double* yp = &a.y[(int64_t)dof[g] * a.nrhs + r];
+          double* yp = &a.y[dof[g] * a.nrhs + r];
           if (first_touch(a, flags[2 * c], i - c * N3, N3)) *yp = ok ? f2d_int(U[i]) : 0.0;
           else if (ok) atomicAdd(yp, f2d_int(U[i]));
         }
@@ -368,6 +370,14 @@ __global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed
         if (flags[2 * c] >= 0 && flags[2 * c + 1]) set_flag(a.status, SFX_DEV_INVERTED);
     __syncthreads();
   }
+}
+
+template <int N, bool DQ, int FORM, int PREC, bool STORED, bool COLL = false>
+__global__ void __launch_bounds__(MixedShape<N, FORM>::NT) k_action_scalar_mixed(const ActArgs a, const int64_t ncell_total,
+                                                                  const int cb, const bool geo_once) {
+  extern __shared__ double smd[];
+  scalar_tile_mixed<N, DQ, FORM, PREC, STORED, COLL, MixedShape<N, FORM>::NT>(a, ncell_total, (int64_t)blockIdx.x * cb,
+                                                                              cb, geo_once, smd);
 }
 
 // ------------------------------------------------------------------ launcher
@@ -407,14 +417,13 @@ int mixed_dispatch(bool dq, sfx_form form, const ActArgs& a, int64_t nc, cudaStr
   return dq ? mixed_dispatch_form<N, true, PREC>(form, a, nc, s) : mixed_dispatch_form<N, false, PREC>(form, a, nc, s);
 }
 
-// Per-colour launch of the split-precision scalar action in format PREC (one
-// instantiation per translation unit).
+// Launch of the split-precision scalar action in format PREC for one degree
+// (one instantiation per translation unit): a colour of a space, or the cells
+// of one degree of a p-adaptive plan (a.map null, a.dq_off set).
 template <int PREC>
-int launch_scalar_mixed_prec(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream) {
-  const bool dq = sp->family == SFX_DQ;
-  const int64_t nc = sp->mesh->ncell;
+int launch_scalar_mixed_degree(int p, bool dq, sfx_form form, const ActArgs& a, int64_t nc, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  switch (sp->p) {
+  switch (p) {
     case 1: return mixed_dispatch<2, PREC>(dq, form, a, nc, s);
     case 2: return mixed_dispatch<3, PREC>(dq, form, a, nc, s);
     case 3: return mixed_dispatch<4, PREC>(dq, form, a, nc, s);
@@ -425,6 +434,11 @@ int launch_scalar_mixed_prec(const sfx_space* sp, sfx_form form, const ActArgs& 
     case 8: return mixed_dispatch<9, PREC>(dq, form, a, nc, s);
   }
   return -1;
+}
+
+template <int PREC>
+int launch_scalar_mixed_prec(const sfx_space* sp, sfx_form form, const ActArgs& a, void* stream) {
+  return launch_scalar_mixed_degree<PREC>(sp->p, sp->family == SFX_DQ, form, a, sp->mesh->ncell, stream);
 }
 
 }  // namespace

@@ -217,6 +217,8 @@ static int upload_tables(const Tab1D* t) {
   if (!e) e = upload_tab_hdivcurl(t);
   if (!e) e = upload_tab_hdivcurl_mixed_tf32(t);
   if (!e) e = upload_tab_hdivcurl_mixed_bf16(t);
+  if (!e) e = upload_tab_batched_mixed_tf32(t);
+  if (!e) e = upload_tab_batched_mixed_bf16(t);
   if (!e) e = upload_tab_elastic(t);
   if (!e) e = upload_tab_elastic_mixed(t);
   if (!e) e = upload_tab_matrix(t);
@@ -261,6 +263,7 @@ constexpr int kBuiltinCells[SFX_TUNE_NKERNEL][kMaxDeg + 1] = {
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // FP64 linearised hyperelastic action (same)
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision linearised hyperelastic action (same)
     {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision NCF / NCE actions (same)
+    {0, 0, 0, 0, 0, 0, 0, 0, 0},    // split-precision p-adaptive batch tiles (the layout's full count)
 };
 // by degree (needs n = p + 1 >= 4): on where it measured faster than the
 // one-role kernel on the 64^3 Laplace and Helmholtz actions (p = 4, 5, 6, 8:
@@ -1405,6 +1408,7 @@ struct sfx_plan {
   sfx_ctx* ctx = nullptr;
   const sfx_mesh* mesh = nullptr;
   int nforms = 0, nrhs = 1;
+  sfx_precision prec = SFX_PREC_FP64;  // tile body: FP64, or the split-precision body
   sfx_form forms[4];
   sfx_form_params params[4];
   int64_t ndof = 0;
@@ -1438,8 +1442,16 @@ extern "C" void sfx_plan_destroy(sfx_plan* pl) {
 extern "C" sfx_status sfx_plan_create_padaptive(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree,
                                                 int nforms, const sfx_form* forms, const sfx_form_params* params,
                                                 int nrhs, sfx_plan** out) {
+  return sfx_plan_create_padaptive_prec(ctx, mesh, degree, nforms, forms, params, nrhs, SFX_PREC_FP64, out);
+}
+
+extern "C" sfx_status sfx_plan_create_padaptive_prec(sfx_ctx* ctx, const sfx_mesh* mesh, const int32_t* degree,
+                                                     int nforms, const sfx_form* forms,
+                                                     const sfx_form_params* params, int nrhs, sfx_precision prec,
+                                                     sfx_plan** out) {
   if (!ctx || !mesh || !degree || !forms || !out || nforms < 1 || nforms > 4 || nrhs < 1 || nrhs > 64)
     return SFX_ERR_ARG;
+  if (prec != SFX_PREC_FP64 && prec != SFX_PREC_TF32X3 && prec != SFX_PREC_BF16X3) return SFX_ERR_ARG;
   if (ctx->device < 0 || mesh->ctx != ctx || !mesh->d_vmap) return SFX_ERR_ARG;
   *out = nullptr;
   for (int f = 0; f < nforms; ++f)
@@ -1453,6 +1465,7 @@ extern "C" sfx_status sfx_plan_create_padaptive(sfx_ctx* ctx, const sfx_mesh* me
   pl->mesh = mesh;
   pl->nforms = nforms;
   pl->nrhs = nrhs;
+  pl->prec = prec;
   for (int f = 0; f < nforms; ++f) {
     pl->forms[f] = forms[f];
     pl->params[f] = params ? params[f] : default_params(forms[f]);
@@ -1476,7 +1489,13 @@ extern "C" sfx_status sfx_plan_create_padaptive(sfx_ctx* ctx, const sfx_mesh* me
     pl->deg_end[p] = (int64_t)sorted.size();
   }
   sfx_status st = SFX_OK;
-  if (batched_config(pl->cb, &pl->smem, &pl->grid) != 0) st = SFX_ERR_CUDA;
+  int form_mask = 0;
+  for (int f = 0; f < nforms; ++f) form_mask |= 1 << (int)forms[f];
+  int ce = 0;
+  if (prec == SFX_PREC_FP64) ce = batched_config(pl->cb, &pl->smem, &pl->grid);
+  else if (prec == SFX_PREC_TF32X3) ce = batched_mixed_config_tf32(form_mask, nrhs, pl->cb, &pl->smem, &pl->grid);
+  else ce = batched_mixed_config_bf16(form_mask, nrhs, pl->cb, &pl->smem, &pl->grid);
+  if (ce != 0) st = SFX_ERR_CUDA;
   // tiles: largest degree first, then form, then cells
   for (int p = kMaxDeg; p >= 1 && !st; --p)
     for (int f = 0; f < nforms; ++f)
@@ -1527,7 +1546,7 @@ static ActArgs plan_args(const sfx_plan* pl, const double* x) {
   // every (cell, l) of a p-adaptive DQ space is its dof's only pair: with one
   // right-hand side the kernels store b^K into y, which then needs no memset
   // (with several, y is zeroed and added to; see first_touch_pays)
-  a.first_all = first_touch_pays(SFX_PREC_FP64, pl->nrhs) ? 1 : 0;
+  a.first_all = first_touch_pays(pl->prec, pl->nrhs) ? 1 : 0;
   return a;
 }
 
@@ -1538,7 +1557,7 @@ extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* co
   for (int f = 0; f < pl->nforms; ++f)
     if (!y[f] || y[f] == x) return SFX_ERR_ARG;
   const size_t ybytes = (size_t)pl->ndof * pl->nrhs * sizeof(double);
-  const bool zero = !first_touch_pays(SFX_PREC_FP64, pl->nrhs);
+  const bool zero = !first_touch_pays(pl->prec, pl->nrhs);
   cudaStream_t s = (cudaStream_t)stream;
   if (mode == SFX_EXEC_PER_LAUNCH) {
     for (int f = 0; f < pl->nforms; ++f) {
@@ -1546,6 +1565,20 @@ extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* co
       for (int p = 1; p <= kMaxDeg; ++p) {
         const int64_t cnt = pl->deg_end[p] - pl->deg_begin[p];
         if (cnt == 0) continue;
+        if (pl->prec != SFX_PREC_FP64) {
+          // split precision: one launch per (form, degree), all right-hand sides
+          ActArgs a = plan_args(pl, x);
+          a.cells = pl->d_sorted + pl->deg_begin[p];
+          a.ncells = cnt;
+          a.y = y[f];
+          a.alpha = pl->params[f].alpha;
+          a.beta = pl->params[f].beta;
+          const int e = pl->prec == SFX_PREC_TF32X3
+                            ? launch_scalar_mixed_degree_tf32(p, true, pl->forms[f], a, pl->mesh->ncell, stream)
+                            : launch_scalar_mixed_degree_bf16(p, true, pl->forms[f], a, pl->mesh->ncell, stream);
+          if (e != 0) return SFX_ERR_CUDA;
+          continue;
+        }
         for (int r = 0; r < pl->nrhs; ++r) {
           ActArgs a = plan_args(pl, x);
           a.cells = pl->d_sorted + pl->deg_begin[p];
@@ -1585,7 +1618,11 @@ extern "C" sfx_status sfx_plan_execute(sfx_plan* pl, const double* x, double* co
     int e = 0;
     for (int f = 0; f < pl->nforms && zero && !e; ++f) e = (int)cudaMemsetAsync(y[f], 0, ybytes, pl->cap);
     if (!e) e = (int)cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
-    if (!e && b.ntiles > 0) e = batched_launch(b, pl->grid, pl->smem, pl->cap);
+    if (!e && b.ntiles > 0) {
+      if (pl->prec == SFX_PREC_FP64) e = batched_launch(b, pl->grid, pl->smem, pl->cap);
+      else if (pl->prec == SFX_PREC_TF32X3) e = batched_mixed_launch_tf32(b, pl->nrhs, pl->grid, pl->smem, pl->cap);
+      else e = batched_mixed_launch_bf16(b, pl->nrhs, pl->grid, pl->smem, pl->cap);
+    }
     cudaError_t ee = cudaStreamEndCapture(pl->cap, &g);
     if (e || ee != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); return SFX_ERR_CUDA; }
     ee = cudaGraphInstantiate(&pl->exec, g, 0);

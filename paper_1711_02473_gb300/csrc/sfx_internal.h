@@ -199,6 +199,15 @@ int launch_vq_expand(const double* S, int64_t ncells, int n3, double* A, void* s
 int batched_config(int* cb_per_degree /*[kMaxDeg+1]*/, size_t* smem, int* grid);
 int batched_launch(const BatchArgs& b, int grid, size_t smem, void* stream);
 int batched_tile_sizes(int* cb_per_degree /*[kMaxDeg+1]*/);
+// The split-precision persistent batch (TF32x3 / BF16x3): tile sizes for the
+// plan's forms (bit f of form_mask: form f, SFX_MASS = 0) and RHS count.
+int batched_mixed_config_tf32(int form_mask, int nrhs, int* cb, size_t* smem, int* grid);
+int batched_mixed_config_bf16(int form_mask, int nrhs, int* cb, size_t* smem, int* grid);
+int batched_mixed_launch_tf32(const BatchArgs& b, int nrhs, int grid, size_t smem, void* stream);
+int batched_mixed_launch_bf16(const BatchArgs& b, int nrhs, int grid, size_t smem, void* stream);
+// One degree's cells of a split-precision scalar action (per-launch plan mode).
+int launch_scalar_mixed_degree_tf32(int p, bool dq, sfx_form form, const ActArgs& a, int64_t ncell_total, void* stream);
+int launch_scalar_mixed_degree_bf16(int p, bool dq, sfx_form form, const ActArgs& a, int64_t ncell_total, void* stream);
 int launch_qdata(const sfx_space* sp, sfx_qdata* q, uint32_t* status, void* stream);
 
 // Cells per CTA of the action kernels: the autotuner's choice per (kernel,
@@ -216,7 +225,8 @@ enum {
   SFX_TUNE_LINEARISED = 8,       // FP64 linearised hyperelastic action
   SFX_TUNE_LINEARISED_MIXED = 9, // split-precision linearised hyperelastic action
   SFX_TUNE_HDIVCURL_MIXED = 10,  // split-precision NCF / NCE actions
-  SFX_TUNE_NKERNEL = 11
+  SFX_TUNE_BATCHED_MIXED = 11,   // cells per tile of the split-precision p-adaptive batch
+  SFX_TUNE_NKERNEL = 12
 };
 // Tuned cells per CTA for the team-per-cell kernels: the tuned value if one
 // is set (at most maxcb, and reduced until the shared memory fits `limit`),
@@ -237,6 +247,8 @@ int upload_tab_scalar_mixed_ws_bf16(const Tab1D* t);
 int upload_tab_hdivcurl(const Tab1D* t);
 int upload_tab_hdivcurl_mixed_tf32(const Tab1D* t);
 int upload_tab_hdivcurl_mixed_bf16(const Tab1D* t);
+int upload_tab_batched_mixed_tf32(const Tab1D* t);
+int upload_tab_batched_mixed_bf16(const Tab1D* t);
 int upload_tab_elastic(const Tab1D* t);
 int upload_tab_elastic_mixed(const Tab1D* t);
 int upload_tab_matrix(const Tab1D* t);

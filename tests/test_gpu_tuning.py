@@ -109,7 +109,8 @@ def test_autotune_other_kinds_small(gpu):
     hyperelastic states keep det F > 0) and sets one of its candidates."""
     sfx, torch, ctx = gpu
     from paper_1711_02473_gb300 import autotune
-    kinds = ("hdivcurl", "elastic", "linearised", "linearised_mixed", "hdivcurl_mixed", "batched", "mixed", "mixed_ws")
+    kinds = ("hdivcurl", "elastic", "linearised", "linearised_mixed", "hdivcurl_mixed", "batched", "batched_mixed",
+             "mixed", "mixed_ws")
     try:
         table = autotune.tune(ctx, degrees=[3], kinds=kinds, dims=(8, 8, 8), reps=1)
         assert ctx.sync_status() == 0
