@@ -113,3 +113,18 @@ def test_mixed_plan_tile_sizes_bitwise(gpu):
     for y in outs[1:]:
         assert torch.equal(outs[0], y)
     assert ctx.sync_status() == 0
+
+
+def test_mixed_plan_argument_errors(gpu):
+    """An unknown precision is an argument error; a degree out of range too."""
+    import ctypes as C
+    sfx, torch, ctx = gpu
+    mesh = sfx.Mesh.box(ctx, 2, 2, 2)
+    deg = np.full(8, 2, dtype=np.int32)
+    forms = (C.c_int * 1)(sfx.FORM["laplace"])
+    h = C.c_void_p()
+    rc = sfx.lib().sfx_plan_create_padaptive_prec(ctx.h, mesh.h, deg.ctypes.data_as(C.c_void_p), 1,
+                                                  C.cast(forms, C.c_void_p), None, 1, 7, C.byref(h))
+    assert rc != 0 and not h.value
+    with pytest.raises(sfx.SfxError):
+        sfx.Plan(ctx, mesh, np.full(8, 9, dtype=np.int32), ["mass"], precision="tf32x3")
