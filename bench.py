@@ -70,6 +70,8 @@ def parse():
                     help="skip the sampled per-cell comparison of each arm against the oracle")
     ap.add_argument("--detail-file", default="",
                     help="also write the full result (every section) to this JSON file")
+    ap.add_argument("--padaptive-dims", default="40,50,100",
+                    help="box of the p-adaptive batch extra (the configuration's 200,000 cells by default)")
     ap.add_argument("--small-extras", action="store_true",
                     help="run the other workloads on meshes 1/8 the size per axis, first two degrees each "
                          "(exercises the full output path quickly)")
@@ -155,6 +157,7 @@ def launches_per_action(fam):
 # --small-extras: the other workloads on meshes 1/8 the size per axis and their
 # first two degrees (a quick run of the full output path; not a measurement)
 SMALL_EXTRAS = False
+PADAPTIVE_DIMS = (40, 50, 100)
 
 
 def _d(*dims):
@@ -328,6 +331,8 @@ def main():
     ws, rank, local = dist_setup(args)
     global SMALL_EXTRAS
     SMALL_EXTRAS = args.small_extras
+    global PADAPTIVE_DIMS
+    PADAPTIVE_DIMS = tuple(int(v) for v in args.padaptive_dims.split(","))
     import torch
     import paper_1711_02473_gb300 as sfx
     from paper_1711_02473_gb300 import inputs
@@ -807,7 +812,7 @@ def extra_padaptive(sfx, torch, ctx, inputs, flush, stream):
     P(p) ~ 1/p, DQ_p per cell, Laplace + mass on 16 RHS (seeds 0..15): one
     graph-captured persistent launch vs one launch per (form, degree, RHS), in
     FP64 and with the TF32x3 tile body."""
-    dims = _d(40, 50, 100)
+    dims = _d(*PADAPTIVE_DIMS)
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
     deg = inputs.padaptive_degrees(int(np.prod(dims)), 8, seed=2)
     forms, R = ["laplace", "mass"], 16
