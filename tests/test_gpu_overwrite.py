@@ -136,3 +136,22 @@ def test_action_in_cuda_graph(gpu, fam, p, prec):
     torch.cuda.synchronize()
     assert torch.equal(y, y_eager)
     assert ctx.sync_status() == 0
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 3), (2, 1, 1), (1, 3, 2)])
+@pytest.mark.parametrize("fam,prec,p", [("Q", "fp64", 2), ("Q", "fp64", 8), ("Q", "tf32x3", 8), ("DQ", "fp64", 3),
+                                        ("DQ", "tf32x3", 8)])
+def test_overwrite_thin_meshes(gpu, dims, fam, prec, p):
+    """Meshes whose parity colours are partly empty (the first launched colour
+    is not colour 0) still write every dof."""
+    sfx, torch, ctx = gpu
+    mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    sp = sfx.Space(mesh, fam, p)
+    xd = torch.from_numpy(inputs.random_vector(sp.ndof, 1, seed=1)).cuda()
+
+    def run(y, acc):
+        sfx.sfx_assemble_action(ctx, "helmholtz", sp, xd, y, accumulate=acc, precision=prec)
+
+    y_over, y_acc = both(sfx, torch, run, sp.ndof)
+    assert torch.equal(y_over, y_acc)
+    assert ctx.sync_status() == 0
