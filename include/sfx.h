@@ -198,6 +198,14 @@ sfx_status sfx_space_info(const sfx_space* space, int64_t* ndof, int* nloc, int6
  * Errors: SFX_ERR_ARG. */
 sfx_status sfx_space_colours(const sfx_space* space, int* ncolour, const int64_t** colour_off,
                              const int32_t** cells);
+/* Host view of a scalar Q_p space's first-touch bits (owned by the space):
+ * ncell rows of *words_per_cell words; bit l of cell c's row is set when
+ * (c, l) is the first of its dof's cell-node pairs in colour order (the order
+ * of the scatter launches).  Overwriting FP64 actions store that pair's
+ * contribution and add the later ones instead of zeroing y first.  Other
+ * families: *words_per_cell = 0, *bits = NULL.  Any output may be NULL.
+ * Errors: SFX_ERR_ARG. */
+sfx_status sfx_space_first_touch(const sfx_space* space, int* words_per_cell, const uint32_t** bits);
 void sfx_space_destroy(sfx_space* space);
 
 /* ------------------------------------------------------------ tabulation */

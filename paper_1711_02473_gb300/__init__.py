@@ -29,7 +29,8 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported combination", -3: "C
 # every symbol include/sfx.h declares
 EXPORTS = ["sfx_ctx_create", "sfx_ctx_destroy", "sfx_sync_status", "sfx_status_string",
            "sfx_mesh_create_box", "sfx_mesh_create_structured", "sfx_mesh_create", "sfx_mesh_info",
-           "sfx_mesh_destroy", "sfx_space_create", "sfx_space_info", "sfx_space_colours", "sfx_space_destroy",
+           "sfx_mesh_destroy", "sfx_space_create", "sfx_space_info", "sfx_space_colours", "sfx_space_first_touch",
+           "sfx_space_destroy",
            "sfx_tabulate_1d",
            "sfx_assemble_action", "sfx_assemble_cell_vectors", "sfx_assemble_cell_matrices",
            "sfx_plan_create_padaptive", "sfx_plan_create_padaptive_prec", "sfx_plan_info", "sfx_plan_execute",
@@ -86,6 +87,7 @@ def lib():
         L.sfx_mesh_create.argtypes = [P, i64, P, i64, P, C.POINTER(P)]
         L.sfx_mesh_info.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(P)]
         L.sfx_space_colours.argtypes = [P, C.POINTER(i), C.POINTER(P), C.POINTER(P)]
+        L.sfx_space_first_touch.argtypes = [P, C.POINTER(i), C.POINTER(P)]
         L.sfx_mesh_destroy.argtypes = [P]
         L.sfx_mesh_destroy.restype = None
         L.sfx_space_create.argtypes = [P, i, i, C.POINTER(P)]
@@ -259,6 +261,15 @@ class Space:
         o = np.ctypeslib.as_array(C.cast(off, C.POINTER(C.c_int64)), shape=(nc.value + 1,)).copy()
         c = np.ctypeslib.as_array(C.cast(cl, C.POINTER(C.c_int32)), shape=(self.ncell,)).copy()
         return o, c
+
+    def first_touch(self):
+        """Host copy of the first-touch bits, uint32 (ncell, words), or None
+        for families other than scalar Q_p."""
+        w, bits = C.c_int(), C.c_void_p()
+        _check(lib().sfx_space_first_touch(self.h, C.byref(w), C.byref(bits)), "sfx_space_first_touch")
+        if w.value == 0:
+            return None
+        return np.ctypeslib.as_array(C.cast(bits, C.POINTER(C.c_uint32)), shape=(self.ncell, w.value)).copy()
 
     def close(self):
         if self.h:

@@ -787,6 +787,29 @@ extern "C" sfx_status sfx_space_create(const sfx_mesh* mesh, sfx_family fam, int
     }
   }
   make_tab1d(p, &s->tab);
+  if (fam == SFX_Q) {
+    // first-touch bits: walk the cells colour by colour (the order of the
+    // launches) and mark each dof's first cell-node pair
+    const int words = (nloc + 31) / 32;
+    std::vector<uint8_t> seen;
+    try {
+      s->first.assign((size_t)ncell * words, 0u);
+      seen.assign((size_t)ndof, 0);
+    } catch (...) {
+      delete s;
+      return SFX_ERR_ALLOC;
+    }
+    for (size_t k = 0; k < cells.size(); ++k) {
+      const int64_t c = cells[k];
+      const int32_t* row = &s->map[(size_t)c * nloc];
+      uint32_t* bits = &s->first[(size_t)c * words];
+      for (int l = 0; l < nloc; ++l)
+        if (!seen[(size_t)row[l]]) {
+          seen[(size_t)row[l]] = 1;
+          bits[l >> 5] |= 1u << (l & 31);
+        }
+    }
+  }
   if (mesh->ctx->device < 0) {
     *out = s;
     return SFX_OK;
@@ -794,32 +817,7 @@ extern "C" sfx_status sfx_space_create(const sfx_mesh* mesh, sfx_family fam, int
   if (upload_tables(&s->tab) != 0) { sfx_space_destroy(s); return SFX_ERR_CUDA; }
   sfx_status st = to_device(s->map.data(), s->map.size(), &s->d_map);
   if (!st) st = to_device(cells.data(), cells.size(), &s->d_cells);
-  if (!st && fam == SFX_Q) {
-    // first-touch bits: walk the cells colour by colour (the order of the
-    // launches) and mark each dof's first cell-node pair
-    const int words = (nloc + 31) / 32;
-    std::vector<uint32_t> first;
-    std::vector<uint8_t> seen;
-    try {
-      first.assign((size_t)ncell * words, 0u);
-      seen.assign((size_t)ndof, 0);
-    } catch (...) {
-      st = SFX_ERR_ALLOC;
-    }
-    if (!st) {
-      for (size_t k = 0; k < cells.size(); ++k) {
-        const int64_t c = cells[k];
-        const int32_t* row = &s->map[(size_t)c * nloc];
-        uint32_t* bits = &first[(size_t)c * words];
-        for (int l = 0; l < nloc; ++l)
-          if (!seen[(size_t)row[l]]) {
-            seen[(size_t)row[l]] = 1;
-            bits[l >> 5] |= 1u << (l & 31);
-          }
-      }
-      st = to_device(first.data(), first.size(), &s->d_first);
-    }
-  }
+  if (!st && !s->first.empty()) st = to_device(s->first.data(), s->first.size(), &s->d_first);
   if (st) { sfx_space_destroy(s); return st; }
   *out = s;
   return SFX_OK;
@@ -841,6 +839,14 @@ extern "C" sfx_status sfx_space_colours(const sfx_space* s, int* ncolour, const 
   if (ncolour) *ncolour = s->ncolour;
   if (colour_off) *colour_off = s->colour_off.data();
   if (cells) *cells = s->cells.data();
+  return SFX_OK;
+}
+
+extern "C" sfx_status sfx_space_first_touch(const sfx_space* s, int* words_per_cell, const uint32_t** bits) {
+  if (!s) return SFX_ERR_ARG;
+  const bool has = !s->first.empty();
+  if (words_per_cell) *words_per_cell = has ? (s->nloc + 31) / 32 : 0;
+  if (bits) *bits = has ? s->first.data() : nullptr;
   return SFX_OK;
 }
 

@@ -75,7 +75,8 @@ struct sfx_space {
   // (c, l) is the first of its dof's cell-node pairs in colour order, so an
   // overwriting action stores that contribution and adds the later ones
   // instead of zeroing y first (DQ_p: every pair is first; no table)
-  uint32_t* d_first = nullptr;
+  std::vector<uint32_t> first;     // host
+  uint32_t* d_first = nullptr;     // device copy
   sfx::Tab1D tab;                  // 1D tables of degree p
   // vector Q_p only: the scalar Q_p space of one component (component a's
   // global dofs are a * scalar->ndof + the scalar numbering), built on first

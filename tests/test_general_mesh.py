@@ -282,3 +282,53 @@ def test_general_mesh_rejects_bad_input(host_ctx):
     with pytest.raises(sfx.SfxError) as e:
         sfx.Csr(sfx.Space(M, "Q", 1))
     assert e.value.code == -2
+
+
+# --------------------------------------------------------------- first touch
+def first_touch_reference(off, cl, cmap):
+    """The dof's first cell-node pair in colour order, recomputed from the map
+    and the colour lists: (cell, l) pairs, one per dof."""
+    ncell, nloc = cmap.shape
+    bits = np.zeros((ncell, (nloc + 31) // 32), dtype=np.uint32)
+    seen = set()
+    for k in range(len(off) - 1):
+        for c in cl[off[k]:off[k + 1]]:
+            for l in range(nloc):
+                d = int(cmap[c, l])
+                if d not in seen:
+                    seen.add(d)
+                    bits[c, l >> 5] |= np.uint32(1 << (l & 31))
+    return bits
+
+
+@pytest.mark.parametrize("which", ["box_1x1x1", "box_1x3x2", "box_3x4x2"] + sorted(MESHES))
+def test_first_touch_bits_exact(host_ctx, which):
+    """Every dof has exactly one first-touch pair, it lies in the earliest
+    colour among the cells holding the dof, and the bits match a recomputation
+    from the map and the colour lists bit for bit; other families have none."""
+    if which.startswith("box_"):
+        dims = tuple(int(v) for v in which[4:].split("x"))
+        M = sfx.Mesh.box(host_ctx, *dims)
+    else:
+        xyz, cells = MESHES[which]()
+        M = sfx.Mesh.general(host_ctx, xyz, cells)
+    for p in (1, 2, 3):
+        sp = sfx.Space(M, "Q", p)
+        bits = sp.first_touch()
+        cmap = sp.cell_map()
+        off, cl = sp.colours()
+        np.testing.assert_array_equal(bits, first_touch_reference(off, cl, cmap))
+        colour = np.empty(sp.ncell, dtype=np.int64)
+        for k in range(len(off) - 1):
+            colour[cl[off[k]:off[k + 1]]] = k
+        l = np.arange(sp.nloc)
+        is_first = ((bits[:, l >> 5] >> (l & 31).astype(np.uint32)) & 1).astype(bool)
+        counts = np.bincount(cmap[is_first], minlength=sp.ndof)
+        assert (counts == 1).all()
+        first_col = np.full(sp.ndof, -1)
+        first_col[cmap[is_first]] = np.broadcast_to(colour[:, None], cmap.shape)[is_first]
+        min_col = np.full(sp.ndof, np.iinfo(np.int64).max)
+        np.minimum.at(min_col, cmap.ravel(), np.repeat(colour, sp.nloc))
+        np.testing.assert_array_equal(first_col, min_col)
+    for fam in ("DQ", "VQ"):
+        assert sfx.Space(M, fam, 2).first_touch() is None
