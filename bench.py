@@ -767,7 +767,7 @@ def extra_hdivcurl_mixed(sfx, torch, ctx, inputs, flush, stream):
 
 def extra_linearised(sfx, torch, ctx, inputs, flush, stream):
     """Linearised hyperelastic operator K(u) du (the Jacobian of the residual;
-    the operator whose action Sec. 4.1 times), vector Q_p on 48^3, p = 2..6,
+    the operator whose matrices Sec. 4.1 assembles and whose action Sec. 4.2 times), vector Q_p on 48^3, p = 2..6,
     state = the residual's displacement: FP64 and TF32x3 (split-precision
     contractions), the speed-up, the error against the FP64 GPU action and
     against the oracle on six sampled cells (first, last and four seeded)."""

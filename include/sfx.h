@@ -168,9 +168,10 @@ void sfx_mesh_destroy(sfx_mesh* mesh);
 
 /* ------------------------------------------------------------------- space */
 
-/* Function space of `family` and degree p (1 <= p <= 8) on `mesh`; builds the
- * int32 cell-node map (ncell x nloc, host and device) and, for the continuous
- * families, the colour lists used by the conflict-free scatter.
+/* Function space of `family` and degree p (1 <= p <= 8) on `mesh` (Secs.
+ * 2.3-2.7 for the families); builds the int32 cell-node map (ncell x nloc,
+ * host and device: the P_K of global assembly, Sec. 1.1) and, for the
+ * continuous families, the colour lists used by the conflict-free scatter.
  * Numbering on a box mesh: Q_p/vector-Q_p global node (I,J,K) on the
  * (pN+1)^3 GLL grid, vector-Q_p component-major; DQ_p cell-major
  * (cell*n^3 + l); NCF_p/NCE_p one lexicographic grid per block, block-major.
@@ -198,7 +199,8 @@ sfx_status sfx_space_info(const sfx_space* space, int64_t* ndof, int* nloc, int6
  * Errors: SFX_ERR_ARG. */
 sfx_status sfx_space_colours(const sfx_space* space, int* ncolour, const int64_t** colour_off,
                              const int32_t** cells);
-/* Host view of a scalar Q_p space's first-touch bits (owned by the space):
+/* Host view of a scalar Q_p space's first-touch bits (owned by the space; an
+ * ordering of the cellwise sum of Sec. 1.1, global assembly):
  * ncell rows of *words_per_cell words; bit l of cell c's row is set when
  * (c, l) is the first of its dof's cell-node pairs in colour order (the order
  * of the scatter launches).  Overwriting FP64 actions store that pair's
@@ -245,8 +247,9 @@ sfx_status sfx_assemble_action(sfx_ctx* ctx, sfx_form form, const sfx_form_param
                                const sfx_space* space, const double* x, double* y, int nrhs,
                                int accumulate, sfx_precision prec, sfx_algo algo, void* stream);
 
-/* Per-cell local vectors b^K (no scatter) for the cells listed in `cells`
- * (device int64, ncells entries, each in [0, ncell)), written to b (device,
+/* Per-cell local vectors b^K (Sec. 3.3, Eq. form_eval; no scatter) for the
+ * cells listed in `cells` (device int64, ncells entries, each in [0, ncell)),
+ * written to b (device,
  * ncells x nloc x nrhs).  Same arithmetic as sfx_assemble_action.  Used to
  * compare sampled cells of large meshes.  Errors as sfx_assemble_action. */
 sfx_status sfx_assemble_cell_vectors(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
@@ -271,8 +274,9 @@ sfx_status sfx_assemble_weighted_cell_matrices(sfx_ctx* ctx, const sfx_space* sp
                                                void* stream);
 
 /* Action of the linearised hyperelastic operator (the Jacobian of the
- * SFX_NEOHOOKE / SFX_SVK residual; Sec. 4.1 times the action of this
- * operator for the Saint Venant-Kirchhoff law) on vector Q_p:
+ * SFX_NEOHOOKE / SFX_SVK residual; Sec. 4.1 states the Saint Venant-Kirchhoff
+ * law and times the assembly of this operator's matrices, Sec. 4.2 its action)
+ * on vector Q_p:
  *   y_(a,j) = sum_K sum_q w_q S dP(F; dF) : (grad^ phi_j G) e_a,
  *   F = I + grad^u G (the state), dF = grad^du G (the direction),
  *   neo-Hookean dP = mu dF + (mu - lambda ln det F) F^{-T} dF^T F^{-T}
@@ -290,7 +294,7 @@ sfx_status sfx_assemble_linearised_action(sfx_ctx* ctx, sfx_form form, const sfx
                                           const sfx_space* space, const double* u, const double* du, double* y,
                                           int nrhs, int accumulate, sfx_precision prec, void* stream);
 
-/* Per-cell vectors of the same operator (no scatter) for the listed cells
+/* Per-cell vectors of the same operator (Sec. 4.1; no scatter) for the listed cells
  * (device int64, each in [0, ncell)), written to b (device, ncells x nloc x
  * nrhs).  Same arithmetic; errors as above. */
 sfx_status sfx_assemble_linearised_cell_vectors(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params,
@@ -356,8 +360,9 @@ sfx_status sfx_csr_info(const sfx_csr* csr, int64_t* nrows, int64_t* nnz, const 
  * Errors: SFX_ERR_ARG (null, form, host-only context), SFX_ERR_CUDA. */
 sfx_status sfx_csr_assemble(sfx_ctx* ctx, sfx_form form, const sfx_form_params* params, const sfx_csr* csr,
                             double* values, void* stream);
-/* y = A x with the given values (device, nnz); x, y device, nrows doubles,
- * must not alias.  A group of lanes per row, fixed-order reduction
+/* y = A x with the given values (device, nnz; the assembled operator that
+ * Sec. 4.2 weighs against the matrix-free action); x, y device, nrows
+ * doubles, must not alias.  A group of lanes per row, fixed-order reduction
  * (deterministic).  Errors: SFX_ERR_ARG, SFX_ERR_CUDA. */
 sfx_status sfx_csr_spmv(sfx_ctx* ctx, const sfx_csr* csr, const double* values, const double* x, double* y,
                         void* stream);
