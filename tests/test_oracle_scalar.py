@@ -222,3 +222,41 @@ def test_multiple_rhs_are_independent(orc):
     Y = orc.action("Q", "laplace", p, DIMS, X, x)
     for r in range(3):
         np.testing.assert_array_equal(Y[:, r], orc.action("Q", "laplace", p, DIMS, X, x[:, r].copy()))
+
+
+@pytest.mark.parametrize("p", [5, 6, 7, 8])
+def test_high_degree_identities(orc, p):
+    """The degrees the benchmark runs, on the perturbed mesh.  Physical x is
+    trilinear in the reference coordinates and S = det J has degree 2 per
+    direction, so with (p+1) Gauss points (exact to degree 2p+1) these hold to
+    rounding:
+      1^T M I(x_k^p) = 1/(p+1)         (integrand degree p+2),
+      (A u)_j = 0 at interior dofs and u^T A u = |a|^2 for u = a.x (patch test),
+      u^T A u = p^2/(2p-1) for u = x_k^p (integrand degree 2p: a rule one
+      point short, exact only to 2p-1, misses it),
+    and Helmholtz = alpha Laplace + beta mass; on DQ_p 1^T M 1 = 1 and the
+    Laplace action annihilates constants."""
+    X = mesh()
+    xq = orc.q_node_coords(p, DIMS, X)
+    for k in range(3):
+        assert abs(orc.action("Q", "mass", p, DIMS, X, xq[:, k] ** p).sum() - 1 / (p + 1)) < 1e-13
+    a = np.array([0.3, -0.7, 1.1])
+    u = xq @ a
+    Au = orc.action("Q", "laplace", p, DIMS, X, u)
+    M = [p * d + 1 for d in DIMS]
+    I, J, K = np.unravel_index(np.arange(len(u)), M)
+    interior = (I > 0) & (I < M[0] - 1) & (J > 0) & (J < M[1] - 1) & (K > 0) & (K < M[2] - 1)
+    assert np.abs(Au[interior]).max() < 1e-12
+    assert abs(u @ Au - a @ a) < 1e-12
+    k = p % 3
+    up = xq[:, k] ** p
+    assert abs(up @ orc.action("Q", "laplace", p, DIMS, X, up) - p * p / (2 * p - 1)) < 1e-12
+    x = inputs.random_vector(len(u), 1, seed=p)
+    H = orc.action("Q", "helmholtz", p, DIMS, X, x, params=(2.0, -3.0, 0, 0))
+    L = orc.action("Q", "laplace", p, DIMS, X, x)
+    Mx = orc.action("Q", "mass", p, DIMS, X, x)
+    assert np.abs(H - (2 * L - 3 * Mx)).max() < 1e-13 * np.abs(H).max()
+    nd, _ = orc.space_size("DQ", p, DIMS)
+    one = np.ones(nd)
+    assert abs(orc.action("DQ", "mass", p, DIMS, X, one).sum() - 1.0) < 1e-13
+    assert np.abs(orc.action("DQ", "laplace", p, DIMS, X, one)).max() < 1e-12
