@@ -95,7 +95,7 @@ def unit_cube_matrix(fam, p, part):
 CUBE = inputs.box_coords(1, 1, 1, perturb=0.0)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 def test_ncf_unit_cube_kronecker(orc, p):
     Am = orc.cell_matrices("NCF", "ncf_mass_divdiv", p, (1, 1, 1), CUBE, params=(1, 0, 0, 0))[0]
     Ad = orc.cell_matrices("NCF", "ncf_mass_divdiv", p, (1, 1, 1), CUBE, params=(0, 1, 0, 0))[0]
@@ -103,7 +103,7 @@ def test_ncf_unit_cube_kronecker(orc, p):
     np.testing.assert_allclose(Ad, unit_cube_matrix("NCF", p, "div"), atol=1e-13 * np.abs(Ad).max())
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 def test_nce_unit_cube_kronecker(orc, p):
     Am = orc.cell_matrices("NCE", "nce_curlcurl", p, (1, 1, 1), CUBE, params=(1, 0, 0, 0))[0]
     Ac = orc.cell_matrices("NCE", "nce_curlcurl", p, (1, 1, 1), CUBE, params=(0, 1, 0, 0))[0]
@@ -141,7 +141,7 @@ def test_ranks_on_perturbed_cells(orc, p):
         assert np.linalg.eigvalsh(0.5 * (Am[c] + Am[c].T))[0] > 0
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 5])
 def test_exact_sequence(orc, p):
     """curl-curl annihilates gradients of Q_p fields and div-div annihilates
     curls of NCE_p fields, on a perturbed mesh (the Piola maps commute with
@@ -192,7 +192,7 @@ def _cube_l2(A, b):
     return m @ m + np.sum(A * A) / 12.0
 
 
-@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("p", [2, 3, 5, 8])
 def test_nce_linear_field_on_perturbed_mesh(orc, p):
     """The covariant interpolant of a linear field is exact for p >= 2 even on
     trilinear cells, so curl u = (A - A^T) axial vector exactly and
@@ -208,10 +208,11 @@ def test_nce_linear_field_on_perturbed_mesh(orc, p):
     assert abs(u @ M - _cube_l2(A_LIN, B_LIN)) < 1e-12
 
 
-def test_ncf_linear_field_on_perturbed_mesh(orc):
+@pytest.mark.parametrize("p", [3, 5, 8])
+def test_ncf_linear_field_on_perturbed_mesh(orc, p):
     """The contravariant interpolant of a linear field is exact for p >= 3 on
     trilinear cells: div u = tr A, u^T D u = (tr A)^2, u^T M u = int |u|^2."""
-    p, d = 3, (2, 2, 2)
+    d = (2, 2, 2)
     X = inputs.box_coords(*d, perturb=0.1, seed=8)
     u = orc.interp_linear_field("NCF", p, d, X, A_LIN, B_LIN)
     Dd = orc.action("NCF", "ncf_mass_divdiv", p, d, X, u, params=(0, 1, 0, 0))
