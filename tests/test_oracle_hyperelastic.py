@@ -28,7 +28,7 @@ def nodal_field(orc, p, X, fn):
 
 
 @pytest.mark.parametrize("form", ["neohooke", "svk"])
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 8])
 def test_zero_translation_rotation(orc, form, p):
     X = mesh()
     ndof, _ = orc.space_size("VQ", p, D)
@@ -95,3 +95,24 @@ def test_homogeneous_energy(orc, form):
         E = 0.5 * (F0.T @ F0 - np.eye(3))
         W = 0.5 * lam * np.trace(E) ** 2 + mu * np.trace(E @ E)
     assert abs(orc.energy(form, p, D, X, u) - W) < 1e-14
+
+
+@pytest.mark.parametrize("form", ["neohooke", "svk"])
+@pytest.mark.parametrize("p", [2, 5, 8])
+def test_homogeneous_patch_test(orc, form, p):
+    """u = (F0 - I) x lies in vector Q_p and gives a constant F, hence a
+    constant P; the cell integrals of P : grad psi_j are integrated exactly
+    (adj J^T grad^ psi_j is a polynomial of degree p + 2 per direction), so by
+    the divergence theorem every interior row of the residual vanishes while
+    the boundary rows carry the traction P n."""
+    X = mesh()
+    F0 = np.array([[1.05, 0.02, -0.01], [0.03, 0.97, 0.02], [0.0, -0.02, 1.01]])
+    u = nodal_field(orc, p, X, lambda x: x @ (F0 - np.eye(3)).T)
+    r = orc.action("VQ", form, p, D, X, u)
+    M = [p * d + 1 for d in D]
+    I, J, K = np.unravel_index(np.arange(M[0] * M[1] * M[2]), M)
+    interior = (I > 0) & (I < M[0] - 1) & (J > 0) & (J < M[1] - 1) & (K > 0) & (K < M[2] - 1)
+    rows = np.concatenate([interior] * 3)
+    assert interior.any()
+    assert np.abs(r[rows]).max() < 1e-12 * np.abs(r).max()
+    assert np.abs(r[~rows]).max() > 1e-3
