@@ -102,7 +102,7 @@ def test_collocated_laplace_cube_kronecker(orc, p, n):
         assert np.abs(A[c] - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("p", [2, 3, 4, 6, 8])
 def test_collocated_perturbed_invariants(orc, p):
     dims = (3, 2, 3)
     X = inputs.box_coords(*dims, perturb=0.1, seed=0)

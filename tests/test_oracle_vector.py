@@ -45,7 +45,7 @@ def test_delta_pattern_and_scalar_blocks(orc, form, p):
                     assert np.abs(blk - As[c]).max() <= 1e-14 * np.abs(As[c]).max()
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 8])
 def test_closed_forms(orc, p):
     X, ndof, nloc, nq = setup(orc, p, seed=1)
     xn = orc.q_node_coords(p, D, X)

@@ -24,7 +24,7 @@ def setup(orc, fam, p, seed=0):
     return X, ndof
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 8])
 def test_energy_and_divergence_theorem(orc, p):
     X, ndof = setup(orc, "Q", p)
     xn = orc.q_node_coords(p, D, X)
@@ -41,7 +41,7 @@ def test_energy_and_divergence_theorem(orc, p):
 
 
 @pytest.mark.parametrize("fam", ["Q", "DQ"])
-@pytest.mark.parametrize("p", [1, 2, 4])
+@pytest.mark.parametrize("p", [1, 2, 4, 8])
 def test_constant_kappa_scales_laplace(orc, fam, p):
     X, ndof = setup(orc, fam, p, seed=2)
     x = inputs.random_vector(ndof, 1, seed=3)
