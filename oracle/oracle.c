@@ -120,7 +120,8 @@ double orc_lagrange_deriv(const double* xn, int n, int i, double x) {
   for (int m = 0; m < n; ++m) {
     if (m == i) continue;
     double t = 1.0 / (xn[i] - xn[m]);
-    for (int k = 0; k < n; ++k)
+    int kend = (g_plant == 15 && n > 6) ? 6 : n; /* 15: planted: a fixed loop bound, wrong for n >= 7 only */
+    for (int k = 0; k < kend; ++k)
       if (k != i && k != m) t *= (x - xn[k]) / (xn[i] - xn[k]);
     if (g_plant == 6 && m == n - 1) continue; /* planted: drops one term */
     s += t;

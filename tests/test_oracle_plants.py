@@ -158,6 +158,17 @@ def q_map_ok(orc):
     return int(m.max()) < ndof and len(np.unique(m)) == ndof
 
 
+def high_degree_energy_ok(orc):
+    """Q_6 Laplace energy of u = x^6 on the perturbed mesh: 36/11 (exact with
+    7 Gauss points).  A mistake confined to 7 or more nodes is seen only by
+    the pins at those sizes (this one, the p = 6..8 scalar-form identities and
+    the 1D Lagrange-basis pins at n = 8, 9), not by the p <= 4 assembly pins
+    or the n = 4 check above."""
+    p, X = 6, inputs.box_coords(*D, perturb=0.1, seed=0)
+    u = orc.q_node_coords(p, D, X)[:, 0] ** p
+    return abs(u @ orc.action("Q", "laplace", p, D, X, u) - p * p / (2 * p - 1)) < 1e-12
+
+
 PLANTS = {
     1: ("G used where G^T belongs", patch_ok),
     2: ("|J| dropped from the scalar forms", moments_ok),
@@ -173,6 +184,7 @@ PLANTS = {
     12: ("geometric term dF S dropped from the SVK linearisation", svk_linearisation_ok),
     13: ("wrong off-diagonal of the Gauss-Legendre Jacobi matrix", gauss_rule_ok),
     14: ("continuous factor advanced by p+1 nodes per cell (no shared dofs)", q_map_ok),
+    15: ("Lagrange derivative loop bound fixed at 6 nodes (wrong for p >= 6 only)", high_degree_energy_ok),
 }
 
 
