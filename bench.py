@@ -1057,15 +1057,20 @@ def underint_block(sfx, torch, ctx, inputs, flush, stream):
 
 def precision_block(sfx, torch, ctx, inputs, flush, stream, dims=None, degrees=None,
                     precs=("fp64", "tf32x3", "bf16x3")):
-    """Per (form, p): event time of each precision, DoF/s, speedup over FP64
-    and the normwise (inf) relative error against the FP64 GPU action (which
-    the GPU tests hold at 1e-12 of the oracle).  The displacement for degree p
-    is the first ndof draws of stream 1 scaled by 0.05 h / p, exactly what
-    inputs.displacement returns; it is generated once at the largest size and
-    sliced, since the stream is counter-based."""
+    """Per (form, p): event time of each precision, DoF/s, speedup over FP64,
+    the normwise (inf) relative error against the FP64 GPU action (which the
+    GPU tests hold at 1e-12 of the oracle) and each precision's error against
+    the oracle itself on six sampled cells (first, last and four seeded):
+    max |b - b_ref| / max |b_ref| over their per-cell vectors.  The
+    displacement for degree p is the first ndof draws of stream 1 scaled by
+    0.05 h / p, exactly what inputs.displacement returns; it is generated once
+    at the largest size and sliced, since the stream is counter-based."""
+    import oracle as orc
     dims = dims or _d(64, 64, 64)
     degrees = degrees or _ps(range(3, 9))
     mesh = sfx.Mesh.box(ctx, *dims, perturb=0.1, seed=0)
+    X = mesh.coords()
+    rng = np.random.default_rng(23)
     rows = []
     for fam, form in [("Q", "laplace"), ("VQ", "neohooke")]:
         spaces = {p: sfx.Space(mesh, fam, p) for p in degrees}
@@ -1083,8 +1088,17 @@ def precision_block(sfx, torch, ctx, inputs, flush, stream, dims=None, degrees=N
             for pr in precs[1:]:
                 row[pr + "_speedup_vs_fp64"] = row["fp64_ms"] / row[pr + "_ms"]
                 row[pr + "_rel_err_vs_fp64"] = float((ys[pr] - ys["fp64"]).abs().max() / ys["fp64"].abs().max())
+            del ys
+            cells = np.unique(np.concatenate([[0, sp.ncell - 1], rng.choice(sp.ncell, 4, replace=False)]))
+            ref = orc.cell_vectors(fam, form, p, dims, X, xd.cpu().numpy(), cells)
+            cd = torch.from_numpy(cells.astype(np.int64)).cuda()
+            for pr in precs:
+                b = torch.empty(len(cells) * sp.nloc, dtype=torch.float64, device="cuda")
+                sfx.sfx_assemble_cell_vectors(ctx, form, sp, xd, cd, b, precision=pr)
+                row[pr + "_rel_err_vs_oracle_sampled"] = float(np.abs(b.cpu().numpy().reshape(ref.shape) - ref).max()
+                                                               / np.abs(ref).max())
             rows.append(row)
-            del xd, ys
+            del xd
         del base, spaces
         torch.cuda.empty_cache()
     status = ctx.sync_status()

@@ -73,3 +73,11 @@ def test_bench_default_output_path_small():
     assert set(out["max_rel_err_vs_oracle"]) == {"tf32x3", "fp64"}
     assert any(k.startswith("extras.") for k in det)
     assert "arms" in det and "tf32x3:stored" in det["arms"]
+    # the precision extra: each precision's sampled error against the oracle
+    # (Q_p Laplace and vector Q_p neo-Hookean), within the parity tolerances
+    rows = det["extras.precision_64cube"]["rows"]
+    assert rows
+    for r in rows:
+        assert r["fp64_rel_err_vs_oracle_sampled"] <= 1e-12
+        assert r["tf32x3_rel_err_vs_oracle_sampled"] <= 2e-5
+        assert r["bf16x3_rel_err_vs_oracle_sampled"] <= 2e-3
