@@ -1,8 +1,10 @@
 """Plain FP64 CPU oracle for sum-factorised hexahedral assembly.
 
-TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package.  The library never
-does, and this package never imports the library.
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py`` (its CPU baseline, its reference arm and its columns of sampled
+error against the oracle) may import this package; no GPU result is ever an
+input here.  The library never does, and this package never imports the
+library.
 
 The C core (``oracle.c``) evaluates every integral by naive quadrature over the
 tensor Gauss rule with every basis function evaluated directly (no sum

@@ -1,7 +1,8 @@
 """Compile the oracle (plain C, FP64, OpenMP) into oracle/_build/liboracle.so.
 
 The oracle is test infrastructure: it is built so the tests, the smoke check
-and the benchmark's CPU-baseline leg can call it.  No -ffast-math: the oracle's
+and the benchmark (CPU baseline, reference arm, sampled-error columns) can call
+it.  No -ffast-math: the oracle's
 floating point follows IEEE double arithmetic in source order.
 """
 import os

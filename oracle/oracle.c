@@ -1,8 +1,8 @@
 /*
  * oracle.c -- plain FP64 CPU reference assembler (naive quadrature).
  *
- * TEST INFRASTRUCTURE ONLY: used by tests/, the smoke check and the benchmark's
- * CPU-baseline leg; never by the library.  Shares no code with the CUDA path.
+ * TEST INFRASTRUCTURE ONLY: used by tests/, the smoke check and the benchmark
+ * (CPU baseline, reference arm, sampled-error columns); never by the library.  Shares no code with the CUDA path.
  *
  * Every routine below follows the paper's definitions directly; nothing is
  * sum-factorised, blocked or fused:

@@ -4,8 +4,8 @@
  * structure: optimal code generation for high-order finite element methods").
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library links, includes or calls
- * this code; only the tests, the smoke check and the benchmark's CPU-baseline
- * leg use it.  It shares no source with the CUDA path.
+ * this code; only the tests, the smoke check and the benchmark (its CPU
+ * baseline, reference arm and sampled-error columns) use it.  It shares no source with the CUDA path.
  *
  * What it computes (naive quadrature, no sum factorisation):
  *   b^K_j = sum_q w_q I(u_K, psi_j, xi_q)          (Sec. 1.1, Eq. laplace_quadrature;
