@@ -12,7 +12,6 @@ factorisation); see the header of ``oracle.c`` for the paper sections each
 routine follows.  This module only marshals numpy arrays.
 """
 import ctypes as C
-import os
 
 import numpy as np
 
