@@ -260,3 +260,38 @@ def test_high_degree_identities(orc, p):
     one = np.ones(nd)
     assert abs(orc.action("DQ", "mass", p, DIMS, X, one).sum() - 1.0) < 1e-13
     assert np.abs(orc.action("DQ", "laplace", p, DIMS, X, one)).max() < 1e-12
+
+
+@pytest.mark.parametrize("p,dims", [(5, (3, 2, 3)), (8, (2, 1, 1))])
+def test_cell_matrices_high_degree(orc, p, dims):
+    """Element matrices at the high degrees the GPU matrix kernels are
+    compared at: symmetric, constants in the Laplace kernel, cell volumes
+    summing to 1, Laplace rank n^3 - 1; assembled, they reproduce the action
+    and the exact energies 1^T M 1 = 1 and u^T A u = p^2/(2p-1) for u = x^p
+    (integrands of degree <= 2p, exact with p+1 Gauss points)."""
+    X = inputs.box_coords(*dims, perturb=0.1, seed=0)
+    L = orc.cell_matrices("Q", "laplace", p, dims, X)
+    M = orc.cell_matrices("Q", "mass", p, dims, X)
+    n = (p + 1) ** 3
+    assert np.abs(L - L.transpose(0, 2, 1)).max() <= 1e-15 * np.abs(L).max()
+    assert np.abs(M - M.transpose(0, 2, 1)).max() <= 1e-15 * np.abs(M).max()
+    assert np.abs(L @ np.ones(n)).max() < 1e-12
+    assert abs(M.sum() - 1.0) < 1e-13
+    ev = np.linalg.eigvalsh(L[0])
+    assert ev[0] > -1e-13 and np.sum(ev > 1e-10 * ev[-1]) == n - 1
+    ndof, _ = orc.space_size("Q", p, dims)
+    m = orc.cell_map("Q", p, dims)
+
+    def assemble(A, v):
+        y = np.zeros(ndof)
+        for c in range(len(m)):
+            np.add.at(y, m[c], A[c] @ v[m[c]])
+        return y
+
+    x = inputs.random_vector(ndof, 1, seed=5)
+    for form, A in (("laplace", L), ("mass", M)):
+        y2 = orc.action("Q", form, p, dims, X, x)
+        assert np.abs(assemble(A, x) - y2).max() < 1e-13 * np.abs(y2).max()
+    u = orc.q_node_coords(p, dims, X)[:, 2] ** p
+    assert abs(u @ assemble(L, u) - p * p / (2 * p - 1)) < 1e-12
+    assert abs(np.ones(ndof) @ assemble(M, np.ones(ndof)) - 1.0) < 1e-13
