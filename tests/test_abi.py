@@ -117,3 +117,45 @@ def test_argument_errors(L, host_ctx):
     bits = C.c_uint32()
     assert L.sfx_sync_status(host_ctx.h, None, C.byref(bits)) == -1
     assert L.sfx_assemble_cell_matrices(host_ctx.h, 5, None, s.h, 0, 1, C.c_void_p(8), 0, 0, None) == -1
+
+
+def test_tuning_table_arguments(L):
+    """The launch-shape table (kinds 0..11, degrees 1..8, 0..64 cells) and the
+    warp-specialised switch check their arguments as documented and
+    round-trip what they store; nothing here touches a device."""
+    i = C.c_int()
+    saved = {}
+    for k in range(12):
+        for p in range(1, 9):
+            assert L.sfx_tune_get_cells_per_cta(k, p, C.byref(i)) == 0
+            saved[k, p] = i.value
+    try:
+        for k in range(12):
+            for p in range(1, 9):
+                assert L.sfx_tune_set_cells_per_cta(k, p, (k + p) % 7 + 1) == 0
+        for k in range(12):
+            for p in range(1, 9):
+                assert L.sfx_tune_get_cells_per_cta(k, p, C.byref(i)) == 0 and i.value == (k + p) % 7 + 1
+        for args in ((-1, 1, 1), (12, 1, 1), (0, 0, 1), (0, 9, 1), (0, 1, -1), (0, 1, 65)):
+            assert L.sfx_tune_set_cells_per_cta(*args) == -1, args
+        assert L.sfx_tune_get_cells_per_cta(0, 1, None) == -1
+        assert L.sfx_tune_get_cells_per_cta(12, 1, C.byref(i)) == -1
+    finally:
+        for (k, p), v in saved.items():
+            assert L.sfx_tune_set_cells_per_cta(k, p, v) == 0
+    e = C.c_int()
+    assert L.sfx_tune_get_warp_specialised(4, C.byref(e)) == 0
+    ws4 = e.value
+    try:
+        assert L.sfx_tune_set_warp_specialised(2, 1) == -2   # no warp-specialised kernel below p = 3
+        assert L.sfx_tune_set_warp_specialised(2, 0) == 0
+        for args in ((0, 1), (9, 0), (4, 2), (4, -1)):
+            assert L.sfx_tune_set_warp_specialised(*args) == -1, args
+        assert L.sfx_tune_get_warp_specialised(4, None) == -1
+        assert L.sfx_tune_get_warp_specialised(0, C.byref(e)) == -1
+        assert L.sfx_tune_set_warp_specialised(4, 1 - ws4) == 0
+        assert L.sfx_tune_get_warp_specialised(4, C.byref(e)) == 0 and e.value == 1 - ws4
+    finally:
+        assert L.sfx_tune_set_warp_specialised(4, ws4) == 0
+    assert L.sfx_set_wait_limit(0) == 0
+    assert L.sfx_set_wait_limit(1 << 21) == 0  # back to the documented default
