@@ -159,3 +159,22 @@ def test_tuning_table_arguments(L):
         assert L.sfx_tune_set_warp_specialised(4, ws4) == 0
     assert L.sfx_set_wait_limit(0) == 0
     assert L.sfx_set_wait_limit(1 << 21) == 0  # back to the documented default
+
+
+def test_plan_arguments(L, host_ctx):
+    """Plan creation rejects bad form counts, right-hand-side counts,
+    precisions, null pointers and a host-only context with SFX_ERR_ARG before
+    touching a device; no plan is returned."""
+    m = sfx.Mesh.box(host_ctx, 2, 2, 2)
+    deg = (C.c_int32 * 8)(*([2] * 8))
+    forms = (C.c_int * 2)(1, 0)
+    out = C.c_void_p()
+    create = L.sfx_plan_create_padaptive_prec
+    for nforms, nrhs, prec in ((0, 1, 0), (5, 1, 0), (1, 0, 0), (1, 65, 0), (1, 1, 3), (1, 1, -1)):
+        assert create(host_ctx.h, m.h, deg, nforms, forms, None, nrhs, prec, C.byref(out)) == -1
+    assert create(host_ctx.h, m.h, deg, 2, forms, None, 4, 0, C.byref(out)) == -1   # host-only context
+    assert create(host_ctx.h, None, deg, 2, forms, None, 4, 0, C.byref(out)) == -1
+    assert create(host_ctx.h, m.h, None, 2, forms, None, 4, 0, C.byref(out)) == -1
+    assert create(host_ctx.h, m.h, deg, 2, forms, None, 4, 0, None) == -1
+    assert L.sfx_plan_create_padaptive(host_ctx.h, m.h, deg, 2, forms, None, 4, C.byref(out)) == -1
+    assert not out.value
