@@ -178,3 +178,21 @@ def test_plan_arguments(L, host_ctx):
     assert create(host_ctx.h, m.h, deg, 2, forms, None, 4, 0, None) == -1
     assert L.sfx_plan_create_padaptive(host_ctx.h, m.h, deg, 2, forms, None, 4, C.byref(out)) == -1
     assert not out.value
+
+
+def test_noalloc_arguments(L, host_ctx):
+    """The allocation-free p-adaptive action rejects null or aliased
+    pointers, bad right-hand-side counts and a host-only context with
+    SFX_ERR_ARG before any device call (fake pointers are never dereferenced
+    on these paths)."""
+    m = sfx.Mesh.box(host_ctx, 2, 2, 2)
+    d, off, x, y = C.c_void_p(64), C.c_void_p(128), C.c_void_p(256), C.c_void_p(512)
+    call = L.sfx_padaptive_action_noalloc
+    assert call(None, m.h, d, off, 1, None, x, y, 1, None) == -1
+    assert call(host_ctx.h, None, d, off, 1, None, x, y, 1, None) == -1
+    assert call(host_ctx.h, m.h, None, off, 1, None, x, y, 1, None) == -1
+    assert call(host_ctx.h, m.h, d, None, 1, None, x, y, 1, None) == -1
+    assert call(host_ctx.h, m.h, d, off, 1, None, x, x, 1, None) == -1       # y aliases x
+    assert call(host_ctx.h, m.h, d, off, 1, None, x, y, 0, None) == -1
+    assert call(host_ctx.h, m.h, d, off, 1, None, x, y, 65, None) == -1
+    assert call(host_ctx.h, m.h, d, off, 1, None, x, y, 1, None) == -1       # host-only context
