@@ -196,3 +196,31 @@ def test_noalloc_arguments(L, host_ctx):
     assert call(host_ctx.h, m.h, d, off, 1, None, x, y, 0, None) == -1
     assert call(host_ctx.h, m.h, d, off, 1, None, x, y, 65, None) == -1
     assert call(host_ctx.h, m.h, d, off, 1, None, x, y, 1, None) == -1       # host-only context
+
+
+def test_assembly_entry_points_reject_host_only_context(L, host_ctx):
+    """Every assembly, matrix, stored-factor and CSR entry point returns
+    SFX_ERR_ARG on a host-only context (no device copies exist) instead of
+    launching; placeholder pointers are never dereferenced on that path."""
+    m = sfx.Mesh.box(host_ctx, 2, 2, 2)
+    q = sfx.Space(m, "Q", 2)
+    vq = sfx.Space(m, "VQ", 2)
+    csr = sfx.Csr(q)
+    a, b, c = C.c_void_p(64), C.c_void_p(128), C.c_void_p(256)
+    h = host_ctx.h
+    out = C.c_void_p()
+    calls = [
+        lambda: L.sfx_assemble_cell_vectors(h, 1, None, q.h, a, 1, b, 1, c, 0, None),
+        lambda: L.sfx_assemble_weighted_action(h, q.h, a, b, c, 1, 0, 0, None),
+        lambda: L.sfx_assemble_weighted_cell_matrices(h, q.h, a, 0, 1, b, 0, None),
+        lambda: L.sfx_assemble_linearised_action(h, 5, None, vq.h, a, b, c, 1, 0, 0, None),
+        lambda: L.sfx_assemble_linearised_cell_vectors(h, 5, None, vq.h, a, b, 1, c, 1, C.c_void_p(512), 0, None),
+        lambda: L.sfx_assemble_linearised_cell_matrices(h, 5, None, vq.h, a, 0, 1, b, 0, None),
+        lambda: L.sfx_csr_assemble(h, 1, None, csr.h, a, None),
+        lambda: L.sfx_csr_spmv(h, csr.h, a, b, c, None),
+        lambda: L.sfx_qdata_create(h, q.h, 1, None, C.byref(out)),
+        lambda: L.sfx_assemble_action_stored(h, 1, None, q.h, None, a, b, 1, 0, 0, None),
+    ]
+    for i, call in enumerate(calls):
+        assert call() == -1, i
+    assert not out.value
